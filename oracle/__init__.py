@@ -1,0 +1,174 @@
+"""FP64 CPU oracle for the pseudo-spectral Navier-Stokes hot path.
+
+TEST INFRASTRUCTURE ONLY: the tests, the smoke check and the bench's CPU
+baseline leg use it; the product library never imports, links or runs it.
+
+This module is a thin ctypes wrapper over ``ns_oracle.cpp`` (plain C++,
+its own radix-2 FFT, no code shared with the CUDA path).  Every function takes
+and returns numpy arrays in the canonical layouts described there:
+
+* truncated spectral state, complex128: 3D ``(3, c, c, h)`` = (comp, kz, ky, kx),
+  2D ``(c, h)`` = (ky, kx); ``kc = (N-1)//3``, ``c = 2 kc + 1``, ``h = kc + 1``;
+  index ``i`` on a full axis holds ``k = i`` if ``i <= kc`` else ``i - c``.
+* physical fields, float64: 3D ``(3, N, N, N)`` = (comp, z, y, x), 2D ``(N, N)``.
+
+Parity status of each function is recorded in the tests that pin it
+(``tests/test_oracle_*.py``).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "ns_oracle.cpp")
+_LIB = os.path.join(_HERE, "libns_oracle.so")
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle into ``oracle/libns_oracle.so`` (g++, OpenMP)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        cmd = ["g++", "-O2", "-std=c++17", "-fopenmp", "-fPIC", "-shared", _SRC, "-o", _LIB + ".tmp"]
+        subprocess.run(cmd, check=True)
+        os.replace(_LIB + ".tmp", _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        build()
+        lib = ctypes.CDLL(_LIB)
+        P = ctypes.c_void_p
+        I = ctypes.c_int
+        D = ctypes.c_double
+        sig = {
+            "orc_threads": ([], I),
+            "orc_set_threads": ([I], None),
+            "orc_fft1d": ([P, I, I], I),
+            "orc_rfftn": ([I, I, P, P], I),
+            "orc_irfftn": ([I, I, P, P], I),
+            "orc_phys_to_state": ([I, I, P, P], I),
+            "orc_state_to_phys": ([I, I, P, P], I),
+            "orc_rhs": ([I, I, P, P, P], I),
+            "orc_step": ([I, I, D, D, I, P, P], I),
+            "orc_diagnostics": ([I, I, P, ctypes.POINTER(D), ctypes.POINTER(D)], I),
+            "orc_nbins": ([I, I], I),
+            "orc_spectrum": ([I, I, P, P, I], I),
+        }
+        for name, (args, res) in sig.items():
+            f = getattr(lib, name)
+            f.argtypes = args
+            f.restype = res
+        _lib = lib
+    return _lib
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _check(rc: int, what: str):
+    if rc != 0:
+        raise ValueError(f"oracle {what} failed (rc={rc})")
+
+
+def sizes(n: int):
+    """(kc, c, h) of the 2/3-rule truncation for N points per axis."""
+    kc = (n - 1) // 3
+    return kc, 2 * kc + 1, kc + 1
+
+
+def state_shape(dim: int, n: int):
+    _, c, h = sizes(n)
+    return (3, c, c, h) if dim == 3 else (c, h)
+
+
+def phys_shape(dim: int, n: int):
+    return (3, n, n, n) if dim == 3 else (n, n)
+
+
+def threads() -> int:
+    return _load().orc_threads()
+
+
+def set_threads(n: int) -> None:
+    _load().orc_set_threads(int(n))
+
+
+def fft1d(x: np.ndarray, sign: int) -> np.ndarray:
+    """Unnormalised 1D DFT, ``X_k = sum_j x_j exp(sign 2 pi i j k / n)``."""
+    y = np.ascontiguousarray(x, dtype=np.complex128).copy()
+    _check(_load().orc_fft1d(_ptr(y), y.size, int(sign)), "fft1d")
+    return y
+
+
+def rfftn(dim: int, n: int, phys: np.ndarray) -> np.ndarray:
+    p = np.ascontiguousarray(phys, dtype=np.float64)
+    shape = (n, n, n // 2 + 1) if dim == 3 else (n, n // 2 + 1)
+    out = np.zeros(shape, np.complex128)
+    _check(_load().orc_rfftn(dim, n, _ptr(p), _ptr(out)), "rfftn")
+    return out
+
+
+def irfftn(dim: int, n: int, spec: np.ndarray) -> np.ndarray:
+    s = np.ascontiguousarray(spec, dtype=np.complex128)
+    out = np.zeros((n,) * dim, np.float64)
+    _check(_load().orc_irfftn(dim, n, _ptr(s), _ptr(out)), "irfftn")
+    return out
+
+
+def phys_to_state(dim: int, n: int, phys: np.ndarray) -> np.ndarray:
+    p = np.ascontiguousarray(phys, dtype=np.float64).reshape(phys_shape(dim, n))
+    out = np.zeros(state_shape(dim, n), np.complex128)
+    _check(_load().orc_phys_to_state(dim, n, _ptr(p), _ptr(out)), "phys_to_state")
+    return out
+
+
+def state_to_phys(dim: int, n: int, state: np.ndarray) -> np.ndarray:
+    s = np.ascontiguousarray(state, dtype=np.complex128).reshape(state_shape(dim, n))
+    out = np.zeros(phys_shape(dim, n), np.float64)
+    _check(_load().orc_state_to_phys(dim, n, _ptr(s), _ptr(out)), "state_to_phys")
+    return out
+
+
+def rhs(dim: int, n: int, state: np.ndarray, forcing: np.ndarray | None = None) -> np.ndarray:
+    s = np.ascontiguousarray(state, dtype=np.complex128).reshape(state_shape(dim, n))
+    f = None if forcing is None else np.ascontiguousarray(forcing, dtype=np.complex128).reshape(s.shape)
+    out = np.zeros_like(s)
+    _check(_load().orc_rhs(dim, n, _ptr(s), None if f is None else _ptr(f), _ptr(out)), "rhs")
+    return out
+
+
+def step(dim: int, n: int, nu: float, dt: float, nsteps: int, state: np.ndarray,
+         forcing: np.ndarray | None = None) -> np.ndarray:
+    """Return the state after ``nsteps`` Lawson IF-RK4 steps (input untouched)."""
+    s = np.ascontiguousarray(state, dtype=np.complex128).reshape(state_shape(dim, n)).copy()
+    f = None if forcing is None else np.ascontiguousarray(forcing, dtype=np.complex128).reshape(s.shape)
+    _check(_load().orc_step(dim, n, float(nu), float(dt), int(nsteps), None if f is None else _ptr(f), _ptr(s)),
+           "step")
+    return s
+
+
+def diagnostics(dim: int, n: int, state: np.ndarray):
+    s = np.ascontiguousarray(state, dtype=np.complex128).reshape(state_shape(dim, n))
+    e = ctypes.c_double()
+    o = ctypes.c_double()
+    _check(_load().orc_diagnostics(dim, n, _ptr(s), ctypes.byref(e), ctypes.byref(o)), "diagnostics")
+    return e.value, o.value
+
+
+def nbins(dim: int, n: int) -> int:
+    return _load().orc_nbins(dim, n)
+
+
+def spectrum(dim: int, n: int, state: np.ndarray) -> np.ndarray:
+    s = np.ascontiguousarray(state, dtype=np.complex128).reshape(state_shape(dim, n))
+    nb = nbins(dim, n)
+    out = np.zeros(nb, np.float64)
+    _check(_load().orc_spectrum(dim, n, _ptr(s), _ptr(out), nb), "spectrum")
+    return out
