@@ -1,0 +1,306 @@
+"""Throughput of the pseudo-spectral Navier-Stokes step on GB300.
+
+Workload (one "step" = one Lawson IF-RK4 step of the whole hot path):
+  3D incompressible NS, 512^3, FP32 state and FFTs, random-phase solenoidal
+  initial velocity with E(k) ~ k^4 exp(-2 (k/4)^2) (mean energy 0.5, seed 0),
+  nu = 2e-3, dt = 1e-3 (the 512^3 configuration; 20 steps per job).
+Metric: Mpoint * RK4-steps / s = N^3 * steps / seconds / 1e6 (whole job over
+all ranks).  Under torchrun every rank advances its own independent replica
+(the single-box problem does not shard without an all-to-all), so per-rank
+work is fixed and scaling is weak.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+
+--impl reference times the FP64 CPU oracle (the baseline this project is
+measured against) on the host cores, rank 0 only, one bounded sample per step.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+N_GRID = 512
+NU, DT = 2e-3, 1e-3
+JOB_STEPS = 20
+METRIC = "Mpoint*RK4-steps/s at 3D 512^3 FP32"
+UNIT = "Mpoint*steps/s"
+WORKLOAD = ("3D incompressible NS 512^3 FP32, random-phase solenoidal IC E(k)~k^4 exp(-2(k/4)^2), E=0.5, seed 0, "
+            "nu=2e-3, dt=1e-3, Lawson IF-RK4, 2/3 dealiasing")
+L2_NOTE = "inputs larger than L2: state 0.49 GB, pass buffers 3.6 GB vs 129 MB L2 (no flush needed)"
+# Algorithmic bytes of one 512^3 FP32 step for the fused three-phase model
+# (truncated spectrum, middle-axis passes counted once): 252.8 B/point.
+MODEL_BYTES_PER_POINT = 252.8
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled during the timed region."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, local_rank: int):
+        vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+        ids = [v.strip() for v in vis.split(",") if v.strip()]
+        self.index = ids[local_rank] if local_rank < len(ids) and ids[local_rank].isdigit() else str(local_rank)
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
+                                          "-lms", "100", "-i", self.index], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.15)
+        self.proc.terminate()
+        out, _ = self.proc.communicate(timeout=10)
+        sm, smax, reasons, power = [], None, set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+                power.append(float(f[3]))
+            except ValueError:
+                continue
+            for name, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm), "power_w_max": max(power) if power else None}
+
+
+def traffic_from_profiles(kernel: str):
+    """DRAM bytes per launch of a kernel from the committed ncu summary, if the
+    kernel source is unchanged since the counters were taken."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
+    if not os.path.exists(path):
+        return None
+    h = hashlib.sha1()
+    csrc = os.path.join(ROOT, "paper_1807_01769_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".cuh", ".h")):
+            with open(os.path.join(csrc, f), "rb") as fh:
+                h.update(fh.read())
+    digest = h.hexdigest()[:12]
+    for line in open(path):
+        kv = dict(tok.split("=", 1) for tok in line.split() if "=" in tok)
+        if kv.get("kernel") == kernel and kv.get("n") == str(N_GRID) and kv.get("source_sha") == digest:
+            return int(kv["dram_bytes_per_launch"])
+    return None
+
+
+def cpu_baseline(n=128, steps=2):
+    """The FP64 oracle as it stands, on this host's cores: a bounded sample
+    (`steps` RK4 steps of the same recipe on an n^3 grid)."""
+    import oracle
+    from paper_1807_01769_gb300 import inputs
+
+    u0 = inputs.random_velocity_3d(n, seed=0, k0=4.0, a=2.0, energy=0.5)
+    t0 = time.perf_counter()
+    oracle.step(3, n, NU, DT, steps, u0)
+    t = time.perf_counter() - t0
+    return {"value": n ** 3 * steps / t / 1e6, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
+            "sample": f"{steps} Lawson IF-RK4 steps of the same recipe at {n}^3 in FP64 ({t:.1f} s); the 512^3 "
+                      f"step is ~{(512 // n) ** 3}x the work"}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    import oracle
+    from paper_1807_01769_gb300 import inputs
+
+    n = 64
+    u = inputs.random_velocity_3d(n, seed=0, k0=4.0, a=2.0, energy=0.5)
+    for _ in range(args.warmup):
+        u = oracle.step(3, n, NU, DT, 1, u)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        u = oracle.step(3, n, NU, DT, 1, u)
+    t = time.perf_counter() - t0
+    v = n ** 3 * args.steps / t / 1e6
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n": N_GRID, "sample_n": n, "l2": L2_NOTE},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
+                             "sample": f"each step is one Lawson IF-RK4 step of the same recipe at {n}^3 in FP64"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_gb300(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    ws, rank, local = dist_env()
+    if args.gpus != ws and ws > 1:
+        print(f"warning: --gpus {args.gpus} but WORLD_SIZE={ws}", file=sys.stderr)
+    torch.cuda.set_device(local)
+    if ws > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if ws > 1:
+            dist.barrier()
+
+    from paper_1807_01769_gb300 import inputs, ns
+
+    # cpu baseline first, before any GPU work (oracle threads, rank 0 only)
+    cpu = cpu_baseline() if (rank == 0 and ws == 1 and not args.no_cpu_baseline) else None
+
+    u0 = inputs.random_velocity_3d(N_GRID, seed=0, k0=4.0, a=2.0, energy=0.5)
+    s = ns.Solver(3, N_GRID, ns.NS_FP32, nu=NU, dt=DT)
+    stream = torch.cuda.current_stream()
+    s.set_stream(stream.cuda_stream)
+    s.set_state_spectral(u0)
+
+    # warm-up (builds the step graph)
+    s.step(max(args.warmup, 3))
+    s.sync()
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    barrier()
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    s.step(args.steps)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1)
+    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+    if ws > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    e, om = s.diagnostics()
+    if not (np.isfinite(e) and np.isfinite(om)):
+        raise RuntimeError("non-finite state after the timed steps")
+
+    # per-kernel CUDA-event timing (instrumented launches, same stream)
+    prof = s.profile_step(3)
+    dom = max((k for k in prof if prof[k][1] > 0), key=lambda k: prof[k][0])
+    dom_ms, dom_n, dom_bytes = prof[dom]
+    dom_avg_s = dom_ms / dom_n / 1e3
+    hbm, peak_kind = peaks()
+    achieved = dom_bytes / dom_avg_s / 1e9
+    traffic = traffic_from_profiles(dom)
+
+    # end to end through the C ABI with pinned host buffers: upload the initial
+    # state, advance one job (JOB_STEPS steps), read back state and spectrum
+    spec_bytes = s.sizes["state_doubles"] * 8
+    h_in = torch.from_numpy(u0.view(np.float64).reshape(-1)).pin_memory()
+    h_out = torch.empty(s.sizes["state_doubles"], dtype=torch.float64).pin_memory()
+    e2e_reps = max(1, args.e2e_reps)
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_reps):
+        s.set_state_spectral_ptr(h_in.data_ptr())
+        s.step(JOB_STEPS)
+        s.get_state_spectral_ptr(h_out.data_ptr())
+        spec = s.energy_spectrum()
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
+    if ws > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    e2e_s = float(t.item())
+    launches_per_step = sum(v[1] for k, v in prof.items()) // 3
+
+    if rank == 0:
+        pts = N_GRID ** 3
+        value = ws * pts * args.steps / (ms_max / 1e3) / 1e6
+        step_bytes = MODEL_BYTES_PER_POINT * pts
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": max(args.warmup, 3), "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n": N_GRID, "precision": "fp32", "parallelism": f"replicas x{ws}",
+                       "l2": L2_NOTE, "job_steps": JOB_STEPS},
+            "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm, "peak_kind": peak_kind,
+                         "unit": "GB/s", "frac": achieved / hbm, "traffic": traffic,
+                         "algorithmic_bytes_per_launch": dom_bytes, "avg_launch_ms": dom_avg_s * 1e3},
+            "step_roofline": {"model_bytes_per_point": MODEL_BYTES_PER_POINT,
+                              "achieved_gbs": step_bytes / (ms_max / args.steps / 1e3) / 1e9,
+                              "frac": step_bytes / (ms_max / args.steps / 1e3) / 1e9 / hbm},
+            "kernels": {k: {"ms_per_launch": v[0] / v[1], "launches_per_step": v[1] / 3,
+                            "algorithmic_gbs": v[2] / (v[0] / v[1] / 1e3) / 1e9}
+                        for k, v in prof.items() if v[1] > 0},
+            "clocks": clk,
+            "e2e": {"value": ws * pts * JOB_STEPS * e2e_reps / e2e_s / 1e6, "unit": UNIT,
+                    "h2d_bytes_per_step": spec_bytes / JOB_STEPS,
+                    "d2h_bytes_per_step": (spec_bytes + spec.nbytes) / JOB_STEPS,
+                    "job": f"H2D of the FP64 initial spectrum (pinned), {JOB_STEPS} steps, D2H of the state and "
+                           f"spectrum; {e2e_reps} jobs"},
+            "gpu_launches": launches_per_step * args.steps,
+            "energy_after": e, "enstrophy_after": om,
+        }
+        if cpu is not None:
+            line["cpu_baseline"] = cpu
+        print(json.dumps(line), flush=True)
+    s.close()
+    if ws > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--e2e-reps", type=int, default=2)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gb300(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,167 @@
+/*
+ * ns.h -- C ABI of libns_gb300.so: the pseudo-spectral Navier-Stokes hot path
+ * of the FluidSim paper (arXiv 1807.01769) on one GB300 GPU (sm_103a).
+ *
+ * What the library computes.  The paper's solvers advance a spectral state on
+ * a periodic box with "FFT, IFFT, dealiasing, divergence, curl" operators and
+ * Runge-Kutta 4 ("Implementation and architecture / The simulation object";
+ * "CFD pseudo-spectral code comparisons / Tri-dimensional simulations": FFTs,
+ * Runge-Kutta 4, curl, vector product, projection).  Concretely, on the box
+ * [0, 2 pi)^d with N points per axis:
+ *   3D (velocity u_hat, 3 components):
+ *     N(u) = P(k) [ dealias( FFT( u x omega ) ) ] + F,  omega_hat = i k x u_hat,
+ *     P(k) = I - k k^T / |k|^2,  N(0) = 0.
+ *   2D (vorticity w_hat):
+ *     N(w) = dealias( FFT( -(u . grad w) ) ) + F,  u = (d_y psi, -d_x psi),
+ *     psi_hat = w_hat / |k|^2,  N(0) = 0.
+ *   Dealiasing keeps a mode iff every |k_i| <= kc = floor((N-1)/3).
+ *   Time step: Lawson integrating-factor RK4 with E = exp(-nu |k|^2 dt),
+ *   E2 = exp(-nu |k|^2 dt / 2):
+ *     a = E2 (u + dt/2 k1), b = E2 u + dt/2 k2, c = E u + dt E2 k3,
+ *     u' = E u + dt/6 (E k1 + 2 E2 k2 + 2 E2 k3 + k4),  k_i = N(stage input).
+ *   FFT normalisation: forward divided by N^d, inverse unnormalised.
+ *
+ * Canonical host layouts (all FP64, C order):
+ *   physical   3D: [3][N][N][N] = (comp, z, y, x);  2D: [N][N] = (y, x);
+ *              point j on an axis sits at x_j = 2 pi j / N.
+ *   spectral   truncated half spectrum, complex as (re, im) double pairs:
+ *              3D: [3][c][c][h] = (comp, kz, ky, kx);  2D: [c][h] = (ky, kx);
+ *              c = 2 kc + 1, h = kc + 1; index i on a full axis holds the
+ *              wavenumber i (i <= kc) or i - c (i > kc); index i on the x axis
+ *              holds kx = i.  Modes outside this set are zero by definition.
+ *
+ * Conventions for every entry point:
+ *   - return NS_OK (0) or a negative NS_E* code; nothing throws across the ABI;
+ *     ns_last_error() describes the last failure of a state.
+ *   - host pointers are read or written only during the call; the library
+ *     never keeps them.  All device memory is owned by the ns_state and freed
+ *     by ns_destroy.
+ *   - work is enqueued on the state's stream (ns_set_stream; by default a
+ *     stream the library creates).  Calls that return host data synchronise
+ *     that stream; ns_step only enqueues.
+ *   - the state is bound to the CUDA device that was current at ns_init;
+ *     every call switches to it and restores the caller's device.
+ *   - one ns_state must not be used from two threads at the same time.
+ */
+#ifndef NS_GB300_H
+#define NS_GB300_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define NS_OK 0
+#define NS_EINVAL (-1)       /* bad argument: null pointer, bad grid, nu < 0, dt <= 0, ... */
+#define NS_ENOMEM (-2)       /* device allocation failed */
+#define NS_ECUDA (-3)        /* a CUDA runtime call or kernel launch failed */
+#define NS_EUNSUPPORTED (-4) /* grid size or precision this build does not handle */
+#define NS_ENONFINITE (-5)   /* diagnostics found a NaN or Inf in the state */
+
+#define NS_FP64 0 /* state, FFTs and products in double precision */
+#define NS_FP32 1 /* state, FFTs and products in single precision; integrating
+                     factors computed in FP64 on the host, reductions in FP64 */
+
+typedef struct ns_state ns_state;
+
+/* Grid description.  dim = 2 or 3; n = points per axis, a power of two with
+ * 16 <= n <= 2048 (2D) or 16 <= n <= 1024 (3D); precision = NS_FP64|NS_FP32. */
+typedef struct {
+  int dim;
+  int n;
+  int precision;
+} ns_grid;
+
+/* Sizes implied by a grid (host only, no GPU needed).  Any output pointer may
+ * be null.  kc, c, h as above; state_doubles = doubles in the canonical
+ * spectral layout (2 per complex); phys_doubles = doubles in the physical
+ * layout; nbins = length of the energy spectrum (shells 0 .. round(sqrt(d) kc)).
+ * Returns NS_EINVAL / NS_EUNSUPPORTED for a bad grid. */
+int ns_sizes(const ns_grid *grid, int *kc, int *c, int *h, long long *state_doubles, long long *phys_doubles,
+             int *nbins);
+
+/* Create a solver state on the current CUDA device.
+ *   nu >= 0 kinematic viscosity (the nu_2 parameter of the paper's solvers);
+ *   dt > 0 constant time step (the paper's benchmarks use RK4 with a constant
+ *   time step: "Performance / 2D benchmarks");
+ *   forcing_phys: nullable host field in the physical layout (3 components in
+ *   3D, one vorticity forcing field in 2D); it is transformed, dealiased,
+ *   projected (3D) and held constant in time.  Copied, not kept.
+ * The initial state is zero.  On failure *out is set to null. */
+int ns_init(ns_state **out, const ns_grid *grid, double nu, double dt, const double *forcing_phys);
+
+/* Set the state from a host physical field (velocity in 3D, vorticity in 2D):
+ * FFT, dealias, project (3D), zero mean.  Synchronises. */
+int ns_set_state(ns_state *s, const double *phys_host);
+
+/* Write the state to a host physical field (inverse FFT).  Synchronises. */
+int ns_get_state(ns_state *s, double *phys_host);
+
+/* Set / get the state in the canonical truncated spectral layout (host
+ * complex128 as double pairs).  Set rounds to the state precision.  The caller
+ * supplies a Hermitian-consistent kx = 0 plane (u(0,-ky,-kz) = conj u(0,ky,kz));
+ * the inverse transforms use the real part of self-conjugate sums.  Synchronise. */
+int ns_set_state_spectral(ns_state *s, const double *spec_host);
+int ns_get_state_spectral(ns_state *s, double *spec_host);
+
+/* Advance nsteps >= 0 Lawson IF-RK4 steps.  Asynchronous: returns after the
+ * work is enqueued on the state's stream (a captured CUDA graph per step). */
+int ns_step(ns_state *s, int nsteps);
+
+/* One evaluation of the nonlinear term N(state) (forcing included), written
+ * to a host buffer in the canonical spectral layout.  Synchronises. */
+int ns_eval_rhs(ns_state *s, double *rhs_host);
+
+/* Mean energy and enstrophy of the state, accumulated in FP64
+ * ("sim.output.spatial_means"):
+ *   3D: E = sum w |u_hat|^2 / 2,          Omega = sum w |i k x u_hat|^2 / 2;
+ *   2D: E = sum w |w_hat|^2 / (2 |k|^2),  Omega = sum w |w_hat|^2 / 2;
+ * w = 1 on the kx = 0 plane, 2 elsewhere.  Synchronises.  Returns
+ * NS_ENONFINITE (values still written) if either is NaN or Inf. */
+int ns_diagnostics(ns_state *s, double *energy, double *enstrophy);
+
+/* Shell energy spectrum ("sim.output.spectra", versus the modulus of the
+ * wavenumber): out[m] = sum over modes with round(|k|) = m of the energy
+ * density above, m = 0 .. *nbins-1.  *nbins: in = capacity of out, out = bins
+ * used; NS_EINVAL if the capacity is too small.  FP64.  Synchronises. */
+int ns_energy_spectrum(ns_state *s, double *out, int *nbins);
+
+/* Bind the state to a CUDA stream (a cudaStream_t passed as void*, e.g.
+ * torch.cuda.current_stream().cuda_stream); null restores the library's own
+ * stream.  The caller keeps the stream alive while it is bound. */
+int ns_set_stream(ns_state *s, void *cuda_stream);
+
+/* Wait for all work enqueued for this state.  Reports asynchronous kernel
+ * failures as NS_ECUDA. */
+int ns_sync(ns_state *s);
+
+/* Instrumented stepping for measurement: advances nsteps like ns_step but
+ * launches kernel by kernel with CUDA events around every launch on the
+ * state's stream, then synchronises.  kernel_ms[i] (total milliseconds) and
+ * kernel_launches[i] are filled for kernel class i < capacity (see
+ * ns_kernel_name / ns_num_kernels). */
+int ns_profile_step(ns_state *s, int nsteps, double *kernel_ms, int *kernel_launches, int capacity);
+
+/* Number of kernel classes and their names (static strings). */
+int ns_num_kernels(void);
+const char *ns_kernel_name(int id);
+
+/* Algorithmic (compulsory) DRAM bytes one launch of kernel class id moves for
+ * this state's grid: bytes read from inputs + bytes written to outputs, no
+ * re-reads.  -1 for an unknown id. */
+long long ns_kernel_bytes(const ns_state *s, int id);
+
+/* Device bytes held by the state. */
+long long ns_device_bytes(const ns_state *s);
+
+/* Release everything the state owns.  Null is ignored. */
+void ns_destroy(ns_state *s);
+
+/* Description of the last failure of s (or of the last failed ns_init when s
+ * is null).  Static storage owned by the library. */
+const char *ns_last_error(const ns_state *s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NS_GB300_H */

@@ -1,0 +1,623 @@
+// ns_api.cu -- host runtime behind the C ABI of include/ns.h: grid checks,
+// device buffers, precomputed tables, the kernel sequence of one RK4 step and
+// its CUDA graph, set/get of the state, diagnostics and instrumented stepping.
+//
+// Kernel sequence of one Lawson IF-RK4 step (FluidSim paper, "The simulation
+// object": RK4 time stepping of the spectral state; "Performance / 2D
+// benchmarks": constant time step):
+//   3D, per stage s = 1..4: inv2 -> xpass -> fwd2 -> fwd1(RK stage s, + next inv1)
+//   2D, per stage s = 1..4: xpass -> fwd1(RK stage s, + next inv1)
+// The first inverse axis of the first stage (inv1 from the state) is launched
+// once per ns_step call unless the buffers still hold it from the previous
+// call; every later inv1 is fused into the preceding fwd1.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "ns.h"
+#include "ns_internal.h"
+
+using nsk::Args;
+using nsk::Geo;
+
+namespace {
+
+const int kNumKernels = 5;
+const char *kKernelNames[kNumKernels] = {"inv1", "inv2", "xpass", "fwd2", "fwd1"};
+
+thread_local std::string g_init_error;
+
+bool is_pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
+
+struct DevGuard {
+  int prev = -1, dev;
+  explicit DevGuard(int d) : dev(d) {
+    if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev);
+  }
+  ~DevGuard() {
+    if (prev >= 0 && prev != dev) cudaSetDevice(prev);
+  }
+};
+
+int grid_check(const ns_grid *g) {
+  if (!g) return NS_EINVAL;
+  if (g->dim != 2 && g->dim != 3) return NS_EINVAL;
+  if (g->precision != NS_FP64 && g->precision != NS_FP32) return NS_EINVAL;
+  if (!is_pow2(g->n)) return NS_EINVAL;
+  const int nmax = g->dim == 3 ? 1024 : 2048;
+  if (g->n < 16 || g->n > nmax) return NS_EUNSUPPORTED;
+  return NS_OK;
+}
+
+}  // namespace
+
+struct ns_state {
+  int dev = 0;
+  ns_grid grid{};
+  Geo g{};
+  int prec = 0, ncomp = 1, nbins = 0;
+  size_t cs = 8;  // bytes per complex element
+  double nu = 0, dt = 0;
+  cudaStream_t own = nullptr, stream = nullptr, cap = nullptr;
+  void *tw = nullptr, *ef = nullptr, *ef2 = nullptr, *u = nullptr, *acc = nullptr, *F = nullptr;
+  void *zb = nullptr, *yb = nullptr, *staging = nullptr, *diag = nullptr;
+  size_t staging_bytes = 0;
+  long long diag_scratch = 0;
+  long long bytes = 0;
+  bool zvalid = false;
+  cudaGraphExec_t graph = nullptr;
+  std::string err;
+};
+
+namespace {
+
+int fail(ns_state *s, int code, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  if (s)
+    s->err = buf;
+  else
+    g_init_error = buf;
+  return code;
+}
+
+#define NS_CK(s, call)                                                                                   \
+  do {                                                                                                   \
+    cudaError_t e_ = (call);                                                                             \
+    if (e_ != cudaSuccess) return fail((s), NS_ECUDA, "%s failed: %s", #call, cudaGetErrorString(e_)); \
+  } while (0)
+
+int dmalloc(ns_state *s, void **p, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    return fail(s, NS_ENOMEM, "cudaMalloc(%zu bytes) failed: %s", bytes, cudaGetErrorString(e));
+  }
+  s->bytes += (long long)bytes;
+  return NS_OK;
+}
+
+int dispatch(ns_state *s, int op, const Args &a, cudaStream_t st) {
+  int rc;
+  if (s->grid.dim == 3)
+    rc = s->prec == NS_FP32 ? nsk::dispatch3_f32(op, a, st) : nsk::dispatch3_f64(op, a, st);
+  else
+    rc = s->prec == NS_FP32 ? nsk::dispatch2_f32(op, a, st) : nsk::dispatch2_f64(op, a, st);
+  if (rc == -1) return fail(s, NS_EUNSUPPORTED, "no kernels instantiated for N=%d", s->grid.n);
+  if (rc != 0)
+    return fail(s, NS_ECUDA, "kernel launch (op %d) failed: %s", op, cudaGetErrorString((cudaError_t)rc));
+  return NS_OK;
+}
+
+Args base_args(ns_state *s) {
+  Args a;
+  std::memset(&a, 0, sizeof a);
+  a.g = s->g;
+  a.tw = s->tw;
+  a.ef = s->ef;
+  a.ef2 = s->ef2;
+  a.u = s->u;
+  a.acc = s->acc;
+  a.F = s->F;
+  a.zb = s->zb;
+  a.yb = s->yb;
+  a.dt = s->dt;
+  return a;
+}
+
+// ---------------------------------------------------------- kernel lists ---
+struct Launch {
+  int op, kernel_class;
+  Args a;
+};
+
+// first inverse axis from array src (curl / velocity form or plain)
+Launch inv1_launch(ns_state *s, const void *src, int curl) {
+  Args a = base_args(s);
+  a.src = src;
+  a.curl = curl;
+  return {nsk::OP_INV1, 0, a};
+}
+
+void stage_launches(ns_state *s, int mode, bool inv, void *dst, std::vector<Launch> &out) {
+  Args a = base_args(s);
+  if (s->grid.dim == 3) {
+    Args b = a;
+    b.nf = 6;
+    out.push_back({nsk::OP_INV2, 1, b});
+    out.push_back({nsk::OP_XPASS, 2, a});
+    b.nf = 3;
+    out.push_back({nsk::OP_FWD2, 3, b});
+  } else {
+    out.push_back({nsk::OP_XPASS, 2, a});
+  }
+  Args f = a;
+  f.mode = mode;
+  f.inv = inv ? 1 : 0;
+  f.dst = dst;
+  out.push_back({nsk::OP_FWD1, 4, f});
+}
+
+std::vector<Launch> step_launches(ns_state *s) {
+  std::vector<Launch> v;
+  for (int st = 1; st <= 4; ++st) stage_launches(s, st, true, nullptr, v);
+  return v;
+}
+
+int run_launches(ns_state *s, const std::vector<Launch> &v, cudaStream_t st) {
+  for (const Launch &l : v) {
+    int rc = dispatch(s, l.op, l.a, st);
+    if (rc) return rc;
+  }
+  return NS_OK;
+}
+
+int build_graph(ns_state *s) {
+  if (s->graph) return NS_OK;
+  std::vector<Launch> v = step_launches(s);
+  NS_CK(s, cudaStreamBeginCapture(s->cap, cudaStreamCaptureModeThreadLocal));
+  int rc = run_launches(s, v, s->cap);
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaStreamEndCapture(s->cap, &graph);
+  if (rc) {
+    if (graph) cudaGraphDestroy(graph);
+    return rc;
+  }
+  if (e != cudaSuccess) return fail(s, NS_ECUDA, "cudaStreamEndCapture failed: %s", cudaGetErrorString(e));
+  e = cudaGraphInstantiate(&s->graph, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) {
+    s->graph = nullptr;
+    return fail(s, NS_ECUDA, "cudaGraphInstantiate failed: %s", cudaGetErrorString(e));
+  }
+  return NS_OK;
+}
+
+long long phys_elems(const ns_state *s) {
+  const long long n = s->grid.n;
+  return s->grid.dim == 3 ? n * n * n : n * n;
+}
+
+long long state_rows(const ns_state *s) {
+  const long long c = s->g.c;
+  return s->grid.dim == 3 ? c * c : c;
+}
+
+// host physical field(s) -> truncated spectrum in dst (PROJ mode: dealias,
+// normalise, project in 3D, zero mean)
+int phys_to_spec(ns_state *s, const double *host, void *dst) {
+  const long long np = phys_elems(s);
+  Args a = base_args(s);
+  for (int c = 0; c < s->ncomp; ++c) {
+    NS_CK(s, cudaMemcpyAsync(s->staging, host + c * np, np * sizeof(double), cudaMemcpyHostToDevice, s->stream));
+    Args x = a;
+    x.phys_in = (const double *)s->staging;
+    x.field = c;
+    int rc = dispatch(s, nsk::OP_XFWD_REAL, x, s->stream);
+    if (rc) return rc;
+  }
+  if (s->grid.dim == 3) {
+    Args b = a;
+    b.nf = 3;
+    int rc = dispatch(s, nsk::OP_FWD2, b, s->stream);
+    if (rc) return rc;
+  }
+  Args f = a;
+  f.mode = nsk::MODE_PROJ;
+  f.inv = 0;
+  f.dst = dst;
+  int rc = dispatch(s, nsk::OP_FWD1, f, s->stream);
+  if (rc) return rc;
+  s->zvalid = false;
+  NS_CK(s, cudaStreamSynchronize(s->stream));
+  return NS_OK;
+}
+
+void free_all(ns_state *s) {
+  if (s->graph) cudaGraphExecDestroy(s->graph);
+  void *ptrs[] = {s->tw, s->ef, s->ef2, s->u, s->acc, s->F, s->zb, s->yb, s->staging, s->diag};
+  for (void *p : ptrs)
+    if (p) cudaFree(p);
+  if (s->own) cudaStreamDestroy(s->own);
+  if (s->cap) cudaStreamDestroy(s->cap);
+}
+
+template <typename R>
+void fill_tables(const ns_state *s, std::vector<unsigned char> &tw, std::vector<unsigned char> &ef,
+                 std::vector<unsigned char> &ef2) {
+  const int n = s->grid.n;
+  const long double two_pi = 6.283185307179586476925286766559005768L;
+  tw.resize(sizeof(R) * 2 * n);
+  R *t = reinterpret_cast<R *>(tw.data());
+  for (int j = 0; j < n; ++j) {
+    const double ang = (double)(two_pi * (long double)j / (long double)n);
+    t[2 * j] = (R)std::cos(ang);
+    t[2 * j + 1] = (R)(-std::sin(ang));
+  }
+  const int mmax = s->grid.dim * s->g.kc * s->g.kc;
+  ef.resize(sizeof(R) * (mmax + 1));
+  ef2.resize(sizeof(R) * (mmax + 1));
+  R *e = reinterpret_cast<R *>(ef.data());
+  R *e2 = reinterpret_cast<R *>(ef2.data());
+  for (int m = 0; m <= mmax; ++m) {
+    e[m] = (R)std::exp(-s->nu * (double)m * s->dt);
+    e2[m] = (R)std::exp(-s->nu * (double)m * s->dt * 0.5);
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+int ns_sizes(const ns_grid *grid, int *kc, int *c, int *h, long long *state_doubles, long long *phys_doubles,
+             int *nbins) {
+  const int rc = grid_check(grid);
+  if (rc) return rc;
+  const int n = grid->n, d = grid->dim;
+  const int k = (n - 1) / 3;
+  const int cc = 2 * k + 1, hh = k + 1;
+  const int ncomp = d == 3 ? 3 : 1;
+  if (kc) *kc = k;
+  if (c) *c = cc;
+  if (h) *h = hh;
+  if (state_doubles) *state_doubles = 2LL * ncomp * (d == 3 ? (long long)cc * cc : cc) * hh;
+  if (phys_doubles) *phys_doubles = (long long)ncomp * (d == 3 ? (long long)n * n * n : (long long)n * n);
+  if (nbins) *nbins = (int)std::floor(std::sqrt((double)d * k * k) + 0.5) + 1;
+  return NS_OK;
+}
+
+int ns_init(ns_state **out, const ns_grid *grid, double nu, double dt, const double *forcing_phys) {
+  if (!out) return fail(nullptr, NS_EINVAL, "ns_init: out is null");
+  *out = nullptr;
+  int rc = grid_check(grid);
+  if (rc) return fail(nullptr, rc, "ns_init: unsupported grid (dim=%d n=%d precision=%d)", grid ? grid->dim : -1,
+                      grid ? grid->n : -1, grid ? grid->precision : -1);
+  if (!(nu >= 0.0) || !std::isfinite(nu)) return fail(nullptr, NS_EINVAL, "ns_init: nu must be finite and >= 0");
+  if (!(dt > 0.0) || !std::isfinite(dt)) return fail(nullptr, NS_EINVAL, "ns_init: dt must be finite and > 0");
+
+  ns_state *s = new ns_state();
+  cudaError_t e = cudaGetDevice(&s->dev);
+  if (e != cudaSuccess) {
+    delete s;
+    return fail(nullptr, NS_ECUDA, "ns_init: no CUDA device: %s", cudaGetErrorString(e));
+  }
+  s->grid = *grid;
+  s->prec = grid->precision;
+  s->ncomp = grid->dim == 3 ? 3 : 1;
+  s->nu = nu;
+  s->dt = dt;
+  s->cs = s->prec == NS_FP32 ? 8 : 16;
+  Geo &g = s->g;
+  g.dim = grid->dim;
+  g.N = grid->n;
+  g.kc = (g.N - 1) / 3;
+  g.c = 2 * g.kc + 1;
+  g.h = g.kc + 1;
+  const int align = s->prec == NS_FP32 ? 16 : 8;  // 128 bytes of complex
+  g.hs = (g.h + align - 1) / align * align;
+  const long long N = g.N;
+  g.st_comp = (g.dim == 3 ? (long long)g.c * g.c : (long long)g.c) * g.hs;
+  g.zb_f = g.dim == 3 ? N * g.c * g.hs : 0;
+  g.yb_f = g.dim == 3 ? N * N * g.hs : N * g.hs;
+  ns_sizes(grid, nullptr, nullptr, nullptr, nullptr, nullptr, &s->nbins);
+
+  auto bail = [&](int code) {
+    g_init_error = s->err;
+    free_all(s);
+    delete s;
+    return code;
+  };
+#define INIT_CK(call)                                                                                   \
+  do {                                                                                                  \
+    cudaError_t e_ = (call);                                                                            \
+    if (e_ != cudaSuccess) {                                                                            \
+      fail(s, NS_ECUDA, "%s failed: %s", #call, cudaGetErrorString(e_));                                \
+      return bail(NS_ECUDA);                                                                            \
+    }                                                                                                   \
+  } while (0)
+  INIT_CK(cudaStreamCreateWithFlags(&s->own, cudaStreamNonBlocking));
+  INIT_CK(cudaStreamCreateWithFlags(&s->cap, cudaStreamNonBlocking));
+  s->stream = s->own;
+
+  std::vector<unsigned char> tw, ef, ef2;
+  if (s->prec == NS_FP32)
+    fill_tables<float>(s, tw, ef, ef2);
+  else
+    fill_tables<double>(s, tw, ef, ef2);
+  const size_t field = s->cs * (size_t)g.st_comp * s->ncomp;
+  const size_t zb = g.dim == 3 ? s->cs * (size_t)g.zb_f * 6 : 0;
+  const size_t yb = s->cs * (size_t)g.yb_f * (g.dim == 3 ? 6 : 4);
+  long long sd = 0;
+  ns_sizes(grid, nullptr, nullptr, nullptr, &sd, nullptr, nullptr);
+  s->staging_bytes = sizeof(double) * (size_t)std::max<long long>(phys_elems(s), sd);
+  s->diag_scratch = nsk::diag_scratch_doubles(g, s->nbins);
+  if ((rc = dmalloc(s, &s->tw, tw.size())) || (rc = dmalloc(s, &s->ef, ef.size())) ||
+      (rc = dmalloc(s, &s->ef2, ef2.size())) || (rc = dmalloc(s, &s->u, field)) ||
+      (rc = dmalloc(s, &s->acc, field)) || (rc = dmalloc(s, &s->zb, zb)) || (rc = dmalloc(s, &s->yb, yb)) ||
+      (rc = dmalloc(s, &s->staging, s->staging_bytes)) ||
+      (rc = dmalloc(s, &s->diag, sizeof(double) * (size_t)(s->diag_scratch + s->nbins + 2))))
+    return bail(rc);
+  if (forcing_phys && (rc = dmalloc(s, &s->F, field))) return bail(rc);
+  INIT_CK(cudaMemcpyAsync(s->tw, tw.data(), tw.size(), cudaMemcpyHostToDevice, s->stream));
+  INIT_CK(cudaMemcpyAsync(s->ef, ef.data(), ef.size(), cudaMemcpyHostToDevice, s->stream));
+  INIT_CK(cudaMemcpyAsync(s->ef2, ef2.data(), ef2.size(), cudaMemcpyHostToDevice, s->stream));
+  INIT_CK(cudaMemsetAsync(s->u, 0, field, s->stream));
+  INIT_CK(cudaMemsetAsync(s->acc, 0, field, s->stream));
+  if (zb) INIT_CK(cudaMemsetAsync(s->zb, 0, zb, s->stream));
+  INIT_CK(cudaMemsetAsync(s->yb, 0, yb, s->stream));
+  Args a = base_args(s);
+  if ((rc = dispatch(s, nsk::OP_PREPARE, a, s->stream))) return bail(rc);
+  if (forcing_phys) {
+    INIT_CK(cudaMemsetAsync(s->F, 0, field, s->stream));
+    if ((rc = phys_to_spec(s, forcing_phys, s->F))) return bail(rc);
+  }
+  INIT_CK(cudaStreamSynchronize(s->stream));
+#undef INIT_CK
+  *out = s;
+  return NS_OK;
+}
+
+int ns_set_stream(ns_state *s, void *cuda_stream) {
+  if (!s) return NS_EINVAL;
+  s->stream = cuda_stream ? (cudaStream_t)cuda_stream : s->own;
+  return NS_OK;
+}
+
+int ns_sync(ns_state *s) {
+  if (!s) return NS_EINVAL;
+  DevGuard dg(s->dev);
+  NS_CK(s, cudaStreamSynchronize(s->stream));
+  NS_CK(s, cudaGetLastError());
+  return NS_OK;
+}
+
+int ns_set_state(ns_state *s, const double *phys_host) {
+  if (!s || !phys_host) return s ? fail(s, NS_EINVAL, "ns_set_state: null field") : NS_EINVAL;
+  DevGuard dg(s->dev);
+  return phys_to_spec(s, phys_host, s->u);
+}
+
+int ns_get_state(ns_state *s, double *phys_host) {
+  if (!s || !phys_host) return s ? fail(s, NS_EINVAL, "ns_get_state: null field") : NS_EINVAL;
+  DevGuard dg(s->dev);
+  int rc;
+  Launch l = inv1_launch(s, s->u, 0);
+  if ((rc = dispatch(s, l.op, l.a, s->stream))) return rc;
+  if (s->grid.dim == 3) {
+    Args b = base_args(s);
+    b.nf = 3;
+    if ((rc = dispatch(s, nsk::OP_INV2, b, s->stream))) return rc;
+  }
+  const long long np = phys_elems(s);
+  for (int c = 0; c < s->ncomp; ++c) {
+    Args x = base_args(s);
+    x.phys_out = (double *)s->staging;
+    x.field = c;
+    if ((rc = dispatch(s, nsk::OP_XINV_REAL, x, s->stream))) return rc;
+    NS_CK(s, cudaMemcpyAsync(phys_host + c * np, s->staging, np * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+  }
+  s->zvalid = false;
+  NS_CK(s, cudaStreamSynchronize(s->stream));
+  return NS_OK;
+}
+
+int ns_set_state_spectral(ns_state *s, const double *spec_host) {
+  if (!s || !spec_host) return s ? fail(s, NS_EINVAL, "ns_set_state_spectral: null buffer") : NS_EINVAL;
+  DevGuard dg(s->dev);
+  const long long rows = state_rows(s);
+  const size_t bytes = sizeof(double) * 2 * (size_t)rows * s->g.h;
+  for (int c = 0; c < s->ncomp; ++c) {
+    NS_CK(s, cudaMemcpyAsync(s->staging, spec_host + c * 2 * rows * s->g.h, bytes, cudaMemcpyHostToDevice,
+                             s->stream));
+    int e = nsk::spec_in(s->prec, (char *)s->u + c * s->cs * s->g.st_comp, (const double *)s->staging, rows,
+                         s->g.h, s->g.hs, s->stream);
+    if (e) return fail(s, NS_ECUDA, "spec_in launch failed: %s", cudaGetErrorString((cudaError_t)e));
+  }
+  s->zvalid = false;
+  NS_CK(s, cudaStreamSynchronize(s->stream));
+  return NS_OK;
+}
+
+static int get_spectral(ns_state *s, const void *src, double *spec_host) {
+  const long long rows = state_rows(s);
+  const size_t bytes = sizeof(double) * 2 * (size_t)rows * s->g.h;
+  for (int c = 0; c < s->ncomp; ++c) {
+    int e = nsk::spec_out(s->prec, (double *)s->staging, (const char *)src + c * s->cs * s->g.st_comp, rows, s->g.h,
+                          s->g.hs, s->stream);
+    if (e) return fail(s, NS_ECUDA, "spec_out launch failed: %s", cudaGetErrorString((cudaError_t)e));
+    NS_CK(s, cudaMemcpyAsync(spec_host + c * 2 * rows * s->g.h, s->staging, bytes, cudaMemcpyDeviceToHost,
+                             s->stream));
+  }
+  NS_CK(s, cudaStreamSynchronize(s->stream));
+  return NS_OK;
+}
+
+int ns_get_state_spectral(ns_state *s, double *spec_host) {
+  if (!s || !spec_host) return s ? fail(s, NS_EINVAL, "ns_get_state_spectral: null buffer") : NS_EINVAL;
+  DevGuard dg(s->dev);
+  return get_spectral(s, s->u, spec_host);
+}
+
+int ns_step(ns_state *s, int nsteps) {
+  if (!s) return NS_EINVAL;
+  if (nsteps < 0) return fail(s, NS_EINVAL, "ns_step: nsteps < 0");
+  if (nsteps == 0) return NS_OK;
+  DevGuard dg(s->dev);
+  int rc;
+  if ((rc = build_graph(s))) return rc;
+  if (!s->zvalid) {
+    Launch l = inv1_launch(s, s->u, 1);
+    if ((rc = dispatch(s, l.op, l.a, s->stream))) return rc;
+  }
+  for (int i = 0; i < nsteps; ++i) NS_CK(s, cudaGraphLaunch(s->graph, s->stream));
+  s->zvalid = true;
+  return NS_OK;
+}
+
+int ns_eval_rhs(ns_state *s, double *rhs_host) {
+  if (!s || !rhs_host) return s ? fail(s, NS_EINVAL, "ns_eval_rhs: null buffer") : NS_EINVAL;
+  DevGuard dg(s->dev);
+  std::vector<Launch> v;
+  v.push_back(inv1_launch(s, s->u, 1));
+  stage_launches(s, nsk::MODE_RHS, false, s->acc, v);
+  int rc = run_launches(s, v, s->stream);
+  if (rc) return rc;
+  s->zvalid = false;
+  return get_spectral(s, s->acc, rhs_host);
+}
+
+static int run_diag(ns_state *s, std::vector<double> &out) {
+  double *scratch = (double *)s->diag;
+  double *dout = scratch + s->diag_scratch;
+  int e = nsk::diagnostics(s->prec, s->g, s->u, s->nbins, scratch, dout, s->stream);
+  if (e) return fail(s, NS_ECUDA, "diagnostics launch failed: %s", cudaGetErrorString((cudaError_t)e));
+  out.resize(s->nbins + 2);
+  NS_CK(s, cudaMemcpyAsync(out.data(), dout, sizeof(double) * out.size(), cudaMemcpyDeviceToHost, s->stream));
+  NS_CK(s, cudaStreamSynchronize(s->stream));
+  return NS_OK;
+}
+
+int ns_diagnostics(ns_state *s, double *energy, double *enstrophy) {
+  if (!s || !energy || !enstrophy) return s ? fail(s, NS_EINVAL, "ns_diagnostics: null output") : NS_EINVAL;
+  DevGuard dg(s->dev);
+  std::vector<double> out;
+  int rc = run_diag(s, out);
+  if (rc) return rc;
+  *energy = out[0];
+  *enstrophy = out[1];
+  if (!std::isfinite(out[0]) || !std::isfinite(out[1]))
+    return fail(s, NS_ENONFINITE, "state holds NaN or Inf (energy=%g enstrophy=%g)", out[0], out[1]);
+  return NS_OK;
+}
+
+int ns_energy_spectrum(ns_state *s, double *out, int *nbins) {
+  if (!s || !out || !nbins) return s ? fail(s, NS_EINVAL, "ns_energy_spectrum: null output") : NS_EINVAL;
+  if (*nbins < s->nbins) {
+    const int need = s->nbins;
+    *nbins = need;
+    return fail(s, NS_EINVAL, "ns_energy_spectrum: capacity too small (need %d bins)", need);
+  }
+  DevGuard dg(s->dev);
+  std::vector<double> v;
+  int rc = run_diag(s, v);
+  if (rc) return rc;
+  std::memcpy(out, v.data() + 2, sizeof(double) * s->nbins);
+  *nbins = s->nbins;
+  return NS_OK;
+}
+
+int ns_profile_step(ns_state *s, int nsteps, double *kernel_ms, int *kernel_launches, int capacity) {
+  if (!s || nsteps < 0 || !kernel_ms || !kernel_launches)
+    return s ? fail(s, NS_EINVAL, "ns_profile_step: bad arguments") : NS_EINVAL;
+  DevGuard dg(s->dev);
+  for (int i = 0; i < capacity; ++i) {
+    kernel_ms[i] = 0.0;
+    kernel_launches[i] = 0;
+  }
+  std::vector<Launch> step = step_launches(s);
+  std::vector<cudaEvent_t> ev(2 * (step.size() + 1));
+  for (auto &e : ev) NS_CK(s, cudaEventCreate(&e));
+  int rc = NS_OK;
+  for (int it = 0; it < nsteps && rc == NS_OK; ++it) {
+    std::vector<Launch> v;
+    if (!s->zvalid) v.push_back(inv1_launch(s, s->u, 1));
+    v.insert(v.end(), step.begin(), step.end());
+    for (size_t i = 0; i < v.size() && rc == NS_OK; ++i) {
+      cudaEventRecord(ev[2 * i], s->stream);
+      rc = dispatch(s, v[i].op, v[i].a, s->stream);
+      cudaEventRecord(ev[2 * i + 1], s->stream);
+    }
+    if (rc) break;
+    s->zvalid = true;
+    cudaError_t e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) {
+      rc = fail(s, NS_ECUDA, "ns_profile_step: %s", cudaGetErrorString(e));
+      break;
+    }
+    for (size_t i = 0; i < v.size(); ++i) {
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, ev[2 * i], ev[2 * i + 1]);
+      const int k = v[i].kernel_class;
+      if (k < capacity) {
+        kernel_ms[k] += ms;
+        kernel_launches[k] += 1;
+      }
+    }
+  }
+  for (auto &e : ev) cudaEventDestroy(e);
+  return rc;
+}
+
+int ns_num_kernels(void) { return kNumKernels; }
+
+const char *ns_kernel_name(int id) { return (id >= 0 && id < kNumKernels) ? kKernelNames[id] : nullptr; }
+
+long long ns_kernel_bytes(const ns_state *s, int id) {
+  if (!s || id < 0 || id >= kNumKernels) return -1;
+  const long long cs = (long long)s->cs, N = s->g.N, c = s->g.c, h = s->g.h;
+  const bool f = s->F != nullptr;
+  if (s->grid.dim == 3) {
+    const long long T = c * c * h, Z = N * c * h, Y = N * N * h;
+    switch (id) {
+      case 0: return cs * (3 * T + 6 * Z);
+      case 1: return cs * (6 * Z + 6 * Y);
+      case 2: return cs * (6 * Y + 3 * Y);
+      case 3: return cs * (3 * Y + 3 * Z);
+      default:  // 3 fields in, 6 out, plus the RK operands averaged over the four
+                // stages (state-sized reads 18 T, writes 12 T per step)
+        return cs * (9 * Z + (15 * T) / 2 + (f ? 3 * T : 0));
+    }
+  }
+  const long long T = c * h, Y = N * h;
+  switch (id) {
+    case 0: return cs * (T + 4 * Y);
+    case 2: return cs * (4 * Y + Y);
+    case 4: return cs * (Y + 4 * Y + (5 * T) / 2 + (f ? T : 0));
+    default: return 0;
+  }
+}
+
+long long ns_device_bytes(const ns_state *s) { return s ? s->bytes : 0; }
+
+void ns_destroy(ns_state *s) {
+  if (!s) return;
+  DevGuard dg(s->dev);
+  if (s->stream) cudaStreamSynchronize(s->stream);
+  free_all(s);
+  delete s;
+}
+
+const char *ns_last_error(const ns_state *s) { return s ? s->err.c_str() : g_init_error.c_str(); }
+
+}  // extern "C"

@@ -1,0 +1,198 @@
+// ns_aux.cu -- layout conversion between the canonical FP64 spectral layout
+// and the padded device state, and the FP64 diagnostics ("sim.output.
+// spatial_means" energy and enstrophy, "sim.output.spectra" shell spectrum in
+// the FluidSim paper's output list).
+//
+// The diagnostics are deterministic: every block owns a fixed set of (kz, ky)
+// rows, each warp a fixed subset of them; along a row |k| grows with kx, so
+// the shell index of 32 consecutive kx is non-decreasing and a warp-wide
+// segmented scan adds each run of equal shells in a fixed order before one
+// lane per run updates the warp's private bins.  Blocks write partial sums to
+// scratch; a single block adds them in block order.
+#include <climits>
+
+#include "ns_fft.cuh"
+#include "ns_internal.h"
+
+namespace nsk {
+
+template <typename C>
+__global__ void k_spec_in(C *__restrict__ dst, const double2 *__restrict__ src, long long rows, int h, int hs) {
+  using R = decltype(C{}.x);
+  const long long total = rows * hs;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
+    const long long r = i / hs;
+    const int k = (int)(i % hs);
+    if (k < h) {
+      const double2 v = src[r * h + k];
+      dst[i] = C{(R)v.x, (R)v.y};
+    } else {
+      dst[i] = C{0, 0};
+    }
+  }
+}
+
+template <typename C>
+__global__ void k_spec_out(double2 *__restrict__ dst, const C *__restrict__ src, long long rows, int h, int hs) {
+  const long long total = rows * h;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
+    const long long r = i / h;
+    const int k = (int)(i % h);
+    const C v = src[r * hs + k];
+    dst[i] = make_double2((double)v.x, (double)v.y);
+  }
+}
+
+static unsigned grid_for(long long n, int threads) {
+  long long b = (n + threads - 1) / threads;
+  if (b > 152LL * 16) b = 152LL * 16;
+  if (b < 1) b = 1;
+  return (unsigned)b;
+}
+
+int spec_in(int prec, void *dst, const double *src, long long rows, int h, int hs, cudaStream_t s) {
+  const unsigned g = grid_for(rows * hs, 256);
+  if (prec == 1)
+    k_spec_in<float2><<<g, 256, 0, s>>>((float2 *)dst, (const double2 *)src, rows, h, hs);
+  else
+    k_spec_in<double2><<<g, 256, 0, s>>>((double2 *)dst, (const double2 *)src, rows, h, hs);
+  return (int)cudaGetLastError();
+}
+
+int spec_out(int prec, double *dst, const void *src, long long rows, int h, int hs, cudaStream_t s) {
+  const unsigned g = grid_for(rows * h, 256);
+  if (prec == 1)
+    k_spec_out<float2><<<g, 256, 0, s>>>((double2 *)dst, (const float2 *)src, rows, h, hs);
+  else
+    k_spec_out<double2><<<g, 256, 0, s>>>((double2 *)dst, (const double2 *)src, rows, h, hs);
+  return (int)cudaGetLastError();
+}
+
+constexpr int kDiagWarps = 8;
+
+static long long diag_rows(const Geo &g) { return g.dim == 3 ? (long long)g.c * g.c : (long long)g.c; }
+
+long long diag_blocks(const Geo &g) {
+  long long nb = (diag_rows(g) + kDiagWarps - 1) / kDiagWarps;
+  if (nb > 152 * 8) nb = 152 * 8;
+  return nb;
+}
+
+long long diag_scratch_doubles(const Geo &g, int nbins) { return diag_blocks(g) * (nbins + 2); }
+
+// scratch row of block b: [energy, enstrophy, bins 0 .. nbins-1]
+template <typename C>
+__global__ void __launch_bounds__(32 * kDiagWarps) k_diag(Geo g, const C *__restrict__ u, int nbins, int rows_per_block,
+                                                          double *__restrict__ scratch) {
+  extern __shared__ __align__(16) unsigned char diag_smem[];
+  double *bins = reinterpret_cast<double *>(diag_smem);  // [kDiagWarps][nbins]
+  double *wsum = bins + kDiagWarps * nbins;              // [kDiagWarps][2]
+  for (int i = threadIdx.x; i < kDiagWarps * nbins; i += blockDim.x) bins[i] = 0.0;
+  __syncthreads();
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const long long nrows = g.dim == 3 ? (long long)g.c * g.c : (long long)g.c;
+  const long long r0 = (long long)blockIdx.x * rows_per_block;
+  const long long r1 = min(nrows, r0 + rows_per_block);
+  double e_acc = 0.0, o_acc = 0.0;
+  double *mybins = bins + warp * nbins;
+  for (long long r = r0 + warp; r < r1; r += kDiagWarps) {
+    const int iy = (int)(r % g.c);
+    const int iz = g.dim == 3 ? (int)(r / g.c) : 0;
+    const int ky = iy <= g.kc ? iy : iy - g.c;
+    const int kz = g.dim == 3 ? (iz <= g.kc ? iz : iz - g.c) : 0;
+    const long long base = r * g.hs;
+    for (int kx0 = 0; kx0 < g.h; kx0 += 32) {
+      const int kx = kx0 + lane;
+      const bool active = kx < g.h;
+      double ve = 0.0, vo = 0.0;
+      int bin = INT_MAX;
+      if (active) {
+        const double w = kx == 0 ? 1.0 : 2.0;
+        const long long k2 = (long long)kx * kx + (long long)ky * ky + (long long)kz * kz;
+        bin = (int)floor(sqrt((double)k2) + 0.5);
+        if (g.dim == 3) {
+          const C a = u[base + kx], b = u[g.st_comp + base + kx], c = u[2 * g.st_comp + base + kx];
+          const double ax = a.x, ay = a.y, bx = b.x, by = b.y, cx = c.x, cy = c.y;
+          ve = 0.5 * w * (ax * ax + ay * ay + bx * bx + by * by + cx * cx + cy * cy);
+          // |k x u|^2, real and imaginary parts separately
+          const double dkx = kx, dky = ky, dkz = kz;
+          const double wxr = dky * cx - dkz * bx, wxi = dky * cy - dkz * by;
+          const double wyr = dkz * ax - dkx * cx, wyi = dkz * ay - dkx * cy;
+          const double wzr = dkx * bx - dky * ax, wzi = dkx * by - dky * ay;
+          vo = 0.5 * w * (wxr * wxr + wxi * wxi + wyr * wyr + wyi * wyi + wzr * wzr + wzi * wzi);
+        } else {
+          const C a = u[base + kx];
+          const double m2 = (double)a.x * a.x + (double)a.y * a.y;
+          vo = 0.5 * w * m2;
+          ve = k2 > 0 ? 0.5 * w * m2 / (double)k2 : 0.0;
+        }
+      }
+      e_acc += ve;
+      o_acc += vo;
+      // segmented inclusive scan of ve over runs of equal bin
+      double sv = ve;
+#pragma unroll
+      for (int off = 1; off < 32; off <<= 1) {
+        const double ov = __shfl_up_sync(0xffffffffu, sv, off);
+        const int ob = __shfl_up_sync(0xffffffffu, bin, off);
+        if (lane >= off && ob == bin) sv += ov;
+      }
+      const int nb = __shfl_down_sync(0xffffffffu, bin, 1);
+      const bool run_end = (lane == 31) || (nb != bin);
+      if (active && run_end) mybins[bin] += sv;
+      __syncwarp();
+    }
+  }
+  // fixed-order warp reduction of the per-lane totals
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    e_acc += __shfl_xor_sync(0xffffffffu, e_acc, off);
+    o_acc += __shfl_xor_sync(0xffffffffu, o_acc, off);
+  }
+  if (lane == 0) {
+    wsum[2 * warp] = e_acc;
+    wsum[2 * warp + 1] = o_acc;
+  }
+  __syncthreads();
+  double *out = scratch + (long long)blockIdx.x * (nbins + 2);
+  if (threadIdx.x == 0) {
+    double e = 0.0, o = 0.0;
+    for (int w = 0; w < kDiagWarps; ++w) {
+      e += wsum[2 * w];
+      o += wsum[2 * w + 1];
+    }
+    out[0] = e;
+    out[1] = o;
+  }
+  for (int j = threadIdx.x; j < nbins; j += blockDim.x) {
+    double sacc = 0.0;
+    for (int w = 0; w < kDiagWarps; ++w) sacc += bins[w * nbins + j];
+    out[2 + j] = sacc;
+  }
+}
+
+__global__ void k_diag_final(const double *__restrict__ scratch, long long nblocks, int width, double *__restrict__ out) {
+  for (int j = threadIdx.x; j < width; j += blockDim.x) {
+    double sacc = 0.0;
+    for (long long b = 0; b < nblocks; ++b) sacc += scratch[b * width + j];
+    out[j] = sacc;
+  }
+}
+
+int diagnostics(int prec, const Geo &g, const void *u, int nbins, double *scratch, double *out, cudaStream_t s) {
+  const long long nb = diag_blocks(g);
+  const long long rows = diag_rows(g);
+  const int rpb = (int)((rows + nb - 1) / nb);
+  const size_t smem = sizeof(double) * ((size_t)kDiagWarps * nbins + 2 * kDiagWarps);
+  if (prec == 1) {
+    cudaFuncSetAttribute(k_diag<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_diag<float2><<<(unsigned)nb, 32 * kDiagWarps, smem, s>>>(g, (const float2 *)u, nbins, rpb, scratch);
+  } else {
+    cudaFuncSetAttribute(k_diag<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_diag<double2><<<(unsigned)nb, 32 * kDiagWarps, smem, s>>>(g, (const double2 *)u, nbins, rpb, scratch);
+  }
+  k_diag_final<<<1, 256, 0, s>>>(scratch, nb, nbins + 2, out);
+  return (int)cudaGetLastError();
+}
+
+}  // namespace nsk

@@ -1,0 +1,232 @@
+// ns_fft.cuh -- device-side building blocks of the pass kernels: complex
+// arithmetic and a batched power-of-two FFT whose data live in registers
+// (8 points per thread) and move between radix stages through shared memory.
+//
+// The FFT is the self-sorting (Stockham) decimation-in-time form: with
+// T = L/8 threads per line, thread t holds x[t + T m], m = 0..7, before the
+// first stage and X[t + T m] after the last one, so a pass kernel can load its
+// inputs straight from global memory and store its outputs straight back with
+// the same, coalesced, index pattern.  A stage of radix R and span Ns takes
+// butterfly j from x[j + r L/R], twiddles input r by exp(+-2 pi i r (j mod Ns)
+// / (Ns R)), does a length-R DFT in registers and writes output r to
+// y[(j / Ns) Ns R + j mod Ns + r Ns].  L = 8^a * R0 with R0 in {1, 2, 4}; the
+// small radix, if any, is the first stage (no twiddles there).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace nsk {
+
+template <typename R>
+struct CplxOf;
+template <>
+struct CplxOf<float> {
+  using T = float2;
+};
+template <>
+struct CplxOf<double> {
+  using T = double2;
+};
+
+template <typename C>
+__device__ __forceinline__ C cadd(C a, C b) {
+  return C{a.x + b.x, a.y + b.y};
+}
+template <typename C>
+__device__ __forceinline__ C csub(C a, C b) {
+  return C{a.x - b.x, a.y - b.y};
+}
+template <typename C>
+__device__ __forceinline__ C cmul(C a, C b) {
+  return C{a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
+}
+template <typename C>
+__device__ __forceinline__ C cconj(C a) {
+  return C{a.x, -a.y};
+}
+template <typename C, typename R>
+__device__ __forceinline__ C cscale(C a, R s) {
+  return C{a.x * s, a.y * s};
+}
+// i * a
+template <typename C>
+__device__ __forceinline__ C cmuli(C a) {
+  return C{-a.y, a.x};
+}
+// (DIR i) * a, DIR = +1 or -1
+template <int DIR, typename C>
+__device__ __forceinline__ C cmul_diri(C a) {
+  return DIR > 0 ? C{-a.y, a.x} : C{a.y, -a.x};
+}
+template <typename C>
+__device__ __forceinline__ C czero() {
+  return C{0, 0};
+}
+
+__host__ __device__ constexpr int ilog2(int n) { return n <= 1 ? 0 : 1 + ilog2(n / 2); }
+
+// ------------------------------------------------------------ small DFTs --
+// X_s = sum_r a_r exp(DIR 2 pi i r s / R), natural order in and out.
+template <int DIR, typename C>
+__device__ __forceinline__ void dft2(C &a0, C &a1) {
+  const C t = a0;
+  a0 = cadd(t, a1);
+  a1 = csub(t, a1);
+}
+
+template <int DIR, typename C>
+__device__ __forceinline__ void dft4(C &a0, C &a1, C &a2, C &a3) {
+  const C t0 = cadd(a0, a2), t1 = csub(a0, a2);
+  const C t2 = cadd(a1, a3), t3 = cmul_diri<DIR>(csub(a1, a3));
+  a0 = cadd(t0, t2);
+  a2 = csub(t0, t2);
+  a1 = cadd(t1, t3);
+  a3 = csub(t1, t3);
+}
+
+template <int DIR, typename C>
+__device__ __forceinline__ void dft8(C (&a)[8]) {
+  using R = decltype(a[0].x);
+  const R h = (R)0.70710678118654752440084436210484903928;  // 1/sqrt(2)
+  C e0 = a[0], e1 = a[2], e2 = a[4], e3 = a[6];
+  C o0 = a[1], o1 = a[3], o2 = a[5], o3 = a[7];
+  dft4<DIR>(e0, e1, e2, e3);
+  dft4<DIR>(o0, o1, o2, o3);
+  // o_k *= w^k, w = exp(DIR 2 pi i / 8) = (1 + DIR i)/sqrt(2)
+  o1 = C{h * (o1.x - DIR * o1.y), h * (o1.y + DIR * o1.x)};
+  o2 = cmul_diri<DIR>(o2);
+  o3 = C{h * (-o3.x - DIR * o3.y), h * (-o3.y + DIR * o3.x)};
+  a[0] = cadd(e0, o0);
+  a[4] = csub(e0, o0);
+  a[1] = cadd(e1, o1);
+  a[5] = csub(e1, o1);
+  a[2] = cadd(e2, o2);
+  a[6] = csub(e2, o2);
+  a[3] = cadd(e3, o3);
+  a[7] = csub(e3, o3);
+}
+
+template <int R, int DIR, typename C>
+__device__ __forceinline__ void dftR(C (&a)[R]);
+template <>
+__device__ __forceinline__ void dftR<2, -1, float2>(float2 (&a)[2]) { dft2<-1>(a[0], a[1]); }
+template <>
+__device__ __forceinline__ void dftR<2, 1, float2>(float2 (&a)[2]) { dft2<1>(a[0], a[1]); }
+template <>
+__device__ __forceinline__ void dftR<2, -1, double2>(double2 (&a)[2]) { dft2<-1>(a[0], a[1]); }
+template <>
+__device__ __forceinline__ void dftR<2, 1, double2>(double2 (&a)[2]) { dft2<1>(a[0], a[1]); }
+template <>
+__device__ __forceinline__ void dftR<4, -1, float2>(float2 (&a)[4]) { dft4<-1>(a[0], a[1], a[2], a[3]); }
+template <>
+__device__ __forceinline__ void dftR<4, 1, float2>(float2 (&a)[4]) { dft4<1>(a[0], a[1], a[2], a[3]); }
+template <>
+__device__ __forceinline__ void dftR<4, -1, double2>(double2 (&a)[4]) { dft4<-1>(a[0], a[1], a[2], a[3]); }
+template <>
+__device__ __forceinline__ void dftR<4, 1, double2>(double2 (&a)[4]) { dft4<1>(a[0], a[1], a[2], a[3]); }
+template <>
+__device__ __forceinline__ void dftR<8, -1, float2>(float2 (&a)[8]) { dft8<-1>(a); }
+template <>
+__device__ __forceinline__ void dftR<8, 1, float2>(float2 (&a)[8]) { dft8<1>(a); }
+template <>
+__device__ __forceinline__ void dftR<8, -1, double2>(double2 (&a)[8]) { dft8<-1>(a); }
+template <>
+__device__ __forceinline__ void dftR<8, 1, double2>(double2 (&a)[8]) { dft8<1>(a); }
+
+// Twiddle exp(DIR 2 pi i k / L) from the table tw[j] = exp(-2 pi i j / L_table),
+// read at j = k * TS (TS = L_table / L).
+template <int DIR, typename C>
+__device__ __forceinline__ C twiddle(const C *__restrict__ tw, int j) {
+  const C w = __ldg(tw + j);
+  return DIR < 0 ? w : cconj(w);
+}
+
+// Shared-memory views used for the exchanges between stages.
+//   column tile [n][pitch], this thread's column at base
+template <typename C>
+struct SmCol {
+  C *base;
+  int pitch;
+  __device__ __forceinline__ C ld(int n) const { return base[n * pitch]; }
+  __device__ __forceinline__ void st(int n, C v) const { base[n * pitch] = v; }
+};
+//   contiguous line with one pad slot every 8 entries (bank-conflict free
+//   stride-8 writes of the first radix-8 stage)
+template <typename C>
+struct SmLine {
+  C *base;
+  __device__ __forceinline__ C ld(int n) const { return base[n + (n >> 3)]; }
+  __device__ __forceinline__ void st(int n, C v) const { base[n + (n >> 3)] = v; }
+};
+__host__ __device__ constexpr int smline_len(int L) { return L + L / 8; }
+
+// One radix-R stage of span NS on a line of length L (see file header).
+template <int L, int R, int NS, int DIR, int TS, bool LAST, typename C, typename SM>
+__device__ __forceinline__ void fft_stage(C (&v)[8], int t, const C *__restrict__ tw, const SM &sm) {
+  constexpr int T = L / 8;
+  constexpr int Q = 8 / R;
+#pragma unroll
+  for (int q = 0; q < Q; ++q) {
+    const int b = t + T * q;
+    C a[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) a[r] = v[q + r * Q];
+    if (NS > 1) {
+      const int e = (b % NS) * (L / (NS * R));
+#pragma unroll
+      for (int r = 1; r < R; ++r) a[r] = cmul(a[r], twiddle<DIR>(tw, r * e * TS));
+    }
+    dftR<R, DIR>(a);
+    if (LAST) {
+#pragma unroll
+      for (int r = 0; r < R; ++r) v[q + r * Q] = a[r];
+    } else {
+      const int base = (b / NS) * NS * R + (b % NS);
+#pragma unroll
+      for (int r = 0; r < R; ++r) sm.st(base + r * NS, a[r]);
+    }
+  }
+}
+
+template <int L, int S>
+struct StagePlan {
+  static constexpr int LOG = ilog2(L);
+  static constexpr int R0 = 1 << (LOG % 3);
+  static constexpr int NST = LOG / 3 + (R0 > 1 ? 1 : 0);
+  static constexpr int RADIX = (S == 0 && R0 > 1) ? R0 : 8;
+  // span before stage S = product of the radices of stages < S
+  static constexpr int NS = S == 0 ? 1 : (R0 > 1 ? R0 * (1 << (3 * (S - 1))) : (1 << (3 * S)));
+};
+
+template <int L, int S, int DIR, int TS, typename C, typename SM>
+struct FftRun {
+  __device__ __forceinline__ static void run(C (&v)[8], int t, const C *__restrict__ tw, const SM &sm) {
+    using P = StagePlan<L, S>;
+    constexpr int T = L / 8;
+    if (S > 0) {
+      __syncthreads();  // the previous stage's shared writes are visible
+#pragma unroll
+      for (int m = 0; m < 8; ++m) v[m] = sm.ld(t + T * m);
+      if (S < P::NST - 1) __syncthreads();  // everyone read before the next writes
+    }
+    fft_stage<L, P::RADIX, P::NS, DIR, TS, S == P::NST - 1>(v, t, tw, sm);
+    FftRun<L, S + 1, DIR, TS, C, SM>::next(v, t, tw, sm);
+  }
+  __device__ __forceinline__ static void next(C (&v)[8], int t, const C *__restrict__ tw, const SM &sm) {
+    if constexpr (S < StagePlan<L, 0>::NST) FftRun<L, S, DIR, TS, C, SM>::run(v, t, tw, sm);
+  }
+};
+
+// Length-L FFT of one line held as v[m] = x[t + T m] (T = L/8) by threads
+// t = 0..T-1.  Every thread of the block must call it (it synchronises the
+// block); sm is this thread's view of a scratch line of at least L entries.
+// On return v[m] = X[t + T m], X_k = sum_j x_j exp(DIR 2 pi i j k / L).
+// Twiddles come from tw[j] = exp(-2 pi i j / (L TS)).
+template <int L, int DIR, int TS, typename C, typename SM>
+__device__ __forceinline__ void fft_line(C (&v)[8], int t, const C *__restrict__ tw, const SM &sm) {
+  static_assert(L >= 8 && (L & (L - 1)) == 0, "power of two >= 8");
+  if (StagePlan<L, 0>::NST > 1) __syncthreads();  // the scratch line is free
+  FftRun<L, 0, DIR, TS, C, SM>::run(v, t, tw, sm);
+}
+
+}  // namespace nsk

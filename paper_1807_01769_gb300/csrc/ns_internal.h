@@ -1,0 +1,73 @@
+// ns_internal.h -- host-side contract between the runtime (ns_api.cu) and the
+// translation units that instantiate the pass kernels.  Not part of the ABI.
+#pragma once
+#include <cuda_runtime.h>
+
+namespace nsk {
+
+// Grid geometry and device layouts (element = one complex of the state precision).
+//  3D state / acc / forcing : [3][c][c][hs]        (comp, kz, ky, kx)
+//  3D zb  (first-axis pass)  : [6][N][c][hs]        (field, z, ky, kx)
+//  3D yb  (middle-axis pass) : [6][N][N][hs]        (field, z, y, kx)
+//  2D state / acc / forcing : [c][hs]              (ky, kx)
+//  2D yb                    : [4][N][hs]           (field, y, kx)
+// hs = h rounded up to 128 bytes of complex; columns h..hs-1 are never read
+// as data and never written by the pass kernels.
+struct Geo {
+  int dim, N, kc, c, h, hs;
+  long long st_comp;  // elements per state component
+  long long zb_f;     // elements per zb field (3D)
+  long long yb_f;     // elements per yb field
+};
+
+enum Op {
+  OP_PREPARE = 0,   // set kernel attributes once (no launch)
+  OP_INV1 = 1,      // first inverse axis (3D: z, with curl or plain; 2D: y, velocity/gradient or plain)
+  OP_INV2 = 2,      // 3D middle axis inverse (y)
+  OP_XPASS = 3,     // c2r of every field, nonlinear product, r2c, dealias in x
+  OP_FWD2 = 4,      // 3D middle axis forward (y), dealias in y
+  OP_FWD1 = 5,      // last forward axis, dealias, normalise, project, forcing, RK stage, (opt.) next inverse
+  OP_XFWD_REAL = 6, // real lines (FP64 staging) -> half spectrum in x
+  OP_XINV_REAL = 7, // half spectrum in x -> real lines (FP64 staging)
+};
+
+enum Mode { MODE_RK1 = 1, MODE_RK2 = 2, MODE_RK3 = 3, MODE_RK4 = 4, MODE_RHS = 5, MODE_PROJ = 6 };
+
+struct Args {
+  Geo g;
+  const void *tw;  // length-N table exp(-2 pi i j / N), state precision
+  const void *ef;  // exp(-nu m dt),   m = |k|^2 = 0 .. dim kc^2
+  const void *ef2; // exp(-nu m dt/2)
+  void *u, *acc;
+  const void *F;   // forcing (nullable)
+  void *zb, *yb;
+  const void *src; // OP_INV1 input (state-shaped)
+  void *dst;       // OP_FWD1 output for MODE_RHS / MODE_PROJ
+  const double *phys_in;
+  double *phys_out;
+  int field;   // OP_XFWD_REAL / OP_XINV_REAL: yb field
+  int nf;      // OP_INV2 / OP_FWD2: number of fields; OP_INV1: 1 = plain copy of field 0..., see kernels
+  int curl;    // OP_INV1: 1 = curl / velocity form, 0 = plain transform of every state component
+  int mode;    // OP_FWD1
+  int inv;     // OP_FWD1: 1 = fuse the next stage's first inverse axis
+  double dt;
+};
+
+// Launch op for the given precision; returns a cudaError_t value (0 = ok) or
+// -1 if N is not instantiated.
+int dispatch3_f32(int op, const Args &a, cudaStream_t s);
+int dispatch3_f64(int op, const Args &a, cudaStream_t s);
+int dispatch2_f32(int op, const Args &a, cudaStream_t s);
+int dispatch2_f64(int op, const Args &a, cudaStream_t s);
+
+// Auxiliary kernels (ns_aux.cu).
+int spec_in(int prec, void *dst, const double *src, long long rows, int h, int hs, cudaStream_t s);
+int spec_out(int prec, double *dst, const void *src, long long rows, int h, int hs, cudaStream_t s);
+// FP64 diagnostics: partial sums into scratch, then energy, enstrophy and the
+// shell spectrum into out[0], out[1], out[2 ..].  scratch must hold
+// diag_scratch_doubles(g, nbins) doubles.
+long long diag_blocks(const Geo &g);
+long long diag_scratch_doubles(const Geo &g, int nbins);
+int diagnostics(int prec, const Geo &g, const void *u, int nbins, double *scratch, double *out, cudaStream_t s);
+
+}  // namespace nsk

@@ -1,0 +1,795 @@
+// ns_kernels.cuh -- the pass kernels of the right-hand side and time step.
+//
+// One RK stage of the 3D solver is four launches (all names refer to the
+// axis transformed):
+//   inv2   (y)  : 6 fields, ky -> y, zero-padded from the c retained rows
+//   xpass  (x)  : per (z, y) line: 6 c2r, n = u x omega, 3 r2c, keep kx <= kc
+//   fwd2   (y)  : 3 fields, y -> ky, keep the c retained rows
+//   fwd1   (z)  : 3 fields, z -> kz, keep retained rows, divide by N^3,
+//                 project, add forcing, RK stage update, then (fused) the
+//                 curl and z -> kz inverse of the next stage input (6 fields)
+// and the first inverse axis of a call (inv1: curl + z inverse from the state)
+// runs once per ns_step call.  The 2D solver is two launches per stage: xpass
+// (4 c2r, n = -(u . grad w), 1 r2c) and fwd1 (y forward, dealias, RK, then
+// velocity / vorticity-gradient forms and y inverse of the next stage).
+//
+// Physical fields never touch global memory: they exist only in registers
+// inside xpass, packed two real points per complex number (z[m] = x[2m] +
+// i x[2m+1]) so the c2r and r2c of length N are complex FFTs of length N/2 with
+// a pre/post-processing step, and the pointwise product acts on the packed
+// pairs directly.  The operators follow the FluidSim paper's list ("The
+// simulation object": FFT, IFFT, dealiasing, divergence, curl; "Tri-dimensional
+// simulations": FFT, RK4, curl, vector product, projection).
+#pragma once
+#include "ns_fft.cuh"
+#include "ns_internal.h"
+
+namespace nsk {
+
+template <typename R>
+__host__ __device__ constexpr int wmax() {
+  return sizeof(R) == 4 ? 16 : 8;  // 128 bytes of complex per tile row
+}
+__host__ __device__ constexpr int cmin(int a, int b) { return a < b ? a : b; }
+__host__ __device__ constexpr int cmax(int a, int b) { return a > b ? a : b; }
+// columns per tile: light kernels (one field live per thread) and the fused
+// fwd1 (three fields live per thread)
+template <typename R, int N>
+__host__ __device__ constexpr int w_light() {
+  return cmin(wmax<R>(), cmax(1, 1024 / (N / 8)));
+}
+template <typename R, int N>
+__host__ __device__ constexpr int w_heavy() {
+  return cmin(wmax<R>(), cmax(1, (sizeof(R) == 4 ? 512 : 256) / (N / 8)));
+}
+// lines per block of the x kernels (N/16 threads per line)
+template <typename R, int N>
+__host__ __device__ constexpr int x_lines() {
+  return cmin(N, cmax(1, (sizeof(R) == 4 ? 256 : 128) / (N / 16)));
+}
+__host__ __device__ constexpr int pitch_of(int W, int csize) { return (W * csize < 128) ? W + 1 : W; }
+
+template <typename C>
+__device__ __forceinline__ C *dyn_smem() {
+  extern __shared__ __align__(16) unsigned char ns_dyn_smem[];
+  return reinterpret_cast<C *>(ns_dyn_smem);
+}
+
+__device__ __forceinline__ bool retained(int n, int N, int kc) { return n <= kc || n >= N - kc; }
+__device__ __forceinline__ int compact_of(int n, int N, int kc, int c) { return n <= kc ? n : n - (N - c); }
+__device__ __forceinline__ int kfull_of(int n, int N, int kc) { return n <= kc ? n : n - N; }
+__device__ __forceinline__ int ktr_of(int i, int kc, int c) { return i <= kc ? i : i - c; }
+
+// componentwise product of packed real pairs
+template <typename C>
+__device__ __forceinline__ C pmul(C a, C b) {
+  return C{a.x * b.x, a.y * b.y};
+}
+template <typename C>
+__device__ __forceinline__ C pfma(C a, C b, C acc) {
+  return C{fma(a.x, b.x, acc.x), fma(a.y, b.y, acc.y)};
+}
+template <typename C>
+__device__ __forceinline__ C pfms(C a, C b, C acc) {  // acc - a*b
+  return C{fma(-a.x, b.x, acc.x), fma(-a.y, b.y, acc.y)};
+}
+
+// ----------------------------------------------- x-line helper routines ---
+// Stage the half spectrum X[0..h-1] of L lines (row stride hs) into shared
+// lines of length H (zero above h).
+template <typename C, int H, int L>
+__device__ __forceinline__ void stage_lines(C *S, const C *__restrict__ src, long long line0, int h, int hs) {
+  constexpr int SL = smline_len(H);
+  for (int idx = threadIdx.x; idx < L * H; idx += blockDim.x) {
+    const int ll = idx / H, k = idx % H;
+    S[ll * SL + k + (k >> 3)] = k < h ? src[(line0 + ll) * hs + k] : czero<C>();
+  }
+}
+
+// c2r pre-processing: Z[k] = (X[k] + conj X[H-k]) + i e^{+2 pi i k/N} (X[k] - conj X[H-k]),
+// X[H] = 0 (never retained), imaginary part of X[0] dropped (real part of the
+// self-conjugate term, as the inverse c2r of a Hermitian spectrum).
+template <typename C, int N>
+__device__ __forceinline__ C c2r_pre(const C *Sl, int k, const C *__restrict__ tw) {
+  constexpr int H = N / 2;
+  C xk = Sl[k + (k >> 3)];
+  C xm;
+  if (k == 0) {
+    xk.y = 0;
+    xm = czero<C>();
+  } else {
+    const int j = H - k;
+    xm = Sl[j + (j >> 3)];
+  }
+  const C a = cadd(xk, cconj(xm));
+  const C b = csub(xk, cconj(xm));
+  const C e = cconj(__ldg(tw + k));
+  return cadd(a, cmuli(cmul(e, b)));
+}
+
+// r2c post-processing: X[k] = (Z[k] + conj Z[H-k])/2 - i/2 e^{-2 pi i k/N} (Z[k] - conj Z[H-k]).
+template <typename C, int N>
+__device__ __forceinline__ C r2c_post(const C *Sl, int k, const C *__restrict__ tw) {
+  constexpr int H = N / 2;
+  using R = decltype(C{}.x);
+  const int j = (H - k) & (H - 1);
+  const C zk = Sl[k + (k >> 3)], zm = Sl[j + (j >> 3)];
+  const C a = cadd(zk, cconj(zm));
+  const C b = csub(zk, cconj(zm));
+  const C e = __ldg(tw + k);
+  const C r = csub(a, cmuli(cmul(e, b)));
+  return C{(R)0.5 * r.x, (R)0.5 * r.y};
+}
+
+// Write the forward-transformed line (v[m] = Z[t + TX m]) to shared memory and
+// emit X[0..h-1] of all L lines to dst (row stride hs), coalesced.
+template <typename C, int N, int L>
+__device__ __forceinline__ void emit_r2c(C (&v)[8], int t, int l, C *S, C *__restrict__ dst, long long line0, int h,
+                                         int hs, const C *__restrict__ tw) {
+  constexpr int H = N / 2, TX = H / 8, SL = smline_len(H);
+  __syncthreads();  // last FFT stage finished reading S
+#pragma unroll
+  for (int m = 0; m < 8; ++m) {
+    const int k = t + TX * m;
+    S[l * SL + k + (k >> 3)] = v[m];
+  }
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < L * h; idx += blockDim.x) {
+    const int ll = idx / h, k = idx % h;
+    dst[(line0 + ll) * hs + k] = r2c_post<C, N>(S + ll * SL, k, tw);
+  }
+}
+
+// ================================================================== 3D ====
+// inv1: z inverse from a state-shaped array.  CURL: six fields (u, i k x u);
+// otherwise three fields (u).  One block = a tile of W kx columns at one ky.
+template <typename R, int N, int W, bool CURL>
+__global__ void __launch_bounds__((N / 8) * W) k3_inv1(Geo g, const typename CplxOf<R>::T *__restrict__ src,
+                                                        typename CplxOf<R>::T *__restrict__ zb,
+                                                        const typename CplxOf<R>::T *__restrict__ tw) {
+  using C = typename CplxOf<R>::T;
+  constexpr int T = N / 8;
+  constexpr int P = pitch_of(W, sizeof(C));
+  C *sm = dyn_smem<C>();
+  const int w = threadIdx.x % W, t = threadIdx.x / W;
+  const int nkt = g.hs / W;
+  const int iy = blockIdx.x / nkt;
+  const int kx = (blockIdx.x % nkt) * W + w;
+  const bool valid = kx < g.h;
+  const R kxr = (R)kx, kyr = (R)ktr_of(iy, g.kc, g.c);
+  const long long plane = (long long)g.c * g.hs;
+  const long long col = (long long)iy * g.hs + kx;
+  const SmCol<C> view{sm + w, P};
+  const long long st = g.st_comp;
+  constexpr int NF = CURL ? 6 : 3;
+  for (int f = 0; f < NF; ++f) {
+    C v[8];
+#pragma unroll
+    for (int m = 0; m < 8; ++m) {
+      const int n = t + T * m;
+      C x = czero<C>();
+      if (valid && retained(n, N, g.kc)) {
+        const long long idx = (long long)compact_of(n, N, g.kc, g.c) * plane + col;
+        if (!CURL || f < 3) {
+          x = src[f * st + idx];
+        } else {
+          const R kzr = (R)kfull_of(n, N, g.kc);
+          C a, b;
+          R ka, kb;
+          if (f == 3) {  // i (ky uz - kz uy)
+            a = src[2 * st + idx];
+            b = src[st + idx];
+            ka = kyr;
+            kb = kzr;
+          } else if (f == 4) {  // i (kz ux - kx uz)
+            a = src[idx];
+            b = src[2 * st + idx];
+            ka = kzr;
+            kb = kxr;
+          } else {  // i (kx uy - ky ux)
+            a = src[st + idx];
+            b = src[idx];
+            ka = kxr;
+            kb = kyr;
+          }
+          x = cmuli(C{ka * a.x - kb * b.x, ka * a.y - kb * b.y});
+        }
+      }
+      v[m] = x;
+    }
+    fft_line<N, +1, 1>(v, t, tw, view);
+    if (valid) {
+#pragma unroll
+      for (int m = 0; m < 8; ++m) zb[f * g.zb_f + (long long)(t + T * m) * plane + col] = v[m];
+    }
+  }
+}
+
+// inv2: y inverse of field blockIdx.z at plane z = blockIdx.y.
+template <typename R, int N, int W>
+__global__ void __launch_bounds__((N / 8) * W) k3_inv2(Geo g, const typename CplxOf<R>::T *__restrict__ zb,
+                                                        typename CplxOf<R>::T *__restrict__ yb,
+                                                        const typename CplxOf<R>::T *__restrict__ tw) {
+  using C = typename CplxOf<R>::T;
+  constexpr int T = N / 8;
+  constexpr int P = pitch_of(W, sizeof(C));
+  C *sm = dyn_smem<C>();
+  const int w = threadIdx.x % W, t = threadIdx.x / W;
+  const int kx = blockIdx.x * W + w;
+  const bool valid = kx < g.h;
+  const int z = blockIdx.y, f = blockIdx.z;
+  const C *in = zb + f * g.zb_f + (long long)z * g.c * g.hs + kx;
+  C *out = yb + f * g.yb_f + (long long)z * N * g.hs + kx;
+  C v[8];
+#pragma unroll
+  for (int m = 0; m < 8; ++m) {
+    const int n = t + T * m;
+    v[m] = (valid && retained(n, N, g.kc)) ? in[(long long)compact_of(n, N, g.kc, g.c) * g.hs] : czero<C>();
+  }
+  fft_line<N, +1, 1>(v, t, tw, SmCol<C>{sm + w, P});
+  if (valid) {
+#pragma unroll
+    for (int m = 0; m < 8; ++m) out[(long long)(t + T * m) * g.hs] = v[m];
+  }
+}
+
+// xpass (3D): lines (z, y); fields u_x, u_y, u_z, w_x, w_y, w_z in, n = u x w out
+// (written over fields 0..2 of the same lines).
+template <typename R, int N, int L>
+__global__ void __launch_bounds__((N / 16) * L) k3_xpass(Geo g, typename CplxOf<R>::T *__restrict__ yb,
+                                                          const typename CplxOf<R>::T *__restrict__ tw) {
+  using C = typename CplxOf<R>::T;
+  constexpr int H = N / 2, TX = H / 8, SL = smline_len(H);
+  C *S = dyn_smem<C>();
+  const int t = threadIdx.x % TX, l = threadIdx.x / TX;
+  const long long line0 = (long long)blockIdx.x * L;
+  const SmLine<C> view{S + l * SL};
+  C ux[8], uy[8], uz[8], nx[8], ny[8], nz[8];
+  for (int f = 0; f < 6; ++f) {
+    __syncthreads();
+    stage_lines<C, H, L>(S, yb + f * g.yb_f, line0, g.h, g.hs);
+    __syncthreads();
+    C v[8];
+#pragma unroll
+    for (int m = 0; m < 8; ++m) v[m] = c2r_pre<C, N>(S + l * SL, t + TX * m, tw);
+    fft_line<H, +1, 2>(v, t, tw, view);
+#pragma unroll
+    for (int m = 0; m < 8; ++m) {
+      switch (f) {
+        case 0: ux[m] = v[m]; break;
+        case 1: uy[m] = v[m]; break;
+        case 2: uz[m] = v[m]; break;
+        case 3:  // w_x:  n_y = u_z w_x,  n_z = -u_y w_x
+          ny[m] = pmul(uz[m], v[m]);
+          nz[m] = pmul(C{-uy[m].x, -uy[m].y}, v[m]);
+          break;
+        case 4:  // w_y:  n_x = -u_z w_y, n_z += u_x w_y
+          nx[m] = pmul(C{-uz[m].x, -uz[m].y}, v[m]);
+          nz[m] = pfma(ux[m], v[m], nz[m]);
+          break;
+        default:  // w_z: n_x += u_y w_z, n_y -= u_x w_z
+          nx[m] = pfma(uy[m], v[m], nx[m]);
+          ny[m] = pfms(ux[m], v[m], ny[m]);
+          break;
+      }
+    }
+  }
+  for (int gg = 0; gg < 3; ++gg) {
+    C v[8];
+#pragma unroll
+    for (int m = 0; m < 8; ++m) v[m] = gg == 0 ? nx[m] : (gg == 1 ? ny[m] : nz[m]);
+    fft_line<H, -1, 2>(v, t, tw, view);
+    emit_r2c<C, N, L>(v, t, l, S, yb + gg * g.yb_f, line0, g.h, g.hs, tw);
+  }
+}
+
+// fwd2: y forward of field blockIdx.z at plane z = blockIdx.y, keep retained ky.
+template <typename R, int N, int W>
+__global__ void __launch_bounds__((N / 8) * W) k3_fwd2(Geo g, const typename CplxOf<R>::T *__restrict__ yb,
+                                                        typename CplxOf<R>::T *__restrict__ zb,
+                                                        const typename CplxOf<R>::T *__restrict__ tw) {
+  using C = typename CplxOf<R>::T;
+  constexpr int T = N / 8;
+  constexpr int P = pitch_of(W, sizeof(C));
+  C *sm = dyn_smem<C>();
+  const int w = threadIdx.x % W, t = threadIdx.x / W;
+  const int kx = blockIdx.x * W + w;
+  const bool valid = kx < g.h;
+  const int z = blockIdx.y, f = blockIdx.z;
+  const C *in = yb + f * g.yb_f + (long long)z * N * g.hs + kx;
+  C *out = zb + f * g.zb_f + (long long)z * g.c * g.hs + kx;
+  C v[8];
+#pragma unroll
+  for (int m = 0; m < 8; ++m) v[m] = valid ? in[(long long)(t + T * m) * g.hs] : czero<C>();
+  fft_line<N, -1, 1>(v, t, tw, SmCol<C>{sm + w, P});
+  if (valid) {
+#pragma unroll
+    for (int m = 0; m < 8; ++m) {
+      const int n = t + T * m;
+      if (retained(n, N, g.kc)) out[(long long)compact_of(n, N, g.kc, g.c) * g.hs] = v[m];
+    }
+  }
+}
+
+template <typename R>
+struct StepBufs {
+  using C = typename CplxOf<R>::T;
+  const C *tw;
+  const R *ef, *ef2;
+  C *u, *acc;
+  const C *F;
+  C *zb;
+  C *yb;
+  C *dst;
+  R dt;
+};
+
+// Lawson IF-RK4 stage update for one mode (see ns.h); returns the next stage input.
+template <int MODE, typename C, typename R>
+__device__ __forceinline__ C rk_update(C nv, long long idx, int k2, const StepBufs<R> &b) {
+  if (MODE == MODE_RK1) {
+    const C uu = b.u[idx];
+    const R e = __ldg(b.ef + k2), e2 = __ldg(b.ef2 + k2);
+    const R c1 = b.dt * e / (R)6;
+    b.acc[idx] = C{e * uu.x + c1 * nv.x, e * uu.y + c1 * nv.y};
+    const R h = b.dt / (R)2;
+    return C{e2 * (uu.x + h * nv.x), e2 * (uu.y + h * nv.y)};
+  } else if (MODE == MODE_RK2) {
+    const C uu = b.u[idx], a = b.acc[idx];
+    const R e2 = __ldg(b.ef2 + k2);
+    const R c2 = b.dt * e2 / (R)3;
+    b.acc[idx] = C{a.x + c2 * nv.x, a.y + c2 * nv.y};
+    const R h = b.dt / (R)2;
+    return C{e2 * uu.x + h * nv.x, e2 * uu.y + h * nv.y};
+  } else if (MODE == MODE_RK3) {
+    const C uu = b.u[idx], a = b.acc[idx];
+    const R e = __ldg(b.ef + k2), e2 = __ldg(b.ef2 + k2);
+    const R c2 = b.dt * e2 / (R)3;
+    b.acc[idx] = C{a.x + c2 * nv.x, a.y + c2 * nv.y};
+    const R c3 = b.dt * e2;
+    return C{e * uu.x + c3 * nv.x, e * uu.y + c3 * nv.y};
+  } else if (MODE == MODE_RK4) {
+    const C a = b.acc[idx];
+    const R c4 = b.dt / (R)6;
+    const C un = C{a.x + c4 * nv.x, a.y + c4 * nv.y};
+    b.u[idx] = un;
+    return un;
+  } else {  // MODE_RHS, MODE_PROJ: write the term itself
+    b.dst[idx] = nv;
+    return czero<C>();
+  }
+}
+
+// fwd1 (3D): z forward of the three product fields, dealias, 1/N^3, projection,
+// forcing, RK stage; INV: curl + z inverse of the next stage input into zb.
+template <typename R, int N, int W, int MODE, bool INV>
+__global__ void __launch_bounds__((N / 8) * W) k3_fwd1(Geo g, StepBufs<R> b) {
+  using C = typename CplxOf<R>::T;
+  constexpr int T = N / 8;
+  constexpr int P = pitch_of(W, sizeof(C));
+  C *sm = dyn_smem<C>();
+  const int w = threadIdx.x % W, t = threadIdx.x / W;
+  const int nkt = g.hs / W;
+  const int iy = blockIdx.x / nkt;
+  const int kx = (blockIdx.x % nkt) * W + w;
+  const bool valid = kx < g.h;
+  const int ky = ktr_of(iy, g.kc, g.c);
+  const R kxr = (R)kx, kyr = (R)ky;
+  const long long plane = (long long)g.c * g.hs;
+  const long long col = (long long)iy * g.hs + kx;
+  const long long st = g.st_comp;
+  const SmCol<C> view{sm + w, P};
+  const R scale = (R)1 / ((R)N * (R)N * (R)N);
+  C s0[8], s1[8], s2[8];
+  for (int gg = 0; gg < 3; ++gg) {
+    C v[8];
+#pragma unroll
+    for (int m = 0; m < 8; ++m) v[m] = valid ? b.zb[gg * g.zb_f + (long long)(t + T * m) * plane + col] : czero<C>();
+    fft_line<N, -1, 1>(v, t, b.tw, view);
+#pragma unroll
+    for (int m = 0; m < 8; ++m) {
+      if (gg == 0) s0[m] = v[m];
+      else if (gg == 1) s1[m] = v[m];
+      else s2[m] = v[m];
+    }
+  }
+#pragma unroll
+  for (int m = 0; m < 8; ++m) {
+    const int n = t + T * m;
+    if (!valid || !retained(n, N, g.kc)) {
+      s0[m] = s1[m] = s2[m] = czero<C>();
+      continue;
+    }
+    const int kz = kfull_of(n, N, g.kc);
+    const R kzr = (R)kz;
+    const int k2 = kx * kx + ky * ky + kz * kz;
+    C ax = cscale(s0[m], scale), ay = cscale(s1[m], scale), az = cscale(s2[m], scale);
+    if (k2 == 0) {
+      ax = ay = az = czero<C>();
+    } else {
+      const R inv = (R)1 / (R)k2;
+      const C kd = C{(kxr * ax.x + kyr * ay.x + kzr * az.x) * inv, (kxr * ax.y + kyr * ay.y + kzr * az.y) * inv};
+      ax = C{ax.x - kxr * kd.x, ax.y - kxr * kd.y};
+      ay = C{ay.x - kyr * kd.x, ay.y - kyr * kd.y};
+      az = C{az.x - kzr * kd.x, az.y - kzr * kd.y};
+    }
+    const long long idx = (long long)compact_of(n, N, g.kc, g.c) * plane + col;
+    if (MODE != MODE_PROJ && b.F != nullptr) {
+      ax = cadd(ax, b.F[idx]);
+      ay = cadd(ay, b.F[st + idx]);
+      az = cadd(az, b.F[2 * st + idx]);
+    }
+    StepBufs<R> b1 = b;
+    b1.u += st;
+    b1.acc += st;
+    b1.dst += st;
+    StepBufs<R> b2 = b1;
+    b2.u += st;
+    b2.acc += st;
+    b2.dst += st;
+    s0[m] = rk_update<MODE>(ax, idx, k2, b);
+    s1[m] = rk_update<MODE>(ay, idx, k2, b1);
+    s2[m] = rk_update<MODE>(az, idx, k2, b2);
+  }
+  if (INV) {
+    for (int f = 0; f < 6; ++f) {
+      C v[8];
+#pragma unroll
+      for (int m = 0; m < 8; ++m) {
+        const R kzr = (R)kfull_of(t + T * m, N, g.kc);
+        if (f == 0) v[m] = s0[m];
+        else if (f == 1) v[m] = s1[m];
+        else if (f == 2) v[m] = s2[m];
+        else if (f == 3) v[m] = cmuli(C{kyr * s2[m].x - kzr * s1[m].x, kyr * s2[m].y - kzr * s1[m].y});
+        else if (f == 4) v[m] = cmuli(C{kzr * s0[m].x - kxr * s2[m].x, kzr * s0[m].y - kxr * s2[m].y});
+        else v[m] = cmuli(C{kxr * s1[m].x - kyr * s0[m].x, kxr * s1[m].y - kyr * s0[m].y});
+      }
+      fft_line<N, +1, 1>(v, t, b.tw, view);
+      if (valid) {
+#pragma unroll
+        for (int m = 0; m < 8; ++m) b.zb[f * g.zb_f + (long long)(t + T * m) * plane + col] = v[m];
+      }
+    }
+  }
+}
+
+// ================================================================== 2D ====
+// inv1 (2D): y inverse from a state-shaped array.  VEL: four fields
+// u_x = i ky psi, u_y = -i kx psi, d_x w = i kx w, d_y w = i ky w with
+// psi = w/|k|^2; otherwise one field (w itself).
+template <typename R, int N, int W, bool VEL>
+__global__ void __launch_bounds__((N / 8) * W) k2_inv1(Geo g, const typename CplxOf<R>::T *__restrict__ src,
+                                                        typename CplxOf<R>::T *__restrict__ yb,
+                                                        const typename CplxOf<R>::T *__restrict__ tw) {
+  using C = typename CplxOf<R>::T;
+  constexpr int T = N / 8;
+  constexpr int P = pitch_of(W, sizeof(C));
+  C *sm = dyn_smem<C>();
+  const int w = threadIdx.x % W, t = threadIdx.x / W;
+  const int kx = blockIdx.x * W + w;
+  const bool valid = kx < g.h;
+  const SmCol<C> view{sm + w, P};
+  C wv[8];
+#pragma unroll
+  for (int m = 0; m < 8; ++m) {
+    const int n = t + T * m;
+    wv[m] = (valid && retained(n, N, g.kc)) ? src[(long long)compact_of(n, N, g.kc, g.c) * g.hs + kx] : czero<C>();
+  }
+  constexpr int NF = VEL ? 4 : 1;
+  for (int f = 0; f < NF; ++f) {
+    C v[8];
+#pragma unroll
+    for (int m = 0; m < 8; ++m) {
+      if (!VEL) {
+        v[m] = wv[m];
+        continue;
+      }
+      const int ky = kfull_of(t + T * m, N, g.kc);
+      const int k2 = kx * kx + ky * ky;
+      const R kxr = (R)kx, kyr = (R)ky;
+      const R ip = k2 > 0 ? (R)1 / (R)k2 : (R)0;
+      if (f == 0) v[m] = cmuli(cscale(wv[m], kyr * ip));
+      else if (f == 1) v[m] = cmuli(cscale(wv[m], -kxr * ip));
+      else if (f == 2) v[m] = cmuli(cscale(wv[m], kxr));
+      else v[m] = cmuli(cscale(wv[m], kyr));
+    }
+    fft_line<N, +1, 1>(v, t, tw, view);
+    if (valid) {
+#pragma unroll
+      for (int m = 0; m < 8; ++m) yb[f * g.yb_f + (long long)(t + T * m) * g.hs + kx] = v[m];
+    }
+  }
+}
+
+// xpass (2D): lines y; fields u_x, u_y, d_x w, d_y w in; n = -(u . grad w)
+// out (field 0).
+template <typename R, int N, int L>
+__global__ void __launch_bounds__((N / 16) * L) k2_xpass(Geo g, typename CplxOf<R>::T *__restrict__ yb,
+                                                          const typename CplxOf<R>::T *__restrict__ tw) {
+  using C = typename CplxOf<R>::T;
+  constexpr int H = N / 2, TX = H / 8, SL = smline_len(H);
+  C *S = dyn_smem<C>();
+  const int t = threadIdx.x % TX, l = threadIdx.x / TX;
+  const long long line0 = (long long)blockIdx.x * L;
+  const SmLine<C> view{S + l * SL};
+  C ux[8], uy[8], nn[8];
+  for (int f = 0; f < 4; ++f) {
+    __syncthreads();
+    stage_lines<C, H, L>(S, yb + f * g.yb_f, line0, g.h, g.hs);
+    __syncthreads();
+    C v[8];
+#pragma unroll
+    for (int m = 0; m < 8; ++m) v[m] = c2r_pre<C, N>(S + l * SL, t + TX * m, tw);
+    fft_line<H, +1, 2>(v, t, tw, view);
+#pragma unroll
+    for (int m = 0; m < 8; ++m) {
+      if (f == 0) ux[m] = v[m];
+      else if (f == 1) uy[m] = v[m];
+      else if (f == 2) nn[m] = pmul(C{-ux[m].x, -ux[m].y}, v[m]);
+      else nn[m] = pfms(uy[m], v[m], nn[m]);
+    }
+  }
+  fft_line<H, -1, 2>(nn, t, tw, view);
+  emit_r2c<C, N, L>(nn, t, l, S, yb, line0, g.h, g.hs, tw);
+}
+
+// fwd1 (2D): y forward of field 0, dealias, 1/N^2, forcing, RK stage; INV:
+// the four inverse fields of the next stage input.
+template <typename R, int N, int W, int MODE, bool INV>
+__global__ void __launch_bounds__((N / 8) * W) k2_fwd1(Geo g, StepBufs<R> b) {
+  using C = typename CplxOf<R>::T;
+  constexpr int T = N / 8;
+  constexpr int P = pitch_of(W, sizeof(C));
+  C *sm = dyn_smem<C>();
+  const int w = threadIdx.x % W, t = threadIdx.x / W;
+  const int kx = blockIdx.x * W + w;
+  const bool valid = kx < g.h;
+  const SmCol<C> view{sm + w, P};
+  const R scale = (R)1 / ((R)N * (R)N);
+  C s[8];
+#pragma unroll
+  for (int m = 0; m < 8; ++m) s[m] = valid ? b.yb[(long long)(t + T * m) * g.hs + kx] : czero<C>();
+  fft_line<N, -1, 1>(s, t, b.tw, view);
+#pragma unroll
+  for (int m = 0; m < 8; ++m) {
+    const int n = t + T * m;
+    if (!valid || !retained(n, N, g.kc)) {
+      s[m] = czero<C>();
+      continue;
+    }
+    const int ky = kfull_of(n, N, g.kc);
+    const int k2 = kx * kx + ky * ky;
+    C nv = k2 == 0 ? czero<C>() : cscale(s[m], scale);
+    const long long idx = (long long)compact_of(n, N, g.kc, g.c) * g.hs + kx;
+    if (MODE != MODE_PROJ && b.F != nullptr) nv = cadd(nv, b.F[idx]);
+    s[m] = rk_update<MODE>(nv, idx, k2, b);
+  }
+  if (INV) {
+    for (int f = 0; f < 4; ++f) {
+      C v[8];
+#pragma unroll
+      for (int m = 0; m < 8; ++m) {
+        const int ky = kfull_of(t + T * m, N, g.kc);
+        const int k2 = kx * kx + ky * ky;
+        const R kxr = (R)kx, kyr = (R)ky;
+        const R ip = k2 > 0 ? (R)1 / (R)k2 : (R)0;
+        if (f == 0) v[m] = cmuli(cscale(s[m], kyr * ip));
+        else if (f == 1) v[m] = cmuli(cscale(s[m], -kxr * ip));
+        else if (f == 2) v[m] = cmuli(cscale(s[m], kxr));
+        else v[m] = cmuli(cscale(s[m], kyr));
+      }
+      fft_line<N, +1, 1>(v, t, b.tw, view);
+      if (valid) {
+#pragma unroll
+        for (int m = 0; m < 8; ++m) b.yb[f * g.yb_f + (long long)(t + T * m) * g.hs + kx] = v[m];
+      }
+    }
+  }
+}
+
+// ================================================ real lines (set / get) ===
+// xfwd_real: FP64 real lines of length N -> X[0..h-1] (row stride hs).
+template <typename R, int N, int L>
+__global__ void __launch_bounds__((N / 16) * L) k_xfwd_real(Geo g, const double *__restrict__ phys,
+                                                             typename CplxOf<R>::T *__restrict__ dst,
+                                                             const typename CplxOf<R>::T *__restrict__ tw) {
+  using C = typename CplxOf<R>::T;
+  constexpr int H = N / 2, TX = H / 8, SL = smline_len(H);
+  C *S = dyn_smem<C>();
+  const int t = threadIdx.x % TX, l = threadIdx.x / TX;
+  const long long line0 = (long long)blockIdx.x * L;
+  const double2 *row = reinterpret_cast<const double2 *>(phys + (line0 + l) * N);
+  C v[8];
+#pragma unroll
+  for (int m = 0; m < 8; ++m) {
+    const double2 p = row[t + TX * m];
+    v[m] = C{(R)p.x, (R)p.y};
+  }
+  fft_line<H, -1, 2>(v, t, tw, SmLine<C>{S + l * SL});
+  emit_r2c<C, N, L>(v, t, l, S, dst, line0, g.h, g.hs, tw);
+}
+
+// xinv_real: X[0..h-1] (row stride hs) -> FP64 real lines of length N.
+template <typename R, int N, int L>
+__global__ void __launch_bounds__((N / 16) * L) k_xinv_real(Geo g, const typename CplxOf<R>::T *__restrict__ src,
+                                                             double *__restrict__ phys,
+                                                             const typename CplxOf<R>::T *__restrict__ tw) {
+  using C = typename CplxOf<R>::T;
+  constexpr int H = N / 2, TX = H / 8, SL = smline_len(H);
+  C *S = dyn_smem<C>();
+  const int t = threadIdx.x % TX, l = threadIdx.x / TX;
+  const long long line0 = (long long)blockIdx.x * L;
+  stage_lines<C, H, L>(S, src, line0, g.h, g.hs);
+  __syncthreads();
+  C v[8];
+#pragma unroll
+  for (int m = 0; m < 8; ++m) v[m] = c2r_pre<C, N>(S + l * SL, t + TX * m, tw);
+  fft_line<H, +1, 2>(v, t, tw, SmLine<C>{S + l * SL});
+  double2 *row = reinterpret_cast<double2 *>(phys + (line0 + l) * N);
+#pragma unroll
+  for (int m = 0; m < 8; ++m) row[t + TX * m] = make_double2((double)v[m].x, (double)v[m].y);
+}
+
+// ============================================================= launching ===
+template <typename K>
+inline void set_smem(K kernel, size_t bytes) {
+  cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+template <typename R>
+inline StepBufs<R> step_bufs(const Args &a) {
+  using C = typename CplxOf<R>::T;
+  StepBufs<R> b;
+  b.tw = (const C *)a.tw;
+  b.ef = (const R *)a.ef;
+  b.ef2 = (const R *)a.ef2;
+  b.u = (C *)a.u;
+  b.acc = (C *)a.acc;
+  b.F = (const C *)a.F;
+  b.zb = (C *)a.zb;
+  b.yb = (C *)a.yb;
+  b.dst = (C *)a.dst;
+  b.dt = (R)a.dt;
+  return b;
+}
+
+template <typename R, int N>
+struct Launch3 {
+  using C = typename CplxOf<R>::T;
+  static constexpr int T = N / 8;
+  static constexpr int WL = w_light<R, N>();
+  static constexpr int WH = w_heavy<R, N>();
+  static constexpr int L = x_lines<R, N>();
+  static constexpr size_t SM_L = (size_t)N * pitch_of(WL, sizeof(C)) * sizeof(C);
+  static constexpr size_t SM_H = (size_t)N * pitch_of(WH, sizeof(C)) * sizeof(C);
+  static constexpr size_t SM_X = (size_t)L * smline_len(N / 2) * sizeof(C);
+
+  static int run(int op, const Args &a, cudaStream_t s) {
+    const Geo &g = a.g;
+    const C *tw = (const C *)a.tw;
+    switch (op) {
+      case OP_PREPARE:
+        set_smem(k3_inv1<R, N, WL, true>, SM_L);
+        set_smem(k3_inv1<R, N, WL, false>, SM_L);
+        set_smem(k3_inv2<R, N, WL>, SM_L);
+        set_smem(k3_fwd2<R, N, WL>, SM_L);
+        set_smem(k3_xpass<R, N, L>, SM_X);
+        set_smem(k_xfwd_real<R, N, L>, SM_X);
+        set_smem(k_xinv_real<R, N, L>, SM_X);
+        set_smem(k3_fwd1<R, N, WH, MODE_RK1, true>, SM_H);
+        set_smem(k3_fwd1<R, N, WH, MODE_RK2, true>, SM_H);
+        set_smem(k3_fwd1<R, N, WH, MODE_RK3, true>, SM_H);
+        set_smem(k3_fwd1<R, N, WH, MODE_RK4, true>, SM_H);
+        set_smem(k3_fwd1<R, N, WH, MODE_RHS, false>, SM_H);
+        set_smem(k3_fwd1<R, N, WH, MODE_PROJ, false>, SM_H);
+        break;
+      case OP_INV1: {
+        const dim3 grid(g.c * (g.hs / WL));
+        if (a.curl)
+          k3_inv1<R, N, WL, true><<<grid, T * WL, SM_L, s>>>(g, (const C *)a.src, (C *)a.zb, tw);
+        else
+          k3_inv1<R, N, WL, false><<<grid, T * WL, SM_L, s>>>(g, (const C *)a.src, (C *)a.zb, tw);
+        break;
+      }
+      case OP_INV2:
+        k3_inv2<R, N, WL><<<dim3(g.hs / WL, N, a.nf), T * WL, SM_L, s>>>(g, (const C *)a.zb, (C *)a.yb, tw);
+        break;
+      case OP_XPASS:
+        k3_xpass<R, N, L><<<(unsigned)((long long)N * N / L), (N / 16) * L, SM_X, s>>>(g, (C *)a.yb, tw);
+        break;
+      case OP_FWD2:
+        k3_fwd2<R, N, WL><<<dim3(g.hs / WL, N, a.nf), T * WL, SM_L, s>>>(g, (const C *)a.yb, (C *)a.zb, tw);
+        break;
+      case OP_FWD1: {
+        const dim3 grid(g.c * (g.hs / WH));
+        const StepBufs<R> b = step_bufs<R>(a);
+        switch (a.mode) {
+          case MODE_RK1: k3_fwd1<R, N, WH, MODE_RK1, true><<<grid, T * WH, SM_H, s>>>(g, b); break;
+          case MODE_RK2: k3_fwd1<R, N, WH, MODE_RK2, true><<<grid, T * WH, SM_H, s>>>(g, b); break;
+          case MODE_RK3: k3_fwd1<R, N, WH, MODE_RK3, true><<<grid, T * WH, SM_H, s>>>(g, b); break;
+          case MODE_RK4: k3_fwd1<R, N, WH, MODE_RK4, true><<<grid, T * WH, SM_H, s>>>(g, b); break;
+          case MODE_RHS: k3_fwd1<R, N, WH, MODE_RHS, false><<<grid, T * WH, SM_H, s>>>(g, b); break;
+          default: k3_fwd1<R, N, WH, MODE_PROJ, false><<<grid, T * WH, SM_H, s>>>(g, b); break;
+        }
+        break;
+      }
+      case OP_XFWD_REAL:
+        k_xfwd_real<R, N, L><<<(unsigned)((long long)N * N / L), (N / 16) * L, SM_X, s>>>(
+            g, a.phys_in, (C *)a.yb + a.field * g.yb_f, tw);
+        break;
+      case OP_XINV_REAL:
+        k_xinv_real<R, N, L><<<(unsigned)((long long)N * N / L), (N / 16) * L, SM_X, s>>>(
+            g, (const C *)a.yb + a.field * g.yb_f, a.phys_out, tw);
+        break;
+      default:
+        return -1;
+    }
+    return (int)cudaGetLastError();
+  }
+};
+
+template <typename R, int N>
+struct Launch2 {
+  using C = typename CplxOf<R>::T;
+  static constexpr int T = N / 8;
+  static constexpr int WL = w_light<R, N>();
+  static constexpr int WH = w_heavy<R, N>();
+  static constexpr int L = x_lines<R, N>();
+  static constexpr size_t SM_L = (size_t)N * pitch_of(WL, sizeof(C)) * sizeof(C);
+  static constexpr size_t SM_H = (size_t)N * pitch_of(WH, sizeof(C)) * sizeof(C);
+  static constexpr size_t SM_X = (size_t)L * smline_len(N / 2) * sizeof(C);
+
+  static int run(int op, const Args &a, cudaStream_t s) {
+    const Geo &g = a.g;
+    const C *tw = (const C *)a.tw;
+    switch (op) {
+      case OP_PREPARE:
+        set_smem(k2_inv1<R, N, WL, true>, SM_L);
+        set_smem(k2_inv1<R, N, WL, false>, SM_L);
+        set_smem(k2_xpass<R, N, L>, SM_X);
+        set_smem(k_xfwd_real<R, N, L>, SM_X);
+        set_smem(k_xinv_real<R, N, L>, SM_X);
+        set_smem(k2_fwd1<R, N, WH, MODE_RK1, true>, SM_H);
+        set_smem(k2_fwd1<R, N, WH, MODE_RK2, true>, SM_H);
+        set_smem(k2_fwd1<R, N, WH, MODE_RK3, true>, SM_H);
+        set_smem(k2_fwd1<R, N, WH, MODE_RK4, true>, SM_H);
+        set_smem(k2_fwd1<R, N, WH, MODE_RHS, false>, SM_H);
+        set_smem(k2_fwd1<R, N, WH, MODE_PROJ, false>, SM_H);
+        break;
+      case OP_INV1:
+        if (a.curl)
+          k2_inv1<R, N, WL, true><<<g.hs / WL, T * WL, SM_L, s>>>(g, (const C *)a.src, (C *)a.yb, tw);
+        else
+          k2_inv1<R, N, WL, false><<<g.hs / WL, T * WL, SM_L, s>>>(g, (const C *)a.src, (C *)a.yb, tw);
+        break;
+      case OP_XPASS:
+        k2_xpass<R, N, L><<<N / L, (N / 16) * L, SM_X, s>>>(g, (C *)a.yb, tw);
+        break;
+      case OP_FWD1: {
+        const StepBufs<R> b = step_bufs<R>(a);
+        const unsigned grid = g.hs / WH;
+        switch (a.mode) {
+          case MODE_RK1: k2_fwd1<R, N, WH, MODE_RK1, true><<<grid, T * WH, SM_H, s>>>(g, b); break;
+          case MODE_RK2: k2_fwd1<R, N, WH, MODE_RK2, true><<<grid, T * WH, SM_H, s>>>(g, b); break;
+          case MODE_RK3: k2_fwd1<R, N, WH, MODE_RK3, true><<<grid, T * WH, SM_H, s>>>(g, b); break;
+          case MODE_RK4: k2_fwd1<R, N, WH, MODE_RK4, true><<<grid, T * WH, SM_H, s>>>(g, b); break;
+          case MODE_RHS: k2_fwd1<R, N, WH, MODE_RHS, false><<<grid, T * WH, SM_H, s>>>(g, b); break;
+          default: k2_fwd1<R, N, WH, MODE_PROJ, false><<<grid, T * WH, SM_H, s>>>(g, b); break;
+        }
+        break;
+      }
+      case OP_XFWD_REAL:
+        k_xfwd_real<R, N, L><<<N / L, (N / 16) * L, SM_X, s>>>(g, a.phys_in, (C *)a.yb + a.field * g.yb_f, tw);
+        break;
+      case OP_XINV_REAL:
+        k_xinv_real<R, N, L><<<N / L, (N / 16) * L, SM_X, s>>>(g, (const C *)a.yb + a.field * g.yb_f,
+                                                               a.phys_out, tw);
+        break;
+      default:
+        return -1;
+    }
+    return (int)cudaGetLastError();
+  }
+};
+
+}  // namespace nsk

@@ -1,0 +1,228 @@
+"""Thin ctypes binding of libns_gb300.so (C ABI in include/ns.h).
+
+Argument marshalling only: every step of the hot path runs in the library's
+CUDA kernels.  The module-level functions carry the C names; ``Solver`` is a
+small convenience wrapper over them.  Importing this module loads the
+library and raises if it is missing: there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libns_gb300.so")
+
+NS_OK = 0
+NS_EINVAL = -1
+NS_ENOMEM = -2
+NS_ECUDA = -3
+NS_EUNSUPPORTED = -4
+NS_ENONFINITE = -5
+NS_FP64 = 0
+NS_FP32 = 1
+
+ERROR_NAMES = {0: "NS_OK", -1: "NS_EINVAL", -2: "NS_ENOMEM", -3: "NS_ECUDA", -4: "NS_EUNSUPPORTED",
+               -5: "NS_ENONFINITE"}
+
+
+class ns_grid(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int), ("n", ctypes.c_int), ("precision", ctypes.c_int)]
+
+
+# (name, argtypes, restype) of every exported symbol declared in include/ns.h
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+_D = ctypes.c_double
+_LL = ctypes.c_longlong
+_PI = ctypes.POINTER(ctypes.c_int)
+_PD = ctypes.POINTER(ctypes.c_double)
+_PLL = ctypes.POINTER(ctypes.c_longlong)
+SIGNATURES = {
+    "ns_sizes": ([ctypes.POINTER(ns_grid), _PI, _PI, _PI, _PLL, _PLL, _PI], _I),
+    "ns_init": ([ctypes.POINTER(_P), ctypes.POINTER(ns_grid), _D, _D, _P], _I),
+    "ns_set_state": ([_P, _P], _I),
+    "ns_get_state": ([_P, _P], _I),
+    "ns_set_state_spectral": ([_P, _P], _I),
+    "ns_get_state_spectral": ([_P, _P], _I),
+    "ns_step": ([_P, _I], _I),
+    "ns_eval_rhs": ([_P, _P], _I),
+    "ns_diagnostics": ([_P, _PD, _PD], _I),
+    "ns_energy_spectrum": ([_P, _P, _PI], _I),
+    "ns_set_stream": ([_P, _P], _I),
+    "ns_sync": ([_P], _I),
+    "ns_profile_step": ([_P, _I, _P, _P, _I], _I),
+    "ns_num_kernels": ([], _I),
+    "ns_kernel_name": ([_I], ctypes.c_char_p),
+    "ns_kernel_bytes": ([_P, _I], _LL),
+    "ns_device_bytes": ([_P], _LL),
+    "ns_destroy": ([_P], None),
+    "ns_last_error": ([_P], ctypes.c_char_p),
+}
+
+
+def load(path: str = LIB_PATH) -> ctypes.CDLL:
+    if not os.path.exists(path):
+        raise ImportError(f"{path} is missing: build it with __graft_entry__.build() "
+                          "(the CUDA library is the only implementation)")
+    lib = ctypes.CDLL(path)
+    for name, (args, res) in SIGNATURES.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = res
+    return lib
+
+
+lib = load()
+
+
+class NSError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{ERROR_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _check(rc: int, state=None):
+    if rc != NS_OK:
+        msg = lib.ns_last_error(state)
+        raise NSError(rc, msg.decode() if msg else "")
+
+
+# ---------------------------------------------------- C-named functions ---
+def ns_sizes(dim: int, n: int, precision: int):
+    g = ns_grid(dim, n, precision)
+    kc, c, h, nb = _I(), _I(), _I(), _I()
+    sd, pd = _LL(), _LL()
+    _check(lib.ns_sizes(ctypes.byref(g), ctypes.byref(kc), ctypes.byref(c), ctypes.byref(h), ctypes.byref(sd),
+                        ctypes.byref(pd), ctypes.byref(nb)))
+    return dict(kc=kc.value, c=c.value, h=h.value, state_doubles=sd.value, phys_doubles=pd.value, nbins=nb.value)
+
+
+def ns_init(dim: int, n: int, precision: int, nu: float, dt: float, forcing_phys=None):
+    g = ns_grid(dim, n, precision)
+    out = _P()
+    f = None if forcing_phys is None else np.ascontiguousarray(forcing_phys, dtype=np.float64)
+    _check(lib.ns_init(ctypes.byref(out), ctypes.byref(g), float(nu), float(dt), None if f is None else _ptr(f)))
+    return out
+
+
+def ns_destroy(state) -> None:
+    lib.ns_destroy(state)
+
+
+def ns_step(state, nsteps: int) -> None:
+    _check(lib.ns_step(state, int(nsteps)), state)
+
+
+def ns_sync(state) -> None:
+    _check(lib.ns_sync(state), state)
+
+
+def ns_set_stream(state, stream_handle: int | None) -> None:
+    _check(lib.ns_set_stream(state, ctypes.c_void_p(stream_handle) if stream_handle else None), state)
+
+
+# ------------------------------------------------------------- wrapper ---
+class Solver:
+    """One solver state: ``Solver(dim, n, precision, nu, dt, forcing_phys=None)``.
+
+    Arrays in and out follow the canonical layouts of include/ns.h: physical
+    float64 ``(3, N, N, N)`` / ``(N, N)``; spectral complex128 ``(3, c, c, h)`` /
+    ``(c, h)``.
+    """
+
+    def __init__(self, dim: int, n: int, precision: int = NS_FP32, nu: float = 0.0, dt: float = 1e-3,
+                 forcing_phys=None):
+        self.dim, self.n, self.precision = dim, n, precision
+        self.sizes = ns_sizes(dim, n, precision)
+        kc, c, h = self.sizes["kc"], self.sizes["c"], self.sizes["h"]
+        self.spec_shape = (3, c, c, h) if dim == 3 else (c, h)
+        self.phys_shape = (3, n, n, n) if dim == 3 else (n, n)
+        if forcing_phys is not None:
+            forcing_phys = np.ascontiguousarray(forcing_phys, dtype=np.float64).reshape(self.phys_shape)
+        self.state = ns_init(dim, n, precision, nu, dt, forcing_phys)
+
+    def close(self):
+        if getattr(self, "state", None):
+            ns_destroy(self.state)
+            self.state = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def set_state(self, phys: np.ndarray) -> None:
+        p = np.ascontiguousarray(phys, dtype=np.float64).reshape(self.phys_shape)
+        _check(lib.ns_set_state(self.state, _ptr(p)), self.state)
+
+    def get_state(self) -> np.ndarray:
+        out = np.empty(self.phys_shape, np.float64)
+        _check(lib.ns_get_state(self.state, _ptr(out)), self.state)
+        return out
+
+    def set_state_spectral(self, spec: np.ndarray) -> None:
+        s = np.ascontiguousarray(spec, dtype=np.complex128).reshape(self.spec_shape)
+        _check(lib.ns_set_state_spectral(self.state, _ptr(s)), self.state)
+
+    def set_state_spectral_ptr(self, host_ptr: int) -> None:
+        """Set from a raw host pointer (e.g. pinned memory) in the canonical layout."""
+        _check(lib.ns_set_state_spectral(self.state, ctypes.c_void_p(host_ptr)), self.state)
+
+    def get_state_spectral(self) -> np.ndarray:
+        out = np.empty(self.spec_shape, np.complex128)
+        _check(lib.ns_get_state_spectral(self.state, _ptr(out)), self.state)
+        return out
+
+    def get_state_spectral_ptr(self, host_ptr: int) -> None:
+        _check(lib.ns_get_state_spectral(self.state, ctypes.c_void_p(host_ptr)), self.state)
+
+    def step(self, nsteps: int) -> None:
+        ns_step(self.state, nsteps)
+
+    def sync(self) -> None:
+        ns_sync(self.state)
+
+    def eval_rhs(self) -> np.ndarray:
+        out = np.empty(self.spec_shape, np.complex128)
+        _check(lib.ns_eval_rhs(self.state, _ptr(out)), self.state)
+        return out
+
+    def diagnostics(self):
+        e, o = _D(), _D()
+        _check(lib.ns_diagnostics(self.state, ctypes.byref(e), ctypes.byref(o)), self.state)
+        return e.value, o.value
+
+    def energy_spectrum(self) -> np.ndarray:
+        nb = self.sizes["nbins"]
+        out = np.zeros(nb, np.float64)
+        cap = _I(nb)
+        _check(lib.ns_energy_spectrum(self.state, _ptr(out), ctypes.byref(cap)), self.state)
+        return out[: cap.value]
+
+    def set_stream(self, stream_handle: int | None) -> None:
+        ns_set_stream(self.state, stream_handle)
+
+    def profile_step(self, nsteps: int):
+        k = lib.ns_num_kernels()
+        ms = np.zeros(k, np.float64)
+        cnt = np.zeros(k, np.int32)
+        _check(lib.ns_profile_step(self.state, int(nsteps), _ptr(ms), _ptr(cnt), k), self.state)
+        names = [lib.ns_kernel_name(i).decode() for i in range(k)]
+        return {names[i]: (float(ms[i]), int(cnt[i]), int(lib.ns_kernel_bytes(self.state, i))) for i in range(k)}
+
+    def device_bytes(self) -> int:
+        return int(lib.ns_device_bytes(self.state))

@@ -1,0 +1,72 @@
+"""The C-ABI library loads and exports every symbol include/ns.h declares;
+host-side argument checks return error codes without touching a GPU."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    text = open(os.path.join(ROOT, "include", "ns.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(ns_[a-z_]+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def ns():
+    from paper_1807_01769_gb300 import build
+
+    build.build()
+    from paper_1807_01769_gb300 import ns as mod
+
+    return mod
+
+
+def test_header_declares_the_boundary():
+    syms = declared_symbols()
+    for name in ["ns_init", "ns_step", "ns_energy_spectrum", "ns_set_state", "ns_get_state", "ns_diagnostics",
+                 "ns_destroy", "ns_last_error", "ns_set_stream"]:
+        assert name in syms
+
+
+def test_library_exports_every_declared_symbol(ns):
+    lib = ctypes.CDLL(ns.LIB_PATH)
+    missing = [s for s in declared_symbols() if not hasattr(lib, s)]
+    assert not missing, missing
+    assert set(declared_symbols()) == set(ns.SIGNATURES)
+
+
+def test_sizes(ns):
+    s = ns.ns_sizes(3, 512, ns.NS_FP32)
+    assert (s["kc"], s["c"], s["h"], s["nbins"]) == (170, 341, 171, 295)
+    assert s["state_doubles"] == 2 * 3 * 341 * 341 * 171
+    s = ns.ns_sizes(2, 128, ns.NS_FP64)
+    assert (s["kc"], s["c"], s["h"], s["nbins"]) == (42, 85, 43, 60)
+
+
+@pytest.mark.parametrize("dim,n,prec,code", [(4, 64, 1, -1), (3, 100, 1, -1), (3, 8, 1, -4), (3, 2048, 1, -4),
+                                              (2, 4096, 1, -4), (2, 64, 7, -1)])
+def test_bad_grids_rejected(ns, dim, n, prec, code):
+    with pytest.raises(ns.NSError) as ei:
+        ns.ns_sizes(dim, n, prec)
+    assert ei.value.code == code
+
+
+@pytest.mark.parametrize("nu,dt", [(-1.0, 1e-3), (1e-3, 0.0), (1e-3, -1.0), (float("nan"), 1e-3)])
+def test_bad_parameters_rejected_before_any_device_call(ns, nu, dt):
+    with pytest.raises(ns.NSError) as ei:
+        ns.ns_init(2, 64, ns.NS_FP32, nu, dt)
+    assert ei.value.code == ns.NS_EINVAL
+
+
+def test_null_state_calls_return_einval(ns):
+    assert ns.lib.ns_step(None, 1) == ns.NS_EINVAL
+    assert ns.lib.ns_sync(None) == ns.NS_EINVAL
+    assert ns.lib.ns_set_state(None, None) == ns.NS_EINVAL
+    assert ns.lib.ns_kernel_bytes(None, 0) == -1
+    ns.lib.ns_destroy(None)
+    assert ns.lib.ns_num_kernels() == 5
+    assert [ns.lib.ns_kernel_name(i).decode() for i in range(5)] == ["inv1", "inv2", "xpass", "fwd2", "fwd1"]
