@@ -189,7 +189,9 @@ def run_gb300(args):
 
     u0 = inputs.random_velocity_3d(N_GRID, seed=0, k0=4.0, a=2.0, energy=0.5)
     s = ns.Solver(3, N_GRID, ns.NS_FP32, nu=NU, dt=DT)
-    stream = torch.cuda.current_stream()
+    # a dedicated (non-default) torch stream: the library launches on it and
+    # the CUDA events below are recorded on it
+    stream = torch.cuda.Stream()
     s.set_stream(stream.cuda_stream)
     s.set_state_spectral(u0)
 
@@ -296,7 +298,10 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--e2e-reps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--n", type=int, default=512, help="grid size override (profiling of smaller cases only)")
     args = ap.parse_args()
+    global N_GRID
+    N_GRID = args.n
     if args.impl == "reference":
         return run_reference(args)
     return run_gb300(args)

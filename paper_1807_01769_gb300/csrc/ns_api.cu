@@ -346,7 +346,7 @@ int ns_init(ns_state **out, const ns_grid *grid, double nu, double dt, const dou
       return bail(NS_ECUDA);                                                                            \
     }                                                                                                   \
   } while (0)
-  INIT_CK(cudaStreamCreateWithFlags(&s->own, cudaStreamNonBlocking));
+  INIT_CK(cudaStreamCreateWithFlags(&s->own, cudaStreamDefault));
   INIT_CK(cudaStreamCreateWithFlags(&s->cap, cudaStreamNonBlocking));
   s->stream = s->own;
 

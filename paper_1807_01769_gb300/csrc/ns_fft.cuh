@@ -198,35 +198,47 @@ struct StagePlan {
   static constexpr int NS = S == 0 ? 1 : (R0 > 1 ? R0 * (1 << (3 * (S - 1))) : (1 << (3 * S)));
 };
 
-template <int L, int S, int DIR, int TS, typename C, typename SM>
+// Synchronisation scope of the exchanges: a whole block, or one warp when
+// every line exchanged lives inside that warp.
+enum SyncScope { SYNC_BLOCK = 0, SYNC_WARP = 1 };
+template <int SY>
+__device__ __forceinline__ void fft_sync() {
+  if (SY == SYNC_WARP)
+    __syncwarp();
+  else
+    __syncthreads();
+}
+
+template <int L, int S, int DIR, int TS, int SY, typename C, typename SM>
 struct FftRun {
   __device__ __forceinline__ static void run(C (&v)[8], int t, const C *__restrict__ tw, const SM &sm) {
     using P = StagePlan<L, S>;
     constexpr int T = L / 8;
     if (S > 0) {
-      __syncthreads();  // the previous stage's shared writes are visible
+      fft_sync<SY>();  // the previous stage's shared writes are visible
 #pragma unroll
       for (int m = 0; m < 8; ++m) v[m] = sm.ld(t + T * m);
-      if (S < P::NST - 1) __syncthreads();  // everyone read before the next writes
+      if (S < P::NST - 1) fft_sync<SY>();  // everyone read before the next writes
     }
     fft_stage<L, P::RADIX, P::NS, DIR, TS, S == P::NST - 1>(v, t, tw, sm);
-    FftRun<L, S + 1, DIR, TS, C, SM>::next(v, t, tw, sm);
+    FftRun<L, S + 1, DIR, TS, SY, C, SM>::next(v, t, tw, sm);
   }
   __device__ __forceinline__ static void next(C (&v)[8], int t, const C *__restrict__ tw, const SM &sm) {
-    if constexpr (S < StagePlan<L, 0>::NST) FftRun<L, S, DIR, TS, C, SM>::run(v, t, tw, sm);
+    if constexpr (S < StagePlan<L, 0>::NST) FftRun<L, S, DIR, TS, SY, C, SM>::run(v, t, tw, sm);
   }
 };
 
 // Length-L FFT of one line held as v[m] = x[t + T m] (T = L/8) by threads
-// t = 0..T-1.  Every thread of the block must call it (it synchronises the
-// block); sm is this thread's view of a scratch line of at least L entries.
-// On return v[m] = X[t + T m], X_k = sum_j x_j exp(DIR 2 pi i j k / L).
-// Twiddles come from tw[j] = exp(-2 pi i j / (L TS)).
-template <int L, int DIR, int TS, typename C, typename SM>
+// t = 0..T-1.  Every thread of the sync scope (the block, or the warp for
+// SYNC_WARP) must call it; sm is this thread's view of a scratch line of at
+// least L entries.  On return v[m] = X[t + T m],
+// X_k = sum_j x_j exp(DIR 2 pi i j k / L).  Twiddles come from
+// tw[j] = exp(-2 pi i j / (L TS)).
+template <int L, int DIR, int TS, typename C, typename SM, int SY = SYNC_BLOCK>
 __device__ __forceinline__ void fft_line(C (&v)[8], int t, const C *__restrict__ tw, const SM &sm) {
   static_assert(L >= 8 && (L & (L - 1)) == 0, "power of two >= 8");
-  if (StagePlan<L, 0>::NST > 1) __syncthreads();  // the scratch line is free
-  FftRun<L, 0, DIR, TS, C, SM>::run(v, t, tw, sm);
+  if (StagePlan<L, 0>::NST > 1) fft_sync<SY>();  // the scratch line is free
+  FftRun<L, 0, DIR, TS, SY, C, SM>::run(v, t, tw, sm);
 }
 
 }  // namespace nsk

@@ -140,6 +140,63 @@ __device__ __forceinline__ void emit_r2c(C (&v)[8], int t, int l, C *S, C *__res
   }
 }
 
+// ------------------------------------- warp-per-line x helpers (TX <= 32) ---
+// Lane t of a line (TX lanes) holds slot m = index k = t + TX m of a length-H
+// line.  Returns the value at index (H - k) mod H: lane (TX - t) mod TX holds
+// it in slot 7 - m (t > 0) or slot (8 - m) mod 8 (t = 0).  All lanes of the
+// warp must call it with the same m.
+template <int TX, typename C>
+__device__ __forceinline__ C shfl_partner(const C (&x)[8], int m, int t) {
+  const C send = (t == 0) ? x[(8 - m) & 7] : x[7 - m];
+  if (TX == 1) return send;
+  const int src = (TX - t) & (TX - 1);
+  return C{__shfl_sync(0xffffffffu, send.x, src, TX), __shfl_sync(0xffffffffu, send.y, src, TX)};
+}
+
+// c2r pre-processing from registers (see c2r_pre); x[m] = X[t + TX m].
+template <typename C, int N, int TX>
+__device__ __forceinline__ C c2r_pre_reg(const C (&x)[8], int m, int t, const C *__restrict__ tw) {
+  const int k = t + TX * m;
+  C xk = x[m];
+  C xm = shfl_partner<TX>(x, m, t);
+  if (k == 0) {
+    xk.y = 0;
+    xm = czero<C>();
+  }
+  const C a = cadd(xk, cconj(xm));
+  const C b = csub(xk, cconj(xm));
+  const C e = cconj(__ldg(tw + k));
+  return cadd(a, cmuli(cmul(e, b)));
+}
+
+// r2c post-processing from registers (see r2c_post); z[m] = Z[t + TX m].
+template <typename C, int N, int TX>
+__device__ __forceinline__ C r2c_post_reg(const C (&z)[8], int m, int t, const C *__restrict__ tw) {
+  using R = decltype(C{}.x);
+  const int k = t + TX * m;
+  const C zk = z[m];
+  const C zm = shfl_partner<TX>(z, m, t);
+  const C a = cadd(zk, cconj(zm));
+  const C b = csub(zk, cconj(zm));
+  const C e = __ldg(tw + k);
+  const C r = csub(a, cmuli(cmul(e, b)));
+  return C{(R)0.5 * r.x, (R)0.5 * r.y};
+}
+
+template <typename C, int TX>
+__device__ __forceinline__ void load_line(C (&x)[8], const C *__restrict__ src, int t, int h) {
+#pragma unroll
+  for (int m = 0; m < 8; ++m) {
+    const int k = t + TX * m;
+    x[m] = k < h ? src[k] : czero<C>();
+  }
+}
+
+template <int N, bool MULTI>
+__host__ __device__ constexpr int xw_line_len() {
+  return smline_len(N / 2) + (MULTI ? 2 : 0);
+}
+
 // ================================================================== 3D ====
 // inv1: z inverse from a state-shaped array.  CURL: six fields (u, i k x u);
 // otherwise three fields (u).  One block = a tile of W kx columns at one ky.
@@ -283,6 +340,78 @@ __global__ void __launch_bounds__((N / 16) * L) k3_xpass(Geo g, typename CplxOf<
   }
 }
 
+// xpass (3D), one warp per line group: lines (z, y), TX = N/16 <= 32 lanes per
+// line, warp-level exchanges only.  Same arithmetic as k3_xpass.  The three
+// velocity fields are parked in a thread-private shared slot [field][m][lane]
+// (each thread reads back only what it wrote) so that the product accumulators
+// and the prefetched next field fit in 128 registers.
+template <typename R, int N, int WPB>
+__global__ void __launch_bounds__(32 * WPB, 16 / WPB) k3_xpass_w(Geo g, typename CplxOf<R>::T *__restrict__ yb,
+                                                                  const typename CplxOf<R>::T *__restrict__ tw) {
+  using C = typename CplxOf<R>::T;
+  constexpr int H = N / 2, TX = H / 8, LPW = 32 / TX;
+  constexpr int SL = xw_line_len<N, (LPW > 1)>();
+  constexpr int WSM = LPW * SL + 3 * 8 * 32;  // per-warp shared elements
+  C *S = dyn_smem<C>();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int t = lane % TX, sub = lane / TX;
+  const long long line = ((long long)blockIdx.x * WPB + warp) * LPW + sub;
+  C *wsm = S + warp * WSM;
+  const SmLine<C> view{wsm + sub * SL};
+  C *park = wsm + LPW * SL + lane;  // park[(a * 8 + m) * 32]
+  const C *src = yb + line * g.hs;
+  C xn[8];
+  load_line<C, TX>(xn, src, t, g.h);
+  C nx[8], ny[8], nz[8];
+#pragma unroll 1
+  for (int f = 0; f < 6; ++f) {
+    C v[8];
+#pragma unroll
+    for (int m = 0; m < 8; ++m) v[m] = c2r_pre_reg<C, N, TX>(xn, m, t, tw);
+    if (f < 5) load_line<C, TX>(xn, src + (f + 1) * g.yb_f, t, g.h);  // prefetch the next field
+    fft_line<H, +1, 2, C, SmLine<C>, SYNC_WARP>(v, t, tw, view);
+    if (f < 3) {
+#pragma unroll
+      for (int m = 0; m < 8; ++m) park[(f * 8 + m) * 32] = v[m];
+    } else if (f == 3) {  // w_x:  n_y = u_z w_x,  n_z = -u_y w_x
+#pragma unroll
+      for (int m = 0; m < 8; ++m) {
+        const C uy = park[(8 + m) * 32], uz = park[(16 + m) * 32];
+        ny[m] = pmul(uz, v[m]);
+        nz[m] = pmul(C{-uy.x, -uy.y}, v[m]);
+      }
+    } else if (f == 4) {  // w_y:  n_x = -u_z w_y, n_z += u_x w_y
+#pragma unroll
+      for (int m = 0; m < 8; ++m) {
+        const C ux = park[m * 32], uz = park[(16 + m) * 32];
+        nx[m] = pmul(C{-uz.x, -uz.y}, v[m]);
+        nz[m] = pfma(ux, v[m], nz[m]);
+      }
+    } else {  // w_z: n_x += u_y w_z, n_y -= u_x w_z
+#pragma unroll
+      for (int m = 0; m < 8; ++m) {
+        const C ux = park[m * 32], uy = park[(8 + m) * 32];
+        nx[m] = pfma(uy, v[m], nx[m]);
+        ny[m] = pfms(ux, v[m], ny[m]);
+      }
+    }
+  }
+#pragma unroll 1
+  for (int gg = 0; gg < 3; ++gg) {
+    C v[8];
+#pragma unroll
+    for (int m = 0; m < 8; ++m) v[m] = gg == 0 ? nx[m] : (gg == 1 ? ny[m] : nz[m]);
+    fft_line<H, -1, 2, C, SmLine<C>, SYNC_WARP>(v, t, tw, view);
+    C *dst = yb + gg * g.yb_f + line * g.hs;
+#pragma unroll
+    for (int m = 0; m < 8; ++m) {
+      const C x = r2c_post_reg<C, N, TX>(v, m, t, tw);
+      const int k = t + TX * m;
+      if (k < g.h) dst[k] = x;
+    }
+  }
+}
+
 // fwd2: y forward of field blockIdx.z at plane z = blockIdx.y, keep retained ky.
 template <typename R, int N, int W>
 __global__ void __launch_bounds__((N / 8) * W) k3_fwd2(Geo g, const typename CplxOf<R>::T *__restrict__ yb,
@@ -380,19 +509,18 @@ __global__ void __launch_bounds__((N / 8) * W) k3_fwd1(Geo g, StepBufs<R> b) {
   const long long st = g.st_comp;
   const SmCol<C> view{sm + w, P};
   const R scale = (R)1 / ((R)N * (R)N * (R)N);
+  // all three fields' loads are issued before the first transform
   C s0[8], s1[8], s2[8];
-  for (int gg = 0; gg < 3; ++gg) {
-    C v[8];
 #pragma unroll
-    for (int m = 0; m < 8; ++m) v[m] = valid ? b.zb[gg * g.zb_f + (long long)(t + T * m) * plane + col] : czero<C>();
-    fft_line<N, -1, 1>(v, t, b.tw, view);
-#pragma unroll
-    for (int m = 0; m < 8; ++m) {
-      if (gg == 0) s0[m] = v[m];
-      else if (gg == 1) s1[m] = v[m];
-      else s2[m] = v[m];
-    }
+  for (int m = 0; m < 8; ++m) {
+    const long long off = (long long)(t + T * m) * plane + col;
+    s0[m] = valid ? b.zb[off] : czero<C>();
+    s1[m] = valid ? b.zb[g.zb_f + off] : czero<C>();
+    s2[m] = valid ? b.zb[2 * g.zb_f + off] : czero<C>();
   }
+  fft_line<N, -1, 1>(s0, t, b.tw, view);
+  fft_line<N, -1, 1>(s1, t, b.tw, view);
+  fft_line<N, -1, 1>(s2, t, b.tw, view);
 #pragma unroll
   for (int m = 0; m < 8; ++m) {
     const int n = t + T * m;
@@ -533,6 +661,47 @@ __global__ void __launch_bounds__((N / 16) * L) k2_xpass(Geo g, typename CplxOf<
   emit_r2c<C, N, L>(nn, t, l, S, yb, line0, g.h, g.hs, tw);
 }
 
+// xpass (2D), one warp per line group (see k3_xpass_w).
+template <typename R, int N, int WPB>
+__global__ void __launch_bounds__(32 * WPB) k2_xpass_w(Geo g, typename CplxOf<R>::T *__restrict__ yb,
+                                                        const typename CplxOf<R>::T *__restrict__ tw) {
+  using C = typename CplxOf<R>::T;
+  constexpr int H = N / 2, TX = H / 8, LPW = 32 / TX;
+  constexpr int SL = xw_line_len<N, (LPW > 1)>();
+  C *S = dyn_smem<C>();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int t = lane % TX, sub = lane / TX;
+  const long long line = ((long long)blockIdx.x * WPB + warp) * LPW + sub;
+  const SmLine<C> view{S + (warp * LPW + sub) * SL};
+  const C *src = yb + line * g.hs;
+  C xn[8];
+  load_line<C, TX>(xn, src, t, g.h);
+  C ux[8], uy[8], nn[8];
+#pragma unroll 1
+  for (int f = 0; f < 4; ++f) {
+    C v[8];
+#pragma unroll
+    for (int m = 0; m < 8; ++m) v[m] = c2r_pre_reg<C, N, TX>(xn, m, t, tw);
+    if (f < 3) load_line<C, TX>(xn, src + (f + 1) * g.yb_f, t, g.h);
+    fft_line<H, +1, 2, C, SmLine<C>, SYNC_WARP>(v, t, tw, view);
+#pragma unroll
+    for (int m = 0; m < 8; ++m) {
+      if (f == 0) ux[m] = v[m];
+      else if (f == 1) uy[m] = v[m];
+      else if (f == 2) nn[m] = pmul(C{-ux[m].x, -ux[m].y}, v[m]);
+      else nn[m] = pfms(uy[m], v[m], nn[m]);
+    }
+  }
+  fft_line<H, -1, 2, C, SmLine<C>, SYNC_WARP>(nn, t, tw, view);
+  C *dst = yb + line * g.hs;
+#pragma unroll
+  for (int m = 0; m < 8; ++m) {
+    const C x = r2c_post_reg<C, N, TX>(nn, m, t, tw);
+    const int k = t + TX * m;
+    if (k < g.h) dst[k] = x;
+  }
+}
+
 // fwd1 (2D): y forward of field 0, dealias, 1/N^2, forcing, RK stage; INV:
 // the four inverse fields of the next stage input.
 template <typename R, int N, int W, int MODE, bool INV>
@@ -663,12 +832,19 @@ struct Launch3 {
   static constexpr size_t SM_L = (size_t)N * pitch_of(WL, sizeof(C)) * sizeof(C);
   static constexpr size_t SM_H = (size_t)N * pitch_of(WH, sizeof(C)) * sizeof(C);
   static constexpr size_t SM_X = (size_t)L * smline_len(N / 2) * sizeof(C);
+  // warp-per-line x pass when a line fits in one warp
+  static constexpr bool XW = N / 16 <= 32;
+  static constexpr int XW_WPB = 4;
+  static constexpr int XW_LPW = XW ? 32 / (N / 16) : 1;
+  static constexpr size_t SM_XW =
+      (size_t)XW_WPB * (XW_LPW * xw_line_len<N, (XW_LPW > 1)>() + 3 * 8 * 32) * sizeof(C);
 
   static int run(int op, const Args &a, cudaStream_t s) {
     const Geo &g = a.g;
     const C *tw = (const C *)a.tw;
     switch (op) {
       case OP_PREPARE:
+        if constexpr (XW) set_smem(k3_xpass_w<R, N, XW_WPB>, SM_XW);
         set_smem(k3_inv1<R, N, WL, true>, SM_L);
         set_smem(k3_inv1<R, N, WL, false>, SM_L);
         set_smem(k3_inv2<R, N, WL>, SM_L);
@@ -695,7 +871,12 @@ struct Launch3 {
         k3_inv2<R, N, WL><<<dim3(g.hs / WL, N, a.nf), T * WL, SM_L, s>>>(g, (const C *)a.zb, (C *)a.yb, tw);
         break;
       case OP_XPASS:
-        k3_xpass<R, N, L><<<(unsigned)((long long)N * N / L), (N / 16) * L, SM_X, s>>>(g, (C *)a.yb, tw);
+        if constexpr (XW) {
+          k3_xpass_w<R, N, XW_WPB><<<(unsigned)((long long)N * N / (XW_WPB * XW_LPW)), 32 * XW_WPB, SM_XW, s>>>(
+              g, (C *)a.yb, tw);
+        } else {
+          k3_xpass<R, N, L><<<(unsigned)((long long)N * N / L), (N / 16) * L, SM_X, s>>>(g, (C *)a.yb, tw);
+        }
         break;
       case OP_FWD2:
         k3_fwd2<R, N, WL><<<dim3(g.hs / WL, N, a.nf), T * WL, SM_L, s>>>(g, (const C *)a.yb, (C *)a.zb, tw);
@@ -738,12 +919,18 @@ struct Launch2 {
   static constexpr size_t SM_L = (size_t)N * pitch_of(WL, sizeof(C)) * sizeof(C);
   static constexpr size_t SM_H = (size_t)N * pitch_of(WH, sizeof(C)) * sizeof(C);
   static constexpr size_t SM_X = (size_t)L * smline_len(N / 2) * sizeof(C);
+  static constexpr int XW_WPB = 4;
+  static constexpr int XW_LPW = N / 16 <= 32 ? 32 / (N / 16) : 1;
+  // warp-per-line x pass when a line fits in one warp and there are enough lines
+  static constexpr bool XW2 = N / 16 <= 32 && N >= 64 && N % (XW_WPB * XW_LPW) == 0;
+  static constexpr size_t SM_XW = (size_t)XW_WPB * XW_LPW * xw_line_len<N, (XW_LPW > 1)>() * sizeof(C);
 
   static int run(int op, const Args &a, cudaStream_t s) {
     const Geo &g = a.g;
     const C *tw = (const C *)a.tw;
     switch (op) {
       case OP_PREPARE:
+        if constexpr (XW2) set_smem(k2_xpass_w<R, N, XW_WPB>, SM_XW);
         set_smem(k2_inv1<R, N, WL, true>, SM_L);
         set_smem(k2_inv1<R, N, WL, false>, SM_L);
         set_smem(k2_xpass<R, N, L>, SM_X);
@@ -763,7 +950,11 @@ struct Launch2 {
           k2_inv1<R, N, WL, false><<<g.hs / WL, T * WL, SM_L, s>>>(g, (const C *)a.src, (C *)a.yb, tw);
         break;
       case OP_XPASS:
-        k2_xpass<R, N, L><<<N / L, (N / 16) * L, SM_X, s>>>(g, (C *)a.yb, tw);
+        if constexpr (XW2) {
+          k2_xpass_w<R, N, XW_WPB><<<N / (XW_WPB * XW_LPW), 32 * XW_WPB, SM_XW, s>>>(g, (C *)a.yb, tw);
+        } else {
+          k2_xpass<R, N, L><<<N / L, (N / 16) * L, SM_X, s>>>(g, (C *)a.yb, tw);
+        }
         break;
       case OP_FWD1: {
         const StepBufs<R> b = step_bufs<R>(a);
