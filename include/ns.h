@@ -153,6 +153,34 @@ long long ns_kernel_bytes(const ns_state *s, int id);
 /* Device bytes held by the state. */
 long long ns_device_bytes(const ns_state *s);
 
+/* Diagnostics for callers that cannot allocate device memory.
+ * The FluidSim paper has no counterpart: this entry point exists for code that
+ * must not call cudaMalloc -- a host callback, an allocator hook, a process
+ * whose device memory is owned and budgeted by another framework -- but holds
+ * a spectrum on the device.  It computes what ns_diagnostics and
+ * ns_energy_spectrum compute, with the same kernels and summation order, and
+ * allocates nothing: its partial sums live in a static device array of
+ * NS_NOALLOC_SCRATCH_DOUBLES doubles (2 MiB) that every GPU loading the
+ * library holds until the process exits.
+ *   grid     : dim, n, precision of the data;
+ *   spec_dev : DEVICE pointer to the state in the canonical truncated spectral
+ *              layout (rows of h complex numbers, no padding), complex128 for
+ *              NS_FP64 or complex64 for NS_FP32; read only;
+ *   out_dev  : DEVICE pointer to nbins + 2 doubles: out[0] energy, out[1]
+ *              enstrophy, out[2 + m] the shell spectrum (see ns_sizes);
+ *   cuda_stream: cudaStream_t as void* (null = the legacy default stream).
+ * Asynchronous: returns once the work is enqueued; synchronise the stream
+ * before reading out_dev.  Returns NS_OK, NS_EINVAL (null pointer, bad grid),
+ * NS_EUNSUPPORTED (the grid needs more scratch than the static array holds:
+ * every 2D grid fits, 3D up to n = 256), or NS_ECUDA.  The first call on a
+ * device looks up the array's device address (cudaGetSymbolAddress) with that
+ * device current; make that first call before any stream capture.  All calls
+ * share the array, so calls whose kernels may overlap on the GPU (unordered
+ * streams) race on it; calls on one stream are ordered and safe.  Each call
+ * rewrites the scratch it reads, so nothing needs clearing in between. */
+#define NS_NOALLOC_SCRATCH_DOUBLES 262144
+int ns_diagnostics_noalloc(const ns_grid *grid, const void *spec_dev, double *out_dev, void *cuda_stream);
+
 /* Release everything the state owns.  Null is ignored. */
 void ns_destroy(ns_state *s);
 

@@ -58,6 +58,7 @@ SIGNATURES = {
     "ns_kernel_name": ([_I], ctypes.c_char_p),
     "ns_kernel_bytes": ([_P, _I], _LL),
     "ns_device_bytes": ([_P], _LL),
+    "ns_diagnostics_noalloc": ([ctypes.POINTER(ns_grid), _P, _P, _P], _I),
     "ns_destroy": ([_P], None),
     "ns_last_error": ([_P], ctypes.c_char_p),
 }
