@@ -21,6 +21,7 @@
 #include <vector>
 
 #include "ns.h"
+#include "ns_fft.cuh"
 #include "ns_internal.h"
 
 using nsk::Args;
@@ -258,12 +259,25 @@ void fill_tables(const ns_state *s, std::vector<unsigned char> &tw, std::vector<
                  std::vector<unsigned char> &ef2) {
   const int n = s->grid.n;
   const long double two_pi = 6.283185307179586476925286766559005768L;
-  tw.resize(sizeof(R) * 2 * n);
+  // exp(-2 pi i j / N), then the stage twiddle tables of lengths N and N/2
+  const int len_n = nsk::stage_tw_len(n), len_h = nsk::stage_tw_len(n / 2);
+  tw.resize(sizeof(R) * 2 * (size_t)(n + len_n + len_h));
   R *t = reinterpret_cast<R *>(tw.data());
-  for (int j = 0; j < n; ++j) {
-    const double ang = (double)(two_pi * (long double)j / (long double)n);
-    t[2 * j] = (R)std::cos(ang);
-    t[2 * j + 1] = (R)(-std::sin(ang));
+  auto put = [&](int idx, long long num, long long den) {  // exp(-2 pi i num / den)
+    const double ang = (double)(two_pi * (long double)num / (long double)den);
+    t[2 * idx] = (R)std::cos(ang);
+    t[2 * idx + 1] = (R)(-std::sin(ang));
+  };
+  for (int j = 0; j < n; ++j) put(j, j, n);
+  int base = n;
+  for (int L : {n, n / 2}) {
+    for (int st = 1; st < nsk::plan_nst(L); ++st) {
+      const int R0 = nsk::plan_radix(L, st), NS = nsk::plan_span(L, st);
+      const int off = base + nsk::stage_tw_offset(L, st);
+      for (int r = 1; r < R0; ++r)
+        for (int j = 0; j < NS; ++j) put(off + (r - 1) * NS + j, (long long)r * j, (long long)NS * R0);
+    }
+    base += nsk::stage_tw_len(L);
   }
   const int mmax = s->grid.dim * s->g.kc * s->g.kc;
   ef.resize(sizeof(R) * (mmax + 1));

@@ -133,8 +133,7 @@ __device__ __forceinline__ void dftR<8, -1, double2>(double2 (&a)[8]) { dft8<-1>
 template <>
 __device__ __forceinline__ void dftR<8, 1, double2>(double2 (&a)[8]) { dft8<1>(a); }
 
-// Twiddle exp(DIR 2 pi i k / L) from the table tw[j] = exp(-2 pi i j / L_table),
-// read at j = k * TS (TS = L_table / L).
+// Table entry j of a table holding exp(-2 pi i (...)), conjugated for DIR = +1.
 template <int DIR, typename C>
 __device__ __forceinline__ C twiddle(const C *__restrict__ tw, int j) {
   const C w = __ldg(tw + j);
@@ -161,8 +160,8 @@ struct SmLine {
 __host__ __device__ constexpr int smline_len(int L) { return L + L / 8; }
 
 // One radix-R stage of span NS on a line of length L (see file header).
-template <int L, int R, int NS, int DIR, int TS, bool LAST, typename C, typename SM>
-__device__ __forceinline__ void fft_stage(C (&v)[8], int t, const C *__restrict__ tw, const SM &sm) {
+template <int L, int R, int NS, int TWOFF, int DIR, bool LAST, typename C, typename SM>
+__device__ __forceinline__ void fft_stage(C (&v)[8], int t, const C *__restrict__ stw, const SM &sm) {
   constexpr int T = L / 8;
   constexpr int Q = 8 / R;
 #pragma unroll
@@ -172,9 +171,9 @@ __device__ __forceinline__ void fft_stage(C (&v)[8], int t, const C *__restrict_
 #pragma unroll
     for (int r = 0; r < R; ++r) a[r] = v[q + r * Q];
     if (NS > 1) {
-      const int e = (b % NS) * (L / (NS * R));
+      const C *w = stw + TWOFF + (b % NS);
 #pragma unroll
-      for (int r = 1; r < R; ++r) a[r] = cmul(a[r], twiddle<DIR>(tw, r * e * TS));
+      for (int r = 1; r < R; ++r) a[r] = cmul(a[r], twiddle<DIR>(w, (r - 1) * NS));
     }
     dftR<R, DIR>(a);
     if (LAST) {
@@ -188,14 +187,29 @@ __device__ __forceinline__ void fft_stage(C (&v)[8], int t, const C *__restrict_
   }
 }
 
+// Radix and span of stage s of a length-L transform (host and device).
+__host__ __device__ constexpr int plan_r0(int L) { return 1 << (ilog2(L) % 3); }
+__host__ __device__ constexpr int plan_nst(int L) { return ilog2(L) / 3 + (plan_r0(L) > 1 ? 1 : 0); }
+__host__ __device__ constexpr int plan_radix(int L, int s) { return (s == 0 && plan_r0(L) > 1) ? plan_r0(L) : 8; }
+__host__ __device__ constexpr int plan_span(int L, int s) {
+  return s == 0 ? 1 : (plan_r0(L) > 1 ? plan_r0(L) * (1 << (3 * (s - 1))) : (1 << (3 * s)));
+}
+// Stage twiddle table of a length-L transform: for every stage s >= 1 a block
+// of (R_s - 1) NS_s entries, entry (r - 1) NS_s + j = exp(-2 pi i r j / (NS_s R_s)),
+// so the twiddles of consecutive butterflies j are consecutive in memory.
+__host__ __device__ constexpr int stage_tw_offset(int L, int s) {
+  return s <= 1 ? 0 : stage_tw_offset(L, s - 1) + (plan_radix(L, s - 1) - 1) * plan_span(L, s - 1);
+}
+__host__ __device__ constexpr int stage_tw_len(int L) { return stage_tw_offset(L, plan_nst(L)); }
+
 template <int L, int S>
 struct StagePlan {
   static constexpr int LOG = ilog2(L);
-  static constexpr int R0 = 1 << (LOG % 3);
-  static constexpr int NST = LOG / 3 + (R0 > 1 ? 1 : 0);
-  static constexpr int RADIX = (S == 0 && R0 > 1) ? R0 : 8;
-  // span before stage S = product of the radices of stages < S
-  static constexpr int NS = S == 0 ? 1 : (R0 > 1 ? R0 * (1 << (3 * (S - 1))) : (1 << (3 * S)));
+  static constexpr int R0 = plan_r0(L);
+  static constexpr int NST = plan_nst(L);
+  static constexpr int RADIX = plan_radix(L, S);
+  static constexpr int NS = plan_span(L, S);  // span before stage S
+  static constexpr int TWOFF = stage_tw_offset(L, S);
 };
 
 // Synchronisation scope of the exchanges: a whole block, or one warp when
@@ -209,9 +223,9 @@ __device__ __forceinline__ void fft_sync() {
     __syncthreads();
 }
 
-template <int L, int S, int DIR, int TS, int SY, typename C, typename SM>
+template <int L, int S, int DIR, int SY, typename C, typename SM>
 struct FftRun {
-  __device__ __forceinline__ static void run(C (&v)[8], int t, const C *__restrict__ tw, const SM &sm) {
+  __device__ __forceinline__ static void run(C (&v)[8], int t, const C *__restrict__ stw, const SM &sm) {
     using P = StagePlan<L, S>;
     constexpr int T = L / 8;
     if (S > 0) {
@@ -220,11 +234,11 @@ struct FftRun {
       for (int m = 0; m < 8; ++m) v[m] = sm.ld(t + T * m);
       if (S < P::NST - 1) fft_sync<SY>();  // everyone read before the next writes
     }
-    fft_stage<L, P::RADIX, P::NS, DIR, TS, S == P::NST - 1>(v, t, tw, sm);
-    FftRun<L, S + 1, DIR, TS, SY, C, SM>::next(v, t, tw, sm);
+    fft_stage<L, P::RADIX, P::NS, P::TWOFF, DIR, S == P::NST - 1>(v, t, stw, sm);
+    FftRun<L, S + 1, DIR, SY, C, SM>::next(v, t, stw, sm);
   }
-  __device__ __forceinline__ static void next(C (&v)[8], int t, const C *__restrict__ tw, const SM &sm) {
-    if constexpr (S < StagePlan<L, 0>::NST) FftRun<L, S, DIR, TS, SY, C, SM>::run(v, t, tw, sm);
+  __device__ __forceinline__ static void next(C (&v)[8], int t, const C *__restrict__ stw, const SM &sm) {
+    if constexpr (S < StagePlan<L, 0>::NST) FftRun<L, S, DIR, SY, C, SM>::run(v, t, stw, sm);
   }
 };
 
@@ -232,13 +246,13 @@ struct FftRun {
 // t = 0..T-1.  Every thread of the sync scope (the block, or the warp for
 // SYNC_WARP) must call it; sm is this thread's view of a scratch line of at
 // least L entries.  On return v[m] = X[t + T m],
-// X_k = sum_j x_j exp(DIR 2 pi i j k / L).  Twiddles come from
-// tw[j] = exp(-2 pi i j / (L TS)).
-template <int L, int DIR, int TS, typename C, typename SM, int SY = SYNC_BLOCK>
-__device__ __forceinline__ void fft_line(C (&v)[8], int t, const C *__restrict__ tw, const SM &sm) {
+// X_k = sum_j x_j exp(DIR 2 pi i j k / L).  stw is the stage twiddle table of
+// length L (stage_tw_len(L) entries, see stage_tw_offset).
+template <int L, int DIR, typename C, typename SM, int SY = SYNC_BLOCK>
+__device__ __forceinline__ void fft_line(C (&v)[8], int t, const C *__restrict__ stw, const SM &sm) {
   static_assert(L >= 8 && (L & (L - 1)) == 0, "power of two >= 8");
   if (StagePlan<L, 0>::NST > 1) fft_sync<SY>();  // the scratch line is free
-  FftRun<L, 0, DIR, TS, SY, C, SM>::run(v, t, tw, sm);
+  FftRun<L, 0, DIR, SY, C, SM>::run(v, t, stw, sm);
 }
 
 }  // namespace nsk

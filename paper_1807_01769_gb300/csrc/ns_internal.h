@@ -35,7 +35,8 @@ enum Mode { MODE_RK1 = 1, MODE_RK2 = 2, MODE_RK3 = 3, MODE_RK4 = 4, MODE_RHS = 5
 
 struct Args {
   Geo g;
-  const void *tw;  // length-N table exp(-2 pi i j / N), state precision
+  const void *tw;  // state precision: exp(-2 pi i j / N) for j < N, then the stage
+                   // twiddle tables of length N and of length N/2 (ns_fft.cuh)
   const void *ef;  // exp(-nu m dt),   m = |k|^2 = 0 .. dim kc^2
   const void *ef2; // exp(-nu m dt/2)
   void *u, *acc;

@@ -254,7 +254,7 @@ __global__ void __launch_bounds__((N / 8) * W) k3_inv1(Geo g, const typename Cpl
       }
       v[m] = x;
     }
-    fft_line<N, +1, 1>(v, t, tw, view);
+    fft_line<N, +1>(v, t, tw + N, view);
     if (valid) {
 #pragma unroll
       for (int m = 0; m < 8; ++m) zb[f * g.zb_f + (long long)(t + T * m) * plane + col] = v[m];
@@ -262,9 +262,10 @@ __global__ void __launch_bounds__((N / 8) * W) k3_inv1(Geo g, const typename Cpl
   }
 }
 
-// inv2: y inverse of field blockIdx.z at plane z = blockIdx.y.
+// inv2: y inverse of fields 0..nf-1 at plane z = blockIdx.y; the next field's
+// loads are issued before the current field is transformed.
 template <typename R, int N, int W>
-__global__ void __launch_bounds__((N / 8) * W) k3_inv2(Geo g, const typename CplxOf<R>::T *__restrict__ zb,
+__global__ void __launch_bounds__((N / 8) * W) k3_inv2(Geo g, int nf, const typename CplxOf<R>::T *__restrict__ zb,
                                                         typename CplxOf<R>::T *__restrict__ yb,
                                                         const typename CplxOf<R>::T *__restrict__ tw) {
   using C = typename CplxOf<R>::T;
@@ -274,19 +275,36 @@ __global__ void __launch_bounds__((N / 8) * W) k3_inv2(Geo g, const typename Cpl
   const int w = threadIdx.x % W, t = threadIdx.x / W;
   const int kx = blockIdx.x * W + w;
   const bool valid = kx < g.h;
-  const int z = blockIdx.y, f = blockIdx.z;
-  const C *in = zb + f * g.zb_f + (long long)z * g.c * g.hs + kx;
-  C *out = yb + f * g.yb_f + (long long)z * N * g.hs + kx;
-  C v[8];
+  const int z = blockIdx.y;
+  const C *in = zb + (long long)z * g.c * g.hs + kx;
+  C *out = yb + (long long)z * N * g.hs + kx;
+  int row[8];
+  bool live[8];
 #pragma unroll
   for (int m = 0; m < 8; ++m) {
     const int n = t + T * m;
-    v[m] = (valid && retained(n, N, g.kc)) ? in[(long long)compact_of(n, N, g.kc, g.c) * g.hs] : czero<C>();
+    live[m] = valid && retained(n, N, g.kc);
+    row[m] = compact_of(n, N, g.kc, g.c);
   }
-  fft_line<N, +1, 1>(v, t, tw, SmCol<C>{sm + w, P});
-  if (valid) {
+  C xn[8];
 #pragma unroll
-    for (int m = 0; m < 8; ++m) out[(long long)(t + T * m) * g.hs] = v[m];
+  for (int m = 0; m < 8; ++m) xn[m] = live[m] ? in[(long long)row[m] * g.hs] : czero<C>();
+#pragma unroll 1
+  for (int f = 0; f < nf; ++f) {
+    C v[8];
+#pragma unroll
+    for (int m = 0; m < 8; ++m) v[m] = xn[m];
+    if (f + 1 < nf) {
+      const C *nin = in + (f + 1) * g.zb_f;
+#pragma unroll
+      for (int m = 0; m < 8; ++m) xn[m] = live[m] ? nin[(long long)row[m] * g.hs] : czero<C>();
+    }
+    fft_line<N, +1>(v, t, tw + N, SmCol<C>{sm + w, P});
+    if (valid) {
+      C *o = out + f * g.yb_f;
+#pragma unroll
+      for (int m = 0; m < 8; ++m) o[(long long)(t + T * m) * g.hs] = v[m];
+    }
   }
 }
 
@@ -309,7 +327,7 @@ __global__ void __launch_bounds__((N / 16) * L) k3_xpass(Geo g, typename CplxOf<
     C v[8];
 #pragma unroll
     for (int m = 0; m < 8; ++m) v[m] = c2r_pre<C, N>(S + l * SL, t + TX * m, tw);
-    fft_line<H, +1, 2>(v, t, tw, view);
+    fft_line<H, +1>(v, t, tw + N + stage_tw_len(N), view);
 #pragma unroll
     for (int m = 0; m < 8; ++m) {
       switch (f) {
@@ -335,7 +353,7 @@ __global__ void __launch_bounds__((N / 16) * L) k3_xpass(Geo g, typename CplxOf<
     C v[8];
 #pragma unroll
     for (int m = 0; m < 8; ++m) v[m] = gg == 0 ? nx[m] : (gg == 1 ? ny[m] : nz[m]);
-    fft_line<H, -1, 2>(v, t, tw, view);
+    fft_line<H, -1>(v, t, tw + N + stage_tw_len(N), view);
     emit_r2c<C, N, L>(v, t, l, S, yb + gg * g.yb_f, line0, g.h, g.hs, tw);
   }
 }
@@ -369,7 +387,7 @@ __global__ void __launch_bounds__(32 * WPB, 16 / WPB) k3_xpass_w(Geo g, typename
 #pragma unroll
     for (int m = 0; m < 8; ++m) v[m] = c2r_pre_reg<C, N, TX>(xn, m, t, tw);
     if (f < 5) load_line<C, TX>(xn, src + (f + 1) * g.yb_f, t, g.h);  // prefetch the next field
-    fft_line<H, +1, 2, C, SmLine<C>, SYNC_WARP>(v, t, tw, view);
+    fft_line<H, +1, C, SmLine<C>, SYNC_WARP>(v, t, tw + N + stage_tw_len(N), view);
     if (f < 3) {
 #pragma unroll
       for (int m = 0; m < 8; ++m) park[(f * 8 + m) * 32] = v[m];
@@ -401,7 +419,7 @@ __global__ void __launch_bounds__(32 * WPB, 16 / WPB) k3_xpass_w(Geo g, typename
     C v[8];
 #pragma unroll
     for (int m = 0; m < 8; ++m) v[m] = gg == 0 ? nx[m] : (gg == 1 ? ny[m] : nz[m]);
-    fft_line<H, -1, 2, C, SmLine<C>, SYNC_WARP>(v, t, tw, view);
+    fft_line<H, -1, C, SmLine<C>, SYNC_WARP>(v, t, tw + N + stage_tw_len(N), view);
     C *dst = yb + gg * g.yb_f + line * g.hs;
 #pragma unroll
     for (int m = 0; m < 8; ++m) {
@@ -412,9 +430,10 @@ __global__ void __launch_bounds__(32 * WPB, 16 / WPB) k3_xpass_w(Geo g, typename
   }
 }
 
-// fwd2: y forward of field blockIdx.z at plane z = blockIdx.y, keep retained ky.
+// fwd2: y forward of fields 0..nf-1 at plane z = blockIdx.y, keep retained ky;
+// the next field's loads are issued before the current field is transformed.
 template <typename R, int N, int W>
-__global__ void __launch_bounds__((N / 8) * W) k3_fwd2(Geo g, const typename CplxOf<R>::T *__restrict__ yb,
+__global__ void __launch_bounds__((N / 8) * W) k3_fwd2(Geo g, int nf, const typename CplxOf<R>::T *__restrict__ yb,
                                                         typename CplxOf<R>::T *__restrict__ zb,
                                                         const typename CplxOf<R>::T *__restrict__ tw) {
   using C = typename CplxOf<R>::T;
@@ -424,18 +443,30 @@ __global__ void __launch_bounds__((N / 8) * W) k3_fwd2(Geo g, const typename Cpl
   const int w = threadIdx.x % W, t = threadIdx.x / W;
   const int kx = blockIdx.x * W + w;
   const bool valid = kx < g.h;
-  const int z = blockIdx.y, f = blockIdx.z;
-  const C *in = yb + f * g.yb_f + (long long)z * N * g.hs + kx;
-  C *out = zb + f * g.zb_f + (long long)z * g.c * g.hs + kx;
-  C v[8];
+  const int z = blockIdx.y;
+  const C *in = yb + (long long)z * N * g.hs + kx;
+  C *out = zb + (long long)z * g.c * g.hs + kx;
+  C xn[8];
 #pragma unroll
-  for (int m = 0; m < 8; ++m) v[m] = valid ? in[(long long)(t + T * m) * g.hs] : czero<C>();
-  fft_line<N, -1, 1>(v, t, tw, SmCol<C>{sm + w, P});
-  if (valid) {
+  for (int m = 0; m < 8; ++m) xn[m] = valid ? in[(long long)(t + T * m) * g.hs] : czero<C>();
+#pragma unroll 1
+  for (int f = 0; f < nf; ++f) {
+    C v[8];
 #pragma unroll
-    for (int m = 0; m < 8; ++m) {
-      const int n = t + T * m;
-      if (retained(n, N, g.kc)) out[(long long)compact_of(n, N, g.kc, g.c) * g.hs] = v[m];
+    for (int m = 0; m < 8; ++m) v[m] = xn[m];
+    if (f + 1 < nf) {
+      const C *nin = in + (f + 1) * g.yb_f;
+#pragma unroll
+      for (int m = 0; m < 8; ++m) xn[m] = valid ? nin[(long long)(t + T * m) * g.hs] : czero<C>();
+    }
+    fft_line<N, -1>(v, t, tw + N, SmCol<C>{sm + w, P});
+    if (valid) {
+      C *o = out + f * g.zb_f;
+#pragma unroll
+      for (int m = 0; m < 8; ++m) {
+        const int n = t + T * m;
+        if (retained(n, N, g.kc)) o[(long long)compact_of(n, N, g.kc, g.c) * g.hs] = v[m];
+      }
     }
   }
 }
@@ -518,9 +549,9 @@ __global__ void __launch_bounds__((N / 8) * W) k3_fwd1(Geo g, StepBufs<R> b) {
     s1[m] = valid ? b.zb[g.zb_f + off] : czero<C>();
     s2[m] = valid ? b.zb[2 * g.zb_f + off] : czero<C>();
   }
-  fft_line<N, -1, 1>(s0, t, b.tw, view);
-  fft_line<N, -1, 1>(s1, t, b.tw, view);
-  fft_line<N, -1, 1>(s2, t, b.tw, view);
+  fft_line<N, -1>(s0, t, b.tw + N, view);
+  fft_line<N, -1>(s1, t, b.tw + N, view);
+  fft_line<N, -1>(s2, t, b.tw + N, view);
 #pragma unroll
   for (int m = 0; m < 8; ++m) {
     const int n = t + T * m;
@@ -572,7 +603,7 @@ __global__ void __launch_bounds__((N / 8) * W) k3_fwd1(Geo g, StepBufs<R> b) {
         else if (f == 4) v[m] = cmuli(C{kzr * s0[m].x - kxr * s2[m].x, kzr * s0[m].y - kxr * s2[m].y});
         else v[m] = cmuli(C{kxr * s1[m].x - kyr * s0[m].x, kxr * s1[m].y - kyr * s0[m].y});
       }
-      fft_line<N, +1, 1>(v, t, b.tw, view);
+      fft_line<N, +1>(v, t, b.tw + N, view);
       if (valid) {
 #pragma unroll
         for (int m = 0; m < 8; ++m) b.zb[f * g.zb_f + (long long)(t + T * m) * plane + col] = v[m];
@@ -621,7 +652,7 @@ __global__ void __launch_bounds__((N / 8) * W) k2_inv1(Geo g, const typename Cpl
       else if (f == 2) v[m] = cmuli(cscale(wv[m], kxr));
       else v[m] = cmuli(cscale(wv[m], kyr));
     }
-    fft_line<N, +1, 1>(v, t, tw, view);
+    fft_line<N, +1>(v, t, tw + N, view);
     if (valid) {
 #pragma unroll
       for (int m = 0; m < 8; ++m) yb[f * g.yb_f + (long long)(t + T * m) * g.hs + kx] = v[m];
@@ -648,7 +679,7 @@ __global__ void __launch_bounds__((N / 16) * L) k2_xpass(Geo g, typename CplxOf<
     C v[8];
 #pragma unroll
     for (int m = 0; m < 8; ++m) v[m] = c2r_pre<C, N>(S + l * SL, t + TX * m, tw);
-    fft_line<H, +1, 2>(v, t, tw, view);
+    fft_line<H, +1>(v, t, tw + N + stage_tw_len(N), view);
 #pragma unroll
     for (int m = 0; m < 8; ++m) {
       if (f == 0) ux[m] = v[m];
@@ -657,7 +688,7 @@ __global__ void __launch_bounds__((N / 16) * L) k2_xpass(Geo g, typename CplxOf<
       else nn[m] = pfms(uy[m], v[m], nn[m]);
     }
   }
-  fft_line<H, -1, 2>(nn, t, tw, view);
+  fft_line<H, -1>(nn, t, tw + N + stage_tw_len(N), view);
   emit_r2c<C, N, L>(nn, t, l, S, yb, line0, g.h, g.hs, tw);
 }
 
@@ -683,7 +714,7 @@ __global__ void __launch_bounds__(32 * WPB) k2_xpass_w(Geo g, typename CplxOf<R>
 #pragma unroll
     for (int m = 0; m < 8; ++m) v[m] = c2r_pre_reg<C, N, TX>(xn, m, t, tw);
     if (f < 3) load_line<C, TX>(xn, src + (f + 1) * g.yb_f, t, g.h);
-    fft_line<H, +1, 2, C, SmLine<C>, SYNC_WARP>(v, t, tw, view);
+    fft_line<H, +1, C, SmLine<C>, SYNC_WARP>(v, t, tw + N + stage_tw_len(N), view);
 #pragma unroll
     for (int m = 0; m < 8; ++m) {
       if (f == 0) ux[m] = v[m];
@@ -692,7 +723,7 @@ __global__ void __launch_bounds__(32 * WPB) k2_xpass_w(Geo g, typename CplxOf<R>
       else nn[m] = pfms(uy[m], v[m], nn[m]);
     }
   }
-  fft_line<H, -1, 2, C, SmLine<C>, SYNC_WARP>(nn, t, tw, view);
+  fft_line<H, -1, C, SmLine<C>, SYNC_WARP>(nn, t, tw + N + stage_tw_len(N), view);
   C *dst = yb + line * g.hs;
 #pragma unroll
   for (int m = 0; m < 8; ++m) {
@@ -718,7 +749,7 @@ __global__ void __launch_bounds__((N / 8) * W) k2_fwd1(Geo g, StepBufs<R> b) {
   C s[8];
 #pragma unroll
   for (int m = 0; m < 8; ++m) s[m] = valid ? b.yb[(long long)(t + T * m) * g.hs + kx] : czero<C>();
-  fft_line<N, -1, 1>(s, t, b.tw, view);
+  fft_line<N, -1>(s, t, b.tw + N, view);
 #pragma unroll
   for (int m = 0; m < 8; ++m) {
     const int n = t + T * m;
@@ -747,7 +778,7 @@ __global__ void __launch_bounds__((N / 8) * W) k2_fwd1(Geo g, StepBufs<R> b) {
         else if (f == 2) v[m] = cmuli(cscale(s[m], kxr));
         else v[m] = cmuli(cscale(s[m], kyr));
       }
-      fft_line<N, +1, 1>(v, t, b.tw, view);
+      fft_line<N, +1>(v, t, b.tw + N, view);
       if (valid) {
 #pragma unroll
         for (int m = 0; m < 8; ++m) b.yb[f * g.yb_f + (long long)(t + T * m) * g.hs + kx] = v[m];
@@ -774,7 +805,7 @@ __global__ void __launch_bounds__((N / 16) * L) k_xfwd_real(Geo g, const double 
     const double2 p = row[t + TX * m];
     v[m] = C{(R)p.x, (R)p.y};
   }
-  fft_line<H, -1, 2>(v, t, tw, SmLine<C>{S + l * SL});
+  fft_line<H, -1>(v, t, tw + N + stage_tw_len(N), SmLine<C>{S + l * SL});
   emit_r2c<C, N, L>(v, t, l, S, dst, line0, g.h, g.hs, tw);
 }
 
@@ -793,7 +824,7 @@ __global__ void __launch_bounds__((N / 16) * L) k_xinv_real(Geo g, const typenam
   C v[8];
 #pragma unroll
   for (int m = 0; m < 8; ++m) v[m] = c2r_pre<C, N>(S + l * SL, t + TX * m, tw);
-  fft_line<H, +1, 2>(v, t, tw, SmLine<C>{S + l * SL});
+  fft_line<H, +1>(v, t, tw + N + stage_tw_len(N), SmLine<C>{S + l * SL});
   double2 *row = reinterpret_cast<double2 *>(phys + (line0 + l) * N);
 #pragma unroll
   for (int m = 0; m < 8; ++m) row[t + TX * m] = make_double2((double)v[m].x, (double)v[m].y);
@@ -868,7 +899,7 @@ struct Launch3 {
         break;
       }
       case OP_INV2:
-        k3_inv2<R, N, WL><<<dim3(g.hs / WL, N, a.nf), T * WL, SM_L, s>>>(g, (const C *)a.zb, (C *)a.yb, tw);
+        k3_inv2<R, N, WL><<<dim3(g.hs / WL, N), T * WL, SM_L, s>>>(g, a.nf, (const C *)a.zb, (C *)a.yb, tw);
         break;
       case OP_XPASS:
         if constexpr (XW) {
@@ -879,7 +910,7 @@ struct Launch3 {
         }
         break;
       case OP_FWD2:
-        k3_fwd2<R, N, WL><<<dim3(g.hs / WL, N, a.nf), T * WL, SM_L, s>>>(g, (const C *)a.yb, (C *)a.zb, tw);
+        k3_fwd2<R, N, WL><<<dim3(g.hs / WL, N), T * WL, SM_L, s>>>(g, a.nf, (const C *)a.yb, (C *)a.zb, tw);
         break;
       case OP_FWD1: {
         const dim3 grid(g.c * (g.hs / WH));
