@@ -62,7 +62,7 @@ struct ns_state {
   int dev = 0;
   ns_grid grid{};
   Geo g{};
-  int prec = 0, ncomp = 1, nbins = 0;
+  int prec = 0, ncomp = 1, nbins = 0, nsm = 1;
   size_t cs = 8;  // bytes per complex element
   double nu = 0, dt = 0;
   cudaStream_t own = nullptr, stream = nullptr, cap = nullptr;
@@ -134,6 +134,7 @@ Args base_args(ns_state *s) {
   a.zb = s->zb;
   a.yb = s->yb;
   a.dt = s->dt;
+  a.nsm = s->nsm;
   return a;
 }
 
@@ -326,6 +327,8 @@ int ns_init(ns_state **out, const ns_grid *grid, double nu, double dt, const dou
     delete s;
     return fail(nullptr, NS_ECUDA, "ns_init: no CUDA device: %s", cudaGetErrorString(e));
   }
+  cudaDeviceGetAttribute(&s->nsm, cudaDevAttrMultiProcessorCount, s->dev);
+  if (s->nsm < 1) s->nsm = 1;
   s->grid = *grid;
   s->prec = grid->precision;
   s->ncomp = grid->dim == 3 ? 3 : 1;

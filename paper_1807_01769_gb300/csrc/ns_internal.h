@@ -52,6 +52,7 @@ struct Args {
   int mode;    // OP_FWD1
   int inv;     // OP_FWD1: 1 = fuse the next stage's first inverse axis
   double dt;
+  int nsm;     // streaming multiprocessors of the device (persistent grids)
 };
 
 // Launch op for the given precision; returns a cudaError_t value (0 = ok) or

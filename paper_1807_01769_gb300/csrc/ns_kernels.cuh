@@ -153,9 +153,30 @@ __device__ __forceinline__ C shfl_partner(const C (&x)[8], int m, int t) {
   return C{__shfl_sync(0xffffffffu, send.x, src, TX), __shfl_sync(0xffffffffu, send.y, src, TX)};
 }
 
-// c2r pre-processing from registers (see c2r_pre); x[m] = X[t + TX m].
+// exp(-2 pi i m / 16), m = 0..7: with TX = N/16 lanes per line,
+// exp(-2 pi i (t + TX m) / N) = exp(-2 pi i t / N) * exp(-2 pi i m / 16).
+template <typename C>
+__device__ __forceinline__ C w16(int m) {
+  using R = decltype(C{}.x);
+  const R c1 = (R)0.92387953251128675612818318939678828682;  // cos(pi/8)
+  const R s1 = (R)0.38268343236508977172845998403039886676;  // sin(pi/8)
+  const R h = (R)0.70710678118654752440084436210484903928;   // cos(pi/4)
+  switch (m) {
+    case 0: return C{(R)1, (R)0};
+    case 1: return C{c1, -s1};
+    case 2: return C{h, -h};
+    case 3: return C{s1, -c1};
+    case 4: return C{(R)0, (R)-1};
+    case 5: return C{-s1, -c1};
+    case 6: return C{-h, -h};
+    default: return C{-c1, -s1};
+  }
+}
+
+// c2r pre-processing from registers (see c2r_pre); x[m] = X[t + TX m];
+// wt = exp(-2 pi i t / N).
 template <typename C, int N, int TX>
-__device__ __forceinline__ C c2r_pre_reg(const C (&x)[8], int m, int t, const C *__restrict__ tw) {
+__device__ __forceinline__ C c2r_pre_reg(const C (&x)[8], int m, int t, C wt) {
   const int k = t + TX * m;
   C xk = x[m];
   C xm = shfl_partner<TX>(x, m, t);
@@ -165,20 +186,20 @@ __device__ __forceinline__ C c2r_pre_reg(const C (&x)[8], int m, int t, const C 
   }
   const C a = cadd(xk, cconj(xm));
   const C b = csub(xk, cconj(xm));
-  const C e = cconj(__ldg(tw + k));
+  const C e = cconj(cmul(wt, w16<C>(m)));
   return cadd(a, cmuli(cmul(e, b)));
 }
 
-// r2c post-processing from registers (see r2c_post); z[m] = Z[t + TX m].
+// r2c post-processing from registers (see r2c_post); z[m] = Z[t + TX m];
+// wt = exp(-2 pi i t / N).
 template <typename C, int N, int TX>
-__device__ __forceinline__ C r2c_post_reg(const C (&z)[8], int m, int t, const C *__restrict__ tw) {
+__device__ __forceinline__ C r2c_post_reg(const C (&z)[8], int m, int t, C wt) {
   using R = decltype(C{}.x);
-  const int k = t + TX * m;
   const C zk = z[m];
   const C zm = shfl_partner<TX>(z, m, t);
   const C a = cadd(zk, cconj(zm));
   const C b = csub(zk, cconj(zm));
-  const C e = __ldg(tw + k);
+  const C e = cmul(wt, w16<C>(m));
   const C r = csub(a, cmuli(cmul(e, b)));
   return C{(R)0.5 * r.x, (R)0.5 * r.y};
 }
@@ -378,6 +399,7 @@ __global__ void __launch_bounds__(32 * WPB, 16 / WPB) k3_xpass_w(Geo g, typename
   const SmLine<C> view{wsm + sub * SL};
   C *park = wsm + LPW * SL + lane;  // park[(a * 8 + m) * 32]
   const C *src = yb + line * g.hs;
+  const C wt = __ldg(tw + t);
   C xn[8];
   load_line<C, TX>(xn, src, t, g.h);
   C nx[8], ny[8], nz[8];
@@ -385,7 +407,7 @@ __global__ void __launch_bounds__(32 * WPB, 16 / WPB) k3_xpass_w(Geo g, typename
   for (int f = 0; f < 6; ++f) {
     C v[8];
 #pragma unroll
-    for (int m = 0; m < 8; ++m) v[m] = c2r_pre_reg<C, N, TX>(xn, m, t, tw);
+    for (int m = 0; m < 8; ++m) v[m] = c2r_pre_reg<C, N, TX>(xn, m, t, wt);
     if (f < 5) load_line<C, TX>(xn, src + (f + 1) * g.yb_f, t, g.h);  // prefetch the next field
     fft_line<H, +1, C, SmLine<C>, SYNC_WARP>(v, t, tw + N + stage_tw_len(N), view);
     if (f < 3) {
@@ -423,7 +445,7 @@ __global__ void __launch_bounds__(32 * WPB, 16 / WPB) k3_xpass_w(Geo g, typename
     C *dst = yb + gg * g.yb_f + line * g.hs;
 #pragma unroll
     for (int m = 0; m < 8; ++m) {
-      const C x = r2c_post_reg<C, N, TX>(v, m, t, tw);
+      const C x = r2c_post_reg<C, N, TX>(v, m, t, wt);
       const int k = t + TX * m;
       if (k < g.h) dst[k] = x;
     }
@@ -520,93 +542,171 @@ __device__ __forceinline__ C rk_update(C nv, long long idx, int k2, const StepBu
   }
 }
 
+// Asynchronous global -> shared copies of BYTES (4, 8 or 16); a false
+// predicate zero-fills the destination without reading the source.
+__device__ __forceinline__ unsigned smem_addr(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+template <int BYTES>
+__device__ __forceinline__ void cp_async(void *dst_smem, const void *src, bool pred) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;\n" ::"r"(smem_addr(dst_smem)), "l"(src), "n"(BYTES),
+               "r"(pred ? BYTES : 0)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+// Lawson IF-RK4 stage update for one mode with its operands already loaded
+// (uu = state, a = accumulator; see rk_update); writes acc / u / dst at gi.
+template <int MODE, typename C, typename R>
+__device__ __forceinline__ C rk_stage(C nv, C uu, C a, int k2, const StepBufs<R> &b, long long gi) {
+  if (MODE == MODE_RK1) {
+    const R e = __ldg(b.ef + k2), e2 = __ldg(b.ef2 + k2);
+    const R c1 = b.dt * e / (R)6;
+    b.acc[gi] = C{e * uu.x + c1 * nv.x, e * uu.y + c1 * nv.y};
+    const R h = b.dt / (R)2;
+    return C{e2 * (uu.x + h * nv.x), e2 * (uu.y + h * nv.y)};
+  } else if (MODE == MODE_RK2) {
+    const R e2 = __ldg(b.ef2 + k2);
+    const R c2 = b.dt * e2 / (R)3;
+    b.acc[gi] = C{a.x + c2 * nv.x, a.y + c2 * nv.y};
+    const R h = b.dt / (R)2;
+    return C{e2 * uu.x + h * nv.x, e2 * uu.y + h * nv.y};
+  } else if (MODE == MODE_RK3) {
+    const R e = __ldg(b.ef + k2), e2 = __ldg(b.ef2 + k2);
+    const R c2 = b.dt * e2 / (R)3;
+    b.acc[gi] = C{a.x + c2 * nv.x, a.y + c2 * nv.y};
+    const R c3 = b.dt * e2;
+    return C{e * uu.x + c3 * nv.x, e * uu.y + c3 * nv.y};
+  } else if (MODE == MODE_RK4) {
+    const R c4 = b.dt / (R)6;
+    const C un = C{a.x + c4 * nv.x, a.y + c4 * nv.y};
+    b.u[gi] = un;
+    return un;
+  } else {
+    b.dst[gi] = nv;
+    return czero<C>();
+  }
+}
+
+// Slots of a column thread that can hold a retained wavenumber: n = t + (N/8) m
+// is retained only for m in {0, 1, 2, 5, 6, 7} (kc < 3N/8 and N - kc > 5N/8),
+// packed as j = 0..5.
+__host__ __device__ constexpr int rk_slot(int m) { return m < 3 ? m : m - 2; }
+
 // fwd1 (3D): z forward of the three product fields, dealias, 1/N^3, projection,
 // forcing, RK stage; INV: curl + z inverse of the next stage input into zb.
+// Persistent: each block walks the column tiles (ky row, W kx columns) with
+// stride gridDim.x.  At the start of a tile the RK operands (u and/or acc) of
+// its retained modes are copied with cp.async into thread-private shared slots
+// [operand][comp][6][threads]; they land while the three forward transforms run.
 template <typename R, int N, int W, int MODE, bool INV>
 __global__ void __launch_bounds__((N / 8) * W) k3_fwd1(Geo g, StepBufs<R> b) {
   using C = typename CplxOf<R>::T;
   constexpr int T = N / 8;
   constexpr int P = pitch_of(W, sizeof(C));
+  constexpr int NT = T * W;
+  constexpr bool NEED_U = MODE == MODE_RK1 || MODE == MODE_RK2 || MODE == MODE_RK3;
+  constexpr bool NEED_ACC = MODE == MODE_RK2 || MODE == MODE_RK3 || MODE == MODE_RK4;
   C *sm = dyn_smem<C>();
+  C *rku = sm + N * P;        // [3][6][NT]
+  C *rka = rku + 18 * NT;     // [3][6][NT]
   const int w = threadIdx.x % W, t = threadIdx.x / W;
   const int nkt = g.hs / W;
-  const int iy = blockIdx.x / nkt;
-  const int kx = (blockIdx.x % nkt) * W + w;
-  const bool valid = kx < g.h;
-  const int ky = ktr_of(iy, g.kc, g.c);
-  const R kxr = (R)kx, kyr = (R)ky;
+  const int ntiles = g.c * nkt;
   const long long plane = (long long)g.c * g.hs;
-  const long long col = (long long)iy * g.hs + kx;
   const long long st = g.st_comp;
   const SmCol<C> view{sm + w, P};
   const R scale = (R)1 / ((R)N * (R)N * (R)N);
-  // all three fields' loads are issued before the first transform
-  C s0[8], s1[8], s2[8];
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int iy = tile / nkt;
+    const int kx = (tile % nkt) * W + w;
+    const bool valid = kx < g.h;
+    const int ky = ktr_of(iy, g.kc, g.c);
+    const R kxr = (R)kx, kyr = (R)ky;
+    const long long col = (long long)iy * g.hs + kx;
+    C s0[8], s1[8], s2[8];
 #pragma unroll
-  for (int m = 0; m < 8; ++m) {
-    const long long off = (long long)(t + T * m) * plane + col;
-    s0[m] = valid ? b.zb[off] : czero<C>();
-    s1[m] = valid ? b.zb[g.zb_f + off] : czero<C>();
-    s2[m] = valid ? b.zb[2 * g.zb_f + off] : czero<C>();
-  }
-  fft_line<N, -1>(s0, t, b.tw + N, view);
-  fft_line<N, -1>(s1, t, b.tw + N, view);
-  fft_line<N, -1>(s2, t, b.tw + N, view);
-#pragma unroll
-  for (int m = 0; m < 8; ++m) {
-    const int n = t + T * m;
-    if (!valid || !retained(n, N, g.kc)) {
-      s0[m] = s1[m] = s2[m] = czero<C>();
-      continue;
+    for (int m = 0; m < 8; ++m) {
+      const long long off = (long long)(t + T * m) * plane + col;
+      s0[m] = valid ? b.zb[off] : czero<C>();
+      s1[m] = valid ? b.zb[g.zb_f + off] : czero<C>();
+      s2[m] = valid ? b.zb[2 * g.zb_f + off] : czero<C>();
     }
-    const int kz = kfull_of(n, N, g.kc);
-    const R kzr = (R)kz;
-    const int k2 = kx * kx + ky * ky + kz * kz;
-    C ax = cscale(s0[m], scale), ay = cscale(s1[m], scale), az = cscale(s2[m], scale);
-    if (k2 == 0) {
-      ax = ay = az = czero<C>();
-    } else {
-      const R inv = (R)1 / (R)k2;
-      const C kd = C{(kxr * ax.x + kyr * ay.x + kzr * az.x) * inv, (kxr * ax.y + kyr * ay.y + kzr * az.y) * inv};
-      ax = C{ax.x - kxr * kd.x, ax.y - kxr * kd.y};
-      ay = C{ay.x - kyr * kd.x, ay.y - kyr * kd.y};
-      az = C{az.x - kzr * kd.x, az.y - kzr * kd.y};
-    }
-    const long long idx = (long long)compact_of(n, N, g.kc, g.c) * plane + col;
-    if (MODE != MODE_PROJ && b.F != nullptr) {
-      ax = cadd(ax, b.F[idx]);
-      ay = cadd(ay, b.F[st + idx]);
-      az = cadd(az, b.F[2 * st + idx]);
-    }
-    StepBufs<R> b1 = b;
-    b1.u += st;
-    b1.acc += st;
-    b1.dst += st;
-    StepBufs<R> b2 = b1;
-    b2.u += st;
-    b2.acc += st;
-    b2.dst += st;
-    s0[m] = rk_update<MODE>(ax, idx, k2, b);
-    s1[m] = rk_update<MODE>(ay, idx, k2, b1);
-    s2[m] = rk_update<MODE>(az, idx, k2, b2);
-  }
-  if (INV) {
-    for (int f = 0; f < 6; ++f) {
-      C v[8];
+    if (NEED_U || NEED_ACC) {
 #pragma unroll
       for (int m = 0; m < 8; ++m) {
-        const R kzr = (R)kfull_of(t + T * m, N, g.kc);
-        if (f == 0) v[m] = s0[m];
-        else if (f == 1) v[m] = s1[m];
-        else if (f == 2) v[m] = s2[m];
-        else if (f == 3) v[m] = cmuli(C{kyr * s2[m].x - kzr * s1[m].x, kyr * s2[m].y - kzr * s1[m].y});
-        else if (f == 4) v[m] = cmuli(C{kzr * s0[m].x - kxr * s2[m].x, kzr * s0[m].y - kxr * s2[m].y});
-        else v[m] = cmuli(C{kxr * s1[m].x - kyr * s0[m].x, kxr * s1[m].y - kyr * s0[m].y});
-      }
-      fft_line<N, +1>(v, t, b.tw + N, view);
-      if (valid) {
+        if (m == 3 || m == 4) continue;
+        const int n = t + T * m;
+        const bool ok = valid && retained(n, N, g.kc);
+        const long long idx = ok ? (long long)compact_of(n, N, g.kc, g.c) * plane + col : 0;
 #pragma unroll
-        for (int m = 0; m < 8; ++m) b.zb[f * g.zb_f + (long long)(t + T * m) * plane + col] = v[m];
+        for (int c = 0; c < 3; ++c) {
+          const int slot = (c * 6 + rk_slot(m)) * NT + threadIdx.x;
+          if (NEED_U) cp_async<sizeof(C)>(rku + slot, b.u + c * st + idx, ok);
+          if (NEED_ACC) cp_async<sizeof(C)>(rka + slot, b.acc + c * st + idx, ok);
+        }
+      }
+      cp_async_commit();
+    }
+    fft_line<N, -1>(s0, t, b.tw + N, view);
+    fft_line<N, -1>(s1, t, b.tw + N, view);
+    fft_line<N, -1>(s2, t, b.tw + N, view);
+    if (NEED_U || NEED_ACC) cp_async_wait_all();
+#pragma unroll
+    for (int m = 0; m < 8; ++m) {
+      const int n = t + T * m;
+      if (m == 3 || m == 4 || !valid || !retained(n, N, g.kc)) {
+        s0[m] = s1[m] = s2[m] = czero<C>();
+        continue;
+      }
+      const int kz = kfull_of(n, N, g.kc);
+      const R kzr = (R)kz;
+      const int k2 = kx * kx + ky * ky + kz * kz;
+      C ax = cscale(s0[m], scale), ay = cscale(s1[m], scale), az = cscale(s2[m], scale);
+      if (k2 == 0) {
+        ax = ay = az = czero<C>();
+      } else {
+        const R inv = (R)1 / (R)k2;
+        const C kd = C{(kxr * ax.x + kyr * ay.x + kzr * az.x) * inv, (kxr * ax.y + kyr * ay.y + kzr * az.y) * inv};
+        ax = C{ax.x - kxr * kd.x, ax.y - kxr * kd.y};
+        ay = C{ay.x - kyr * kd.x, ay.y - kyr * kd.y};
+        az = C{az.x - kzr * kd.x, az.y - kzr * kd.y};
+      }
+      const long long idx = (long long)compact_of(n, N, g.kc, g.c) * plane + col;
+      if (MODE != MODE_PROJ && b.F != nullptr) {
+        ax = cadd(ax, b.F[idx]);
+        ay = cadd(ay, b.F[st + idx]);
+        az = cadd(az, b.F[2 * st + idx]);
+      }
+      C nv[3] = {ax, ay, az};
+      C out[3];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const int slot = (c * 6 + rk_slot(m)) * NT + threadIdx.x;
+        const long long gi = c * st + idx;
+        out[c] = rk_stage<MODE>(nv[c], NEED_U ? rku[slot] : czero<C>(), NEED_ACC ? rka[slot] : czero<C>(), k2, b, gi);
+      }
+      s0[m] = out[0];
+      s1[m] = out[1];
+      s2[m] = out[2];
+    }
+    if (INV) {
+      for (int f = 0; f < 6; ++f) {
+        C v[8];
+#pragma unroll
+        for (int m = 0; m < 8; ++m) {
+          const R kzr = (R)kfull_of(t + T * m, N, g.kc);
+          if (f == 0) v[m] = s0[m];
+          else if (f == 1) v[m] = s1[m];
+          else if (f == 2) v[m] = s2[m];
+          else if (f == 3) v[m] = cmuli(C{kyr * s2[m].x - kzr * s1[m].x, kyr * s2[m].y - kzr * s1[m].y});
+          else if (f == 4) v[m] = cmuli(C{kzr * s0[m].x - kxr * s2[m].x, kzr * s0[m].y - kxr * s2[m].y});
+          else v[m] = cmuli(C{kxr * s1[m].x - kyr * s0[m].x, kxr * s1[m].y - kyr * s0[m].y});
+        }
+        fft_line<N, +1>(v, t, b.tw + N, view);
+        if (valid) {
+#pragma unroll
+          for (int m = 0; m < 8; ++m) b.zb[f * g.zb_f + (long long)(t + T * m) * plane + col] = v[m];
+        }
       }
     }
   }
@@ -705,6 +805,7 @@ __global__ void __launch_bounds__(32 * WPB) k2_xpass_w(Geo g, typename CplxOf<R>
   const long long line = ((long long)blockIdx.x * WPB + warp) * LPW + sub;
   const SmLine<C> view{S + (warp * LPW + sub) * SL};
   const C *src = yb + line * g.hs;
+  const C wt = __ldg(tw + t);
   C xn[8];
   load_line<C, TX>(xn, src, t, g.h);
   C ux[8], uy[8], nn[8];
@@ -712,7 +813,7 @@ __global__ void __launch_bounds__(32 * WPB) k2_xpass_w(Geo g, typename CplxOf<R>
   for (int f = 0; f < 4; ++f) {
     C v[8];
 #pragma unroll
-    for (int m = 0; m < 8; ++m) v[m] = c2r_pre_reg<C, N, TX>(xn, m, t, tw);
+    for (int m = 0; m < 8; ++m) v[m] = c2r_pre_reg<C, N, TX>(xn, m, t, wt);
     if (f < 3) load_line<C, TX>(xn, src + (f + 1) * g.yb_f, t, g.h);
     fft_line<H, +1, C, SmLine<C>, SYNC_WARP>(v, t, tw + N + stage_tw_len(N), view);
 #pragma unroll
@@ -727,7 +828,7 @@ __global__ void __launch_bounds__(32 * WPB) k2_xpass_w(Geo g, typename CplxOf<R>
   C *dst = yb + line * g.hs;
 #pragma unroll
   for (int m = 0; m < 8; ++m) {
-    const C x = r2c_post_reg<C, N, TX>(nn, m, t, tw);
+    const C x = r2c_post_reg<C, N, TX>(nn, m, t, wt);
     const int k = t + TX * m;
     if (k < g.h) dst[k] = x;
   }
@@ -862,6 +963,8 @@ struct Launch3 {
   static constexpr int L = x_lines<R, N>();
   static constexpr size_t SM_L = (size_t)N * pitch_of(WL, sizeof(C)) * sizeof(C);
   static constexpr size_t SM_H = (size_t)N * pitch_of(WH, sizeof(C)) * sizeof(C);
+  // persistent fwd1: exchange tile + RK operand slots (2 operands x 3 comps x 6 per thread)
+  static constexpr size_t SM_F1 = SM_H + (size_t)36 * T * WH * sizeof(C);
   static constexpr size_t SM_X = (size_t)L * smline_len(N / 2) * sizeof(C);
   // warp-per-line x pass when a line fits in one warp
   static constexpr bool XW = N / 16 <= 32;
@@ -883,12 +986,12 @@ struct Launch3 {
         set_smem(k3_xpass<R, N, L>, SM_X);
         set_smem(k_xfwd_real<R, N, L>, SM_X);
         set_smem(k_xinv_real<R, N, L>, SM_X);
-        set_smem(k3_fwd1<R, N, WH, MODE_RK1, true>, SM_H);
-        set_smem(k3_fwd1<R, N, WH, MODE_RK2, true>, SM_H);
-        set_smem(k3_fwd1<R, N, WH, MODE_RK3, true>, SM_H);
-        set_smem(k3_fwd1<R, N, WH, MODE_RK4, true>, SM_H);
-        set_smem(k3_fwd1<R, N, WH, MODE_RHS, false>, SM_H);
-        set_smem(k3_fwd1<R, N, WH, MODE_PROJ, false>, SM_H);
+        set_smem(k3_fwd1<R, N, WH, MODE_RK1, true>, SM_F1);
+        set_smem(k3_fwd1<R, N, WH, MODE_RK2, true>, SM_F1);
+        set_smem(k3_fwd1<R, N, WH, MODE_RK3, true>, SM_F1);
+        set_smem(k3_fwd1<R, N, WH, MODE_RK4, true>, SM_F1);
+        set_smem(k3_fwd1<R, N, WH, MODE_RHS, false>, SM_F1);
+        set_smem(k3_fwd1<R, N, WH, MODE_PROJ, false>, SM_F1);
         break;
       case OP_INV1: {
         const dim3 grid(g.c * (g.hs / WL));
@@ -913,15 +1016,22 @@ struct Launch3 {
         k3_fwd2<R, N, WL><<<dim3(g.hs / WL, N), T * WL, SM_L, s>>>(g, a.nf, (const C *)a.yb, (C *)a.zb, tw);
         break;
       case OP_FWD1: {
-        const dim3 grid(g.c * (g.hs / WH));
+        // persistent: one wave of resident blocks (the kernel walks the tiles)
+        const int tiles = g.c * (g.hs / WH);
+        static int per_sm = 0;
+        if (per_sm == 0) {
+          cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k3_fwd1<R, N, WH, MODE_RK2, true>, T * WH, SM_F1);
+          if (per_sm < 1) per_sm = 1;
+        }
+        const int grid = cmin(tiles, per_sm * (a.nsm > 0 ? a.nsm : 1));
         const StepBufs<R> b = step_bufs<R>(a);
         switch (a.mode) {
-          case MODE_RK1: k3_fwd1<R, N, WH, MODE_RK1, true><<<grid, T * WH, SM_H, s>>>(g, b); break;
-          case MODE_RK2: k3_fwd1<R, N, WH, MODE_RK2, true><<<grid, T * WH, SM_H, s>>>(g, b); break;
-          case MODE_RK3: k3_fwd1<R, N, WH, MODE_RK3, true><<<grid, T * WH, SM_H, s>>>(g, b); break;
-          case MODE_RK4: k3_fwd1<R, N, WH, MODE_RK4, true><<<grid, T * WH, SM_H, s>>>(g, b); break;
-          case MODE_RHS: k3_fwd1<R, N, WH, MODE_RHS, false><<<grid, T * WH, SM_H, s>>>(g, b); break;
-          default: k3_fwd1<R, N, WH, MODE_PROJ, false><<<grid, T * WH, SM_H, s>>>(g, b); break;
+          case MODE_RK1: k3_fwd1<R, N, WH, MODE_RK1, true><<<grid, T * WH, SM_F1, s>>>(g, b); break;
+          case MODE_RK2: k3_fwd1<R, N, WH, MODE_RK2, true><<<grid, T * WH, SM_F1, s>>>(g, b); break;
+          case MODE_RK3: k3_fwd1<R, N, WH, MODE_RK3, true><<<grid, T * WH, SM_F1, s>>>(g, b); break;
+          case MODE_RK4: k3_fwd1<R, N, WH, MODE_RK4, true><<<grid, T * WH, SM_F1, s>>>(g, b); break;
+          case MODE_RHS: k3_fwd1<R, N, WH, MODE_RHS, false><<<grid, T * WH, SM_F1, s>>>(g, b); break;
+          default: k3_fwd1<R, N, WH, MODE_PROJ, false><<<grid, T * WH, SM_F1, s>>>(g, b); break;
         }
         break;
       }
