@@ -140,27 +140,62 @@ __device__ __forceinline__ C twiddle(const C *__restrict__ tw, int j) {
   return DIR < 0 ? w : cconj(w);
 }
 
-// Shared-memory views used for the exchanges between stages.
+// Radix and span of stage s of a length-L transform (host and device).
+__host__ __device__ constexpr int plan_r0(int L) { return 1 << (ilog2(L) % 3); }
+__host__ __device__ constexpr int plan_nst(int L) { return ilog2(L) / 3 + (plan_r0(L) > 1 ? 1 : 0); }
+__host__ __device__ constexpr int plan_radix(int L, int s) { return (s == 0 && plan_r0(L) > 1) ? plan_r0(L) : 8; }
+__host__ __device__ constexpr int plan_span(int L, int s) {
+  return s == 0 ? 1 : (plan_r0(L) > 1 ? plan_r0(L) * (1 << (3 * (s - 1))) : (1 << (3 * s)));
+}
+// Stage twiddle table of a length-L transform: for every stage s >= 1 a block
+// of (R_s - 1) NS_s entries, entry (r - 1) NS_s + j = exp(-2 pi i r j / (NS_s R_s)),
+// so the twiddles of consecutive butterflies j are consecutive in memory (the
+// transform reads the r = 1 row and forms the other powers by products).
+__host__ __device__ constexpr int stage_tw_offset(int L, int s) {
+  return s <= 1 ? 0 : stage_tw_offset(L, s - 1) + (plan_radix(L, s - 1) - 1) * plan_span(L, s - 1);
+}
+__host__ __device__ constexpr int stage_tw_len(int L) { return stage_tw_offset(L, plan_nst(L)); }
+
+// Shared-memory views used for the exchanges between stages.  ld<X>/st<X>
+// address the exchange that follows stage X.
 //   column tile [n][pitch], this thread's column at base
 template <typename C>
 struct SmCol {
   C *base;
   int pitch;
-  __device__ __forceinline__ C ld(int n) const { return base[n * pitch]; }
-  __device__ __forceinline__ void st(int n, C v) const { base[n * pitch] = v; }
+  template <int X>
+  __device__ __forceinline__ C ld(int n) const {
+    return base[n * pitch];
+  }
+  template <int X>
+  __device__ __forceinline__ void st(int n, C v) const {
+    base[n * pitch] = v;
+  }
 };
-//   contiguous line with one pad slot every 8 entries (bank-conflict free
-//   stride-8 writes of the first radix-8 stage)
-template <typename C>
+//   contiguous line of a length-L transform with one pad slot every 8 entries,
+//   or every 16 after a radix-2/4 first stage (its stride-2/4 writes are then
+//   free of bank conflicts; the stride-8 writes of radix-8 stages and the
+//   grouped writes of later stages need the 1-in-8 padding)
+template <typename C, int L = 0>
 struct SmLine {
   C *base;
-  __device__ __forceinline__ C ld(int n) const { return base[n + (n >> 3)]; }
-  __device__ __forceinline__ void st(int n, C v) const { base[n + (n >> 3)] = v; }
+  template <int X>
+  static __device__ __forceinline__ int pad(int n) {
+    return (X == 0 && L > 0 && plan_r0(L) != 1) ? n + (n >> 4) : n + (n >> 3);
+  }
+  template <int X>
+  __device__ __forceinline__ C ld(int n) const {
+    return base[pad<X>(n)];
+  }
+  template <int X>
+  __device__ __forceinline__ void st(int n, C v) const {
+    base[pad<X>(n)] = v;
+  }
 };
 __host__ __device__ constexpr int smline_len(int L) { return L + L / 8; }
 
 // One radix-R stage of span NS on a line of length L (see file header).
-template <int L, int R, int NS, int TWOFF, int DIR, bool LAST, typename C, typename SM>
+template <int L, int R, int NS, int TWOFF, int DIR, bool LAST, int XS, typename C, typename SM>
 __device__ __forceinline__ void fft_stage(C (&v)[8], int t, const C *__restrict__ stw, const SM &sm) {
   constexpr int T = L / 8;
   constexpr int Q = 8 / R;
@@ -171,9 +206,19 @@ __device__ __forceinline__ void fft_stage(C (&v)[8], int t, const C *__restrict_
 #pragma unroll
     for (int r = 0; r < R; ++r) a[r] = v[q + r * Q];
     if (NS > 1) {
-      const C *w = stw + TWOFF + (b % NS);
+      // w^r from one table load, by a product tree of depth <= 3
+      C wp[8];
+      wp[1] = twiddle<DIR>(stw + TWOFF, b % NS);
+      if (R > 2) wp[2] = cmul(wp[1], wp[1]);
+      if (R > 3) wp[3] = cmul(wp[2], wp[1]);
+      if (R > 4) {
+        wp[4] = cmul(wp[2], wp[2]);
+        wp[5] = cmul(wp[4], wp[1]);
+        wp[6] = cmul(wp[4], wp[2]);
+        wp[7] = cmul(wp[4], wp[3]);
+      }
 #pragma unroll
-      for (int r = 1; r < R; ++r) a[r] = cmul(a[r], twiddle<DIR>(w, (r - 1) * NS));
+      for (int r = 1; r < R; ++r) a[r] = cmul(a[r], wp[r]);
     }
     dftR<R, DIR>(a);
     if (LAST) {
@@ -182,25 +227,10 @@ __device__ __forceinline__ void fft_stage(C (&v)[8], int t, const C *__restrict_
     } else {
       const int base = (b / NS) * NS * R + (b % NS);
 #pragma unroll
-      for (int r = 0; r < R; ++r) sm.st(base + r * NS, a[r]);
+      for (int r = 0; r < R; ++r) sm.template st<XS>(base + r * NS, a[r]);
     }
   }
 }
-
-// Radix and span of stage s of a length-L transform (host and device).
-__host__ __device__ constexpr int plan_r0(int L) { return 1 << (ilog2(L) % 3); }
-__host__ __device__ constexpr int plan_nst(int L) { return ilog2(L) / 3 + (plan_r0(L) > 1 ? 1 : 0); }
-__host__ __device__ constexpr int plan_radix(int L, int s) { return (s == 0 && plan_r0(L) > 1) ? plan_r0(L) : 8; }
-__host__ __device__ constexpr int plan_span(int L, int s) {
-  return s == 0 ? 1 : (plan_r0(L) > 1 ? plan_r0(L) * (1 << (3 * (s - 1))) : (1 << (3 * s)));
-}
-// Stage twiddle table of a length-L transform: for every stage s >= 1 a block
-// of (R_s - 1) NS_s entries, entry (r - 1) NS_s + j = exp(-2 pi i r j / (NS_s R_s)),
-// so the twiddles of consecutive butterflies j are consecutive in memory.
-__host__ __device__ constexpr int stage_tw_offset(int L, int s) {
-  return s <= 1 ? 0 : stage_tw_offset(L, s - 1) + (plan_radix(L, s - 1) - 1) * plan_span(L, s - 1);
-}
-__host__ __device__ constexpr int stage_tw_len(int L) { return stage_tw_offset(L, plan_nst(L)); }
 
 template <int L, int S>
 struct StagePlan {
@@ -231,10 +261,10 @@ struct FftRun {
     if (S > 0) {
       fft_sync<SY>();  // the previous stage's shared writes are visible
 #pragma unroll
-      for (int m = 0; m < 8; ++m) v[m] = sm.ld(t + T * m);
+      for (int m = 0; m < 8; ++m) v[m] = sm.template ld<S - 1>(t + T * m);
       if (S < P::NST - 1) fft_sync<SY>();  // everyone read before the next writes
     }
-    fft_stage<L, P::RADIX, P::NS, P::TWOFF, DIR, S == P::NST - 1>(v, t, stw, sm);
+    fft_stage<L, P::RADIX, P::NS, P::TWOFF, DIR, S == P::NST - 1, S>(v, t, stw, sm);
     FftRun<L, S + 1, DIR, SY, C, SM>::next(v, t, stw, sm);
   }
   __device__ __forceinline__ static void next(C (&v)[8], int t, const C *__restrict__ stw, const SM &sm) {

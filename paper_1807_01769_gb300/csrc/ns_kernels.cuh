@@ -42,6 +42,12 @@ template <typename R, int N>
 __host__ __device__ constexpr int w_heavy() {
   return cmin(wmax<R>(), cmax(1, (sizeof(R) == 4 ? 512 : 256) / (N / 8)));
 }
+// columns per tile of the y passes: 512-thread blocks so that two independent
+// blocks share an SM
+template <typename R, int N>
+__host__ __device__ constexpr int w_ypass() {
+  return cmin(wmax<R>(), cmax(1, 512 / (N / 8)));
+}
 // lines per block of the x kernels (N/16 threads per line)
 template <typename R, int N>
 __host__ __device__ constexpr int x_lines() {
@@ -396,7 +402,7 @@ __global__ void __launch_bounds__(32 * WPB, 16 / WPB) k3_xpass_w(Geo g, typename
   const int t = lane % TX, sub = lane / TX;
   const long long line = ((long long)blockIdx.x * WPB + warp) * LPW + sub;
   C *wsm = S + warp * WSM;
-  const SmLine<C> view{wsm + sub * SL};
+  const SmLine<C, N / 2> view{wsm + sub * SL};
   C *park = wsm + LPW * SL + lane;  // park[(a * 8 + m) * 32]
   const C *src = yb + line * g.hs;
   const C wt = __ldg(tw + t);
@@ -409,7 +415,7 @@ __global__ void __launch_bounds__(32 * WPB, 16 / WPB) k3_xpass_w(Geo g, typename
 #pragma unroll
     for (int m = 0; m < 8; ++m) v[m] = c2r_pre_reg<C, N, TX>(xn, m, t, wt);
     if (f < 5) load_line<C, TX>(xn, src + (f + 1) * g.yb_f, t, g.h);  // prefetch the next field
-    fft_line<H, +1, C, SmLine<C>, SYNC_WARP>(v, t, tw + N + stage_tw_len(N), view);
+    fft_line<H, +1, C, SmLine<C, N / 2>, SYNC_WARP>(v, t, tw + N + stage_tw_len(N), view);
     if (f < 3) {
 #pragma unroll
       for (int m = 0; m < 8; ++m) park[(f * 8 + m) * 32] = v[m];
@@ -441,7 +447,7 @@ __global__ void __launch_bounds__(32 * WPB, 16 / WPB) k3_xpass_w(Geo g, typename
     C v[8];
 #pragma unroll
     for (int m = 0; m < 8; ++m) v[m] = gg == 0 ? nx[m] : (gg == 1 ? ny[m] : nz[m]);
-    fft_line<H, -1, C, SmLine<C>, SYNC_WARP>(v, t, tw + N + stage_tw_len(N), view);
+    fft_line<H, -1, C, SmLine<C, N / 2>, SYNC_WARP>(v, t, tw + N + stage_tw_len(N), view);
     C *dst = yb + gg * g.yb_f + line * g.hs;
 #pragma unroll
     for (int m = 0; m < 8; ++m) {
@@ -803,7 +809,7 @@ __global__ void __launch_bounds__(32 * WPB) k2_xpass_w(Geo g, typename CplxOf<R>
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int t = lane % TX, sub = lane / TX;
   const long long line = ((long long)blockIdx.x * WPB + warp) * LPW + sub;
-  const SmLine<C> view{S + (warp * LPW + sub) * SL};
+  const SmLine<C, N / 2> view{S + (warp * LPW + sub) * SL};
   const C *src = yb + line * g.hs;
   const C wt = __ldg(tw + t);
   C xn[8];
@@ -815,7 +821,7 @@ __global__ void __launch_bounds__(32 * WPB) k2_xpass_w(Geo g, typename CplxOf<R>
 #pragma unroll
     for (int m = 0; m < 8; ++m) v[m] = c2r_pre_reg<C, N, TX>(xn, m, t, wt);
     if (f < 3) load_line<C, TX>(xn, src + (f + 1) * g.yb_f, t, g.h);
-    fft_line<H, +1, C, SmLine<C>, SYNC_WARP>(v, t, tw + N + stage_tw_len(N), view);
+    fft_line<H, +1, C, SmLine<C, N / 2>, SYNC_WARP>(v, t, tw + N + stage_tw_len(N), view);
 #pragma unroll
     for (int m = 0; m < 8; ++m) {
       if (f == 0) ux[m] = v[m];
@@ -824,7 +830,7 @@ __global__ void __launch_bounds__(32 * WPB) k2_xpass_w(Geo g, typename CplxOf<R>
       else nn[m] = pfms(uy[m], v[m], nn[m]);
     }
   }
-  fft_line<H, -1, C, SmLine<C>, SYNC_WARP>(nn, t, tw + N + stage_tw_len(N), view);
+  fft_line<H, -1, C, SmLine<C, N / 2>, SYNC_WARP>(nn, t, tw + N + stage_tw_len(N), view);
   C *dst = yb + line * g.hs;
 #pragma unroll
   for (int m = 0; m < 8; ++m) {
@@ -961,7 +967,9 @@ struct Launch3 {
   static constexpr int WL = w_light<R, N>();
   static constexpr int WH = w_heavy<R, N>();
   static constexpr int L = x_lines<R, N>();
+  static constexpr int WY = w_ypass<R, N>();
   static constexpr size_t SM_L = (size_t)N * pitch_of(WL, sizeof(C)) * sizeof(C);
+  static constexpr size_t SM_Y = (size_t)N * pitch_of(WY, sizeof(C)) * sizeof(C);
   static constexpr size_t SM_H = (size_t)N * pitch_of(WH, sizeof(C)) * sizeof(C);
   // persistent fwd1: exchange tile + RK operand slots (2 operands x 3 comps x 6 per thread)
   static constexpr size_t SM_F1 = SM_H + (size_t)36 * T * WH * sizeof(C);
@@ -981,8 +989,8 @@ struct Launch3 {
         if constexpr (XW) set_smem(k3_xpass_w<R, N, XW_WPB>, SM_XW);
         set_smem(k3_inv1<R, N, WL, true>, SM_L);
         set_smem(k3_inv1<R, N, WL, false>, SM_L);
-        set_smem(k3_inv2<R, N, WL>, SM_L);
-        set_smem(k3_fwd2<R, N, WL>, SM_L);
+        set_smem(k3_inv2<R, N, WY>, SM_Y);
+        set_smem(k3_fwd2<R, N, WY>, SM_Y);
         set_smem(k3_xpass<R, N, L>, SM_X);
         set_smem(k_xfwd_real<R, N, L>, SM_X);
         set_smem(k_xinv_real<R, N, L>, SM_X);
@@ -1002,7 +1010,7 @@ struct Launch3 {
         break;
       }
       case OP_INV2:
-        k3_inv2<R, N, WL><<<dim3(g.hs / WL, N), T * WL, SM_L, s>>>(g, a.nf, (const C *)a.zb, (C *)a.yb, tw);
+        k3_inv2<R, N, WY><<<dim3(g.hs / WY, N), T * WY, SM_Y, s>>>(g, a.nf, (const C *)a.zb, (C *)a.yb, tw);
         break;
       case OP_XPASS:
         if constexpr (XW) {
@@ -1013,7 +1021,7 @@ struct Launch3 {
         }
         break;
       case OP_FWD2:
-        k3_fwd2<R, N, WL><<<dim3(g.hs / WL, N), T * WL, SM_L, s>>>(g, a.nf, (const C *)a.yb, (C *)a.zb, tw);
+        k3_fwd2<R, N, WY><<<dim3(g.hs / WY, N), T * WY, SM_Y, s>>>(g, a.nf, (const C *)a.yb, (C *)a.zb, tw);
         break;
       case OP_FWD1: {
         // persistent: one wave of resident blocks (the kernel walks the tiles)
