@@ -157,39 +157,46 @@ __host__ __device__ constexpr int stage_tw_offset(int L, int s) {
 __host__ __device__ constexpr int stage_tw_len(int L) { return stage_tw_offset(L, plan_nst(L)); }
 
 // Shared-memory views used for the exchanges between stages.  ld<X>/st<X>
-// address the exchange that follows stage X.
+// address the exchange that follows stage X.  With DB (double buffer) the
+// exchanges alternate between two buffers bofs elements apart, so a thread
+// may write the next exchange while others still read the previous one: a
+// transform then needs one barrier per exchange instead of two.
 //   column tile [n][pitch], this thread's column at base
-template <typename C>
+template <typename C, bool DBUF = false>
 struct SmCol {
+  static constexpr bool DB = DBUF;
   C *base;
   int pitch;
+  int bofs;
   template <int X>
   __device__ __forceinline__ C ld(int n) const {
-    return base[n * pitch];
+    return base[(DB && (X & 1) ? bofs : 0) + n * pitch];
   }
   template <int X>
   __device__ __forceinline__ void st(int n, C v) const {
-    base[n * pitch] = v;
+    base[(DB && (X & 1) ? bofs : 0) + n * pitch] = v;
   }
 };
 //   contiguous line of a length-L transform with one pad slot every 8 entries,
 //   or every 16 after a radix-2/4 first stage (its stride-2/4 writes are then
 //   free of bank conflicts; the stride-8 writes of radix-8 stages and the
 //   grouped writes of later stages need the 1-in-8 padding)
-template <typename C, int L = 0>
+template <typename C, int L = 0, bool DBUF = false>
 struct SmLine {
+  static constexpr bool DB = DBUF;
   C *base;
+  int bofs;
   template <int X>
   static __device__ __forceinline__ int pad(int n) {
     return (X == 0 && L > 0 && plan_r0(L) != 1) ? n + (n >> 4) : n + (n >> 3);
   }
   template <int X>
   __device__ __forceinline__ C ld(int n) const {
-    return base[pad<X>(n)];
+    return base[(DB && (X & 1) ? bofs : 0) + pad<X>(n)];
   }
   template <int X>
   __device__ __forceinline__ void st(int n, C v) const {
-    base[pad<X>(n)] = v;
+    base[(DB && (X & 1) ? bofs : 0) + pad<X>(n)] = v;
   }
 };
 __host__ __device__ constexpr int smline_len(int L) { return L + L / 8; }
@@ -262,7 +269,8 @@ struct FftRun {
       fft_sync<SY>();  // the previous stage's shared writes are visible
 #pragma unroll
       for (int m = 0; m < 8; ++m) v[m] = sm.template ld<S - 1>(t + T * m);
-      if (S < P::NST - 1) fft_sync<SY>();  // everyone read before the next writes
+      // single buffer: everyone read before the next writes
+      if (!SM::DB && S < P::NST - 1) fft_sync<SY>();
     }
     fft_stage<L, P::RADIX, P::NS, P::TWOFF, DIR, S == P::NST - 1, S>(v, t, stw, sm);
     FftRun<L, S + 1, DIR, SY, C, SM>::next(v, t, stw, sm);
@@ -275,13 +283,17 @@ struct FftRun {
 // Length-L FFT of one line held as v[m] = x[t + T m] (T = L/8) by threads
 // t = 0..T-1.  Every thread of the sync scope (the block, or the warp for
 // SYNC_WARP) must call it; sm is this thread's view of a scratch line of at
-// least L entries.  On return v[m] = X[t + T m],
-// X_k = sum_j x_j exp(DIR 2 pi i j k / L).  stw is the stage twiddle table of
-// length L (stage_tw_len(L) entries, see stage_tw_offset).
+// least L entries (two, bofs apart, for a double-buffered view).  On return
+// v[m] = X[t + T m], X_k = sum_j x_j exp(DIR 2 pi i j k / L).  stw is the
+// stage twiddle table of length L (stage_tw_len(L) entries, see
+// stage_tw_offset).  The leading barrier protects the scratch from the
+// previous transform's last reads; a double-buffered view whose last exchange
+// uses the second buffer does not need it.
 template <int L, int DIR, typename C, typename SM, int SY = SYNC_BLOCK>
 __device__ __forceinline__ void fft_line(C (&v)[8], int t, const C *__restrict__ stw, const SM &sm) {
   static_assert(L >= 8 && (L & (L - 1)) == 0, "power of two >= 8");
-  if (StagePlan<L, 0>::NST > 1) fft_sync<SY>();  // the scratch line is free
+  constexpr int NST = StagePlan<L, 0>::NST;
+  if (NST > 1 && !(SM::DB && ((NST - 2) & 1))) fft_sync<SY>();
   FftRun<L, 0, DIR, SY, C, SM>::run(v, t, stw, sm);
 }
 

@@ -55,6 +55,19 @@ __host__ __device__ constexpr int x_lines() {
 }
 __host__ __device__ constexpr int pitch_of(int W, int csize) { return (W * csize < 128) ? W + 1 : W; }
 
+// Shared memory of a column kernel: the exchange tile [N][pitch], doubled when
+// two copies plus `extra` bytes fit in one block's shared memory.
+constexpr size_t kSmemMax = 232448;
+__host__ __device__ constexpr size_t col_tile_bytes(int N, int W, int csize) {
+  return (size_t)N * pitch_of(W, csize) * csize;
+}
+__host__ __device__ constexpr bool col_db(int N, int W, int csize, size_t extra) {
+  return 2 * col_tile_bytes(N, W, csize) + extra <= kSmemMax;
+}
+__host__ __device__ constexpr size_t col_smem(int N, int W, int csize, size_t extra) {
+  return (col_db(N, W, csize, extra) ? 2 : 1) * col_tile_bytes(N, W, csize) + extra;
+}
+
 template <typename C>
 __device__ __forceinline__ C *dyn_smem() {
   extern __shared__ __align__(16) unsigned char ns_dyn_smem[];
@@ -234,6 +247,7 @@ __global__ void __launch_bounds__((N / 8) * W) k3_inv1(Geo g, const typename Cpl
   using C = typename CplxOf<R>::T;
   constexpr int T = N / 8;
   constexpr int P = pitch_of(W, sizeof(C));
+  constexpr size_t EXTRA_SMEM = 0;
   C *sm = dyn_smem<C>();
   const int w = threadIdx.x % W, t = threadIdx.x / W;
   const int nkt = g.hs / W;
@@ -243,7 +257,8 @@ __global__ void __launch_bounds__((N / 8) * W) k3_inv1(Geo g, const typename Cpl
   const R kxr = (R)kx, kyr = (R)ktr_of(iy, g.kc, g.c);
   const long long plane = (long long)g.c * g.hs;
   const long long col = (long long)iy * g.hs + kx;
-  const SmCol<C> view{sm + w, P};
+  constexpr bool DB = col_db(N, W, sizeof(C), EXTRA_SMEM);
+  const SmCol<C, DB> view{sm + w, P, N * P};
   const long long st = g.st_comp;
   constexpr int NF = CURL ? 6 : 3;
   for (int f = 0; f < NF; ++f) {
@@ -298,6 +313,7 @@ __global__ void __launch_bounds__((N / 8) * W) k3_inv2(Geo g, int nf, const type
   using C = typename CplxOf<R>::T;
   constexpr int T = N / 8;
   constexpr int P = pitch_of(W, sizeof(C));
+  constexpr size_t EXTRA_SMEM = 0;
   C *sm = dyn_smem<C>();
   const int w = threadIdx.x % W, t = threadIdx.x / W;
   const int kx = blockIdx.x * W + w;
@@ -326,7 +342,7 @@ __global__ void __launch_bounds__((N / 8) * W) k3_inv2(Geo g, int nf, const type
 #pragma unroll
       for (int m = 0; m < 8; ++m) xn[m] = live[m] ? nin[(long long)row[m] * g.hs] : czero<C>();
     }
-    fft_line<N, +1>(v, t, tw + N, SmCol<C>{sm + w, P});
+    fft_line<N, +1>(v, t, tw + N, SmCol<C, col_db(N, W, sizeof(C), 0)>{sm + w, P, N * P});
     if (valid) {
       C *o = out + f * g.yb_f;
 #pragma unroll
@@ -467,6 +483,7 @@ __global__ void __launch_bounds__((N / 8) * W) k3_fwd2(Geo g, int nf, const type
   using C = typename CplxOf<R>::T;
   constexpr int T = N / 8;
   constexpr int P = pitch_of(W, sizeof(C));
+  constexpr size_t EXTRA_SMEM = 0;
   C *sm = dyn_smem<C>();
   const int w = threadIdx.x % W, t = threadIdx.x / W;
   const int kx = blockIdx.x * W + w;
@@ -487,7 +504,7 @@ __global__ void __launch_bounds__((N / 8) * W) k3_fwd2(Geo g, int nf, const type
 #pragma unroll
       for (int m = 0; m < 8; ++m) xn[m] = valid ? nin[(long long)(t + T * m) * g.hs] : czero<C>();
     }
-    fft_line<N, -1>(v, t, tw + N, SmCol<C>{sm + w, P});
+    fft_line<N, -1>(v, t, tw + N, SmCol<C, col_db(N, W, sizeof(C), 0)>{sm + w, P, N * P});
     if (valid) {
       C *o = out + f * g.zb_f;
 #pragma unroll
@@ -610,17 +627,22 @@ __global__ void __launch_bounds__((N / 8) * W) k3_fwd1(Geo g, StepBufs<R> b) {
   constexpr int T = N / 8;
   constexpr int P = pitch_of(W, sizeof(C));
   constexpr int NT = T * W;
+  // single exchange tile: the RK operand slots already take most of the
+  // shared memory, and a larger carve-out would shrink the L1 that serves the
+  // table and twiddle loads
+  constexpr size_t EXTRA_SMEM = kSmemMax;  // forces a single buffer below
   constexpr bool NEED_U = MODE == MODE_RK1 || MODE == MODE_RK2 || MODE == MODE_RK3;
   constexpr bool NEED_ACC = MODE == MODE_RK2 || MODE == MODE_RK3 || MODE == MODE_RK4;
   C *sm = dyn_smem<C>();
-  C *rku = sm + N * P;        // [3][6][NT]
+  C *rku = sm + N * P;  // [3][6][NT]
   C *rka = rku + 18 * NT;     // [3][6][NT]
   const int w = threadIdx.x % W, t = threadIdx.x / W;
   const int nkt = g.hs / W;
   const int ntiles = g.c * nkt;
   const long long plane = (long long)g.c * g.hs;
   const long long st = g.st_comp;
-  const SmCol<C> view{sm + w, P};
+  constexpr bool DB = col_db(N, W, sizeof(C), EXTRA_SMEM);
+  const SmCol<C, DB> view{sm + w, P, N * P};
   const R scale = (R)1 / ((R)N * (R)N * (R)N);
   for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const int iy = tile / nkt;
@@ -729,11 +751,13 @@ __global__ void __launch_bounds__((N / 8) * W) k2_inv1(Geo g, const typename Cpl
   using C = typename CplxOf<R>::T;
   constexpr int T = N / 8;
   constexpr int P = pitch_of(W, sizeof(C));
+  constexpr size_t EXTRA_SMEM = 0;
   C *sm = dyn_smem<C>();
   const int w = threadIdx.x % W, t = threadIdx.x / W;
   const int kx = blockIdx.x * W + w;
   const bool valid = kx < g.h;
-  const SmCol<C> view{sm + w, P};
+  constexpr bool DB = col_db(N, W, sizeof(C), EXTRA_SMEM);
+  const SmCol<C, DB> view{sm + w, P, N * P};
   C wv[8];
 #pragma unroll
   for (int m = 0; m < 8; ++m) {
@@ -847,11 +871,13 @@ __global__ void __launch_bounds__((N / 8) * W) k2_fwd1(Geo g, StepBufs<R> b) {
   using C = typename CplxOf<R>::T;
   constexpr int T = N / 8;
   constexpr int P = pitch_of(W, sizeof(C));
+  constexpr size_t EXTRA_SMEM = 0;
   C *sm = dyn_smem<C>();
   const int w = threadIdx.x % W, t = threadIdx.x / W;
   const int kx = blockIdx.x * W + w;
   const bool valid = kx < g.h;
-  const SmCol<C> view{sm + w, P};
+  constexpr bool DB = col_db(N, W, sizeof(C), EXTRA_SMEM);
+  const SmCol<C, DB> view{sm + w, P, N * P};
   const R scale = (R)1 / ((R)N * (R)N);
   C s[8];
 #pragma unroll
@@ -968,11 +994,11 @@ struct Launch3 {
   static constexpr int WH = w_heavy<R, N>();
   static constexpr int L = x_lines<R, N>();
   static constexpr int WY = w_ypass<R, N>();
-  static constexpr size_t SM_L = (size_t)N * pitch_of(WL, sizeof(C)) * sizeof(C);
-  static constexpr size_t SM_Y = (size_t)N * pitch_of(WY, sizeof(C)) * sizeof(C);
-  static constexpr size_t SM_H = (size_t)N * pitch_of(WH, sizeof(C)) * sizeof(C);
-  // persistent fwd1: exchange tile + RK operand slots (2 operands x 3 comps x 6 per thread)
-  static constexpr size_t SM_F1 = SM_H + (size_t)36 * T * WH * sizeof(C);
+  static constexpr size_t SM_L = col_smem(N, WL, sizeof(C), 0);
+  static constexpr size_t SM_Y = col_smem(N, WY, sizeof(C), 0);
+  // persistent fwd1: exchange tile(s) + RK operand slots (2 operands x 3 comps x 6 per thread)
+  static constexpr size_t SM_F1 = col_tile_bytes(N, WH, sizeof(C)) + (size_t)36 * T * WH * sizeof(C);
+  static_assert(SM_F1 <= kSmemMax, "fwd1 shared memory");
   static constexpr size_t SM_X = (size_t)L * smline_len(N / 2) * sizeof(C);
   // warp-per-line x pass when a line fits in one warp
   static constexpr bool XW = N / 16 <= 32;
@@ -1065,8 +1091,8 @@ struct Launch2 {
   static constexpr int WL = w_light<R, N>();
   static constexpr int WH = w_heavy<R, N>();
   static constexpr int L = x_lines<R, N>();
-  static constexpr size_t SM_L = (size_t)N * pitch_of(WL, sizeof(C)) * sizeof(C);
-  static constexpr size_t SM_H = (size_t)N * pitch_of(WH, sizeof(C)) * sizeof(C);
+  static constexpr size_t SM_L = col_smem(N, WL, sizeof(C), 0);
+  static constexpr size_t SM_H = col_smem(N, WH, sizeof(C), 0);
   static constexpr size_t SM_X = (size_t)L * smline_len(N / 2) * sizeof(C);
   static constexpr int XW_WPB = 4;
   static constexpr int XW_LPW = N / 16 <= 32 ? 32 / (N / 16) : 1;
