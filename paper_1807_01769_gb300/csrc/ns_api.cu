@@ -15,6 +15,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdarg>
+#include <cstdlib>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -73,6 +74,12 @@ struct ns_state {
   long long bytes = 0;
   bool zvalid = false;
   cudaGraphExec_t graph = nullptr;
+  // 3D step schedule: the y inverse, x pass and y forward of a stage run as a
+  // pipeline over zchunks plane chunks on three forked streams, the y inverse
+  // at most zlook chunks ahead of the x pass
+  int zchunks = 1, zlook = 2;
+  cudaStream_t pipe[3] = {nullptr, nullptr, nullptr};
+  std::vector<cudaEvent_t> pev;  // [3][zchunks] + 1
   std::string err;
 };
 
@@ -185,11 +192,53 @@ int run_launches(ns_state *s, const std::vector<Launch> &v, cudaStream_t st) {
   return NS_OK;
 }
 
+// Capture of one step with the plane-chunk pipeline (3D, zchunks > 1).
+int capture_pipelined_step(ns_state *s) {
+  const int K = s->zchunks, D = s->zlook, N = s->grid.n, nzc = N / K;
+  cudaEvent_t *evA = s->pev.data(), *evB = evA + K, *evC = evB + K, start = evC[K];
+  for (int st = 1; st <= 4; ++st) {
+    NS_CK(s, cudaEventRecord(start, s->cap));
+    for (int i = 0; i < 3; ++i) NS_CK(s, cudaStreamWaitEvent(s->pipe[i], start, 0));
+    for (int c = 0; c < K; ++c) {
+      Args a = base_args(s);
+      a.z0 = c * nzc;
+      a.nz = nzc;
+      int rc;
+      if (c >= D) NS_CK(s, cudaStreamWaitEvent(s->pipe[0], evB[c - D], 0));
+      Args b = a;
+      b.nf = 6;
+      if ((rc = dispatch(s, nsk::OP_INV2, b, s->pipe[0]))) return rc;
+      NS_CK(s, cudaEventRecord(evA[c], s->pipe[0]));
+      NS_CK(s, cudaStreamWaitEvent(s->pipe[1], evA[c], 0));
+      if ((rc = dispatch(s, nsk::OP_XPASS, a, s->pipe[1]))) return rc;
+      NS_CK(s, cudaEventRecord(evB[c], s->pipe[1]));
+      NS_CK(s, cudaStreamWaitEvent(s->pipe[2], evB[c], 0));
+      b.nf = 3;
+      if ((rc = dispatch(s, nsk::OP_FWD2, b, s->pipe[2]))) return rc;
+      NS_CK(s, cudaEventRecord(evC[c], s->pipe[2]));
+    }
+    NS_CK(s, cudaStreamWaitEvent(s->cap, evA[K - 1], 0));
+    NS_CK(s, cudaStreamWaitEvent(s->cap, evB[K - 1], 0));
+    NS_CK(s, cudaStreamWaitEvent(s->cap, evC[K - 1], 0));
+    Args f = base_args(s);
+    f.mode = st;
+    f.inv = 1;
+    int rc = dispatch(s, nsk::OP_FWD1, f, s->cap);
+    if (rc) return rc;
+  }
+  return NS_OK;
+}
+
 int build_graph(ns_state *s) {
   if (s->graph) return NS_OK;
-  std::vector<Launch> v = step_launches(s);
   NS_CK(s, cudaStreamBeginCapture(s->cap, cudaStreamCaptureModeThreadLocal));
-  int rc = run_launches(s, v, s->cap);
+  int rc;
+  if (s->grid.dim == 3 && s->zchunks > 1) {
+    rc = capture_pipelined_step(s);
+  } else {
+    std::vector<Launch> v = step_launches(s);
+    rc = run_launches(s, v, s->cap);
+  }
   cudaGraph_t graph = nullptr;
   cudaError_t e = cudaStreamEndCapture(s->cap, &graph);
   if (rc) {
@@ -253,7 +302,17 @@ void free_all(ns_state *s) {
     if (p) cudaFree(p);
   if (s->own) cudaStreamDestroy(s->own);
   if (s->cap) cudaStreamDestroy(s->cap);
+  for (cudaStream_t p : s->pipe)
+    if (p) cudaStreamDestroy(p);
+  for (cudaEvent_t e : s->pev)
+    if (e) cudaEventDestroy(e);
 }
+
+// Plane chunks of the 3D y-x-y pipeline.
+// Measured on GB300 at 512^3: one chunk (no pipelining) is fastest, because
+// every pass fills the SMs on its own and the x pass is bound by its shared
+// memory traffic rather than by where its inputs come from.
+int default_zchunks(int) { return 1; }
 
 template <typename R>
 void fill_tables(const ns_state *s, std::vector<unsigned char> &tw, std::vector<unsigned char> &ef,
@@ -366,6 +425,21 @@ int ns_init(ns_state **out, const ns_grid *grid, double nu, double dt, const dou
   INIT_CK(cudaStreamCreateWithFlags(&s->own, cudaStreamDefault));
   INIT_CK(cudaStreamCreateWithFlags(&s->cap, cudaStreamNonBlocking));
   s->stream = s->own;
+  if (g.dim == 3 && g.N >= 128) {
+    s->zchunks = default_zchunks(g.N);
+    s->zlook = 2;
+    if (const char *v = std::getenv("NS_ZCHUNKS")) s->zchunks = std::atoi(v);
+    if (const char *v = std::getenv("NS_ZLOOKAHEAD")) s->zlook = std::atoi(v);
+    if (s->zchunks < 1 || g.N % s->zchunks != 0 || s->zlook < 1) {
+      fail(s, NS_EINVAL, "ns_init: bad plane-chunk schedule (zchunks=%d, lookahead=%d)", s->zchunks, s->zlook);
+      return bail(NS_EINVAL);
+    }
+  }
+  if (s->zchunks > 1) {
+    for (cudaStream_t &p : s->pipe) INIT_CK(cudaStreamCreateWithFlags(&p, cudaStreamNonBlocking));
+    s->pev.assign(3 * s->zchunks + 1, nullptr);
+    for (cudaEvent_t &e : s->pev) INIT_CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  }
 
   std::vector<unsigned char> tw, ef, ef2;
   if (s->prec == NS_FP32)

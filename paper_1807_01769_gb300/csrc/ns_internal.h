@@ -53,6 +53,7 @@ struct Args {
   int inv;     // OP_FWD1: 1 = fuse the next stage's first inverse axis
   double dt;
   int nsm;     // streaming multiprocessors of the device (persistent grids)
+  int z0, nz;  // 3D OP_INV2 / OP_XPASS / OP_FWD2: planes z0 .. z0+nz-1 (nz = 0: all)
 };
 
 // Launch op for the given precision; returns a cudaError_t value (0 = ok) or

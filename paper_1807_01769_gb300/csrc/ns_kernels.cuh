@@ -307,7 +307,7 @@ __global__ void __launch_bounds__((N / 8) * W) k3_inv1(Geo g, const typename Cpl
 // inv2: y inverse of fields 0..nf-1 at plane z = blockIdx.y; the next field's
 // loads are issued before the current field is transformed.
 template <typename R, int N, int W>
-__global__ void __launch_bounds__((N / 8) * W) k3_inv2(Geo g, int nf, const typename CplxOf<R>::T *__restrict__ zb,
+__global__ void __launch_bounds__((N / 8) * W) k3_inv2(Geo g, int nf, int z0, const typename CplxOf<R>::T *__restrict__ zb,
                                                         typename CplxOf<R>::T *__restrict__ yb,
                                                         const typename CplxOf<R>::T *__restrict__ tw) {
   using C = typename CplxOf<R>::T;
@@ -318,7 +318,7 @@ __global__ void __launch_bounds__((N / 8) * W) k3_inv2(Geo g, int nf, const type
   const int w = threadIdx.x % W, t = threadIdx.x / W;
   const int kx = blockIdx.x * W + w;
   const bool valid = kx < g.h;
-  const int z = blockIdx.y;
+  const int z = z0 + blockIdx.y;
   const C *in = zb + (long long)z * g.c * g.hs + kx;
   C *out = yb + (long long)z * N * g.hs + kx;
   int row[8];
@@ -354,13 +354,14 @@ __global__ void __launch_bounds__((N / 8) * W) k3_inv2(Geo g, int nf, const type
 // xpass (3D): lines (z, y); fields u_x, u_y, u_z, w_x, w_y, w_z in, n = u x w out
 // (written over fields 0..2 of the same lines).
 template <typename R, int N, int L>
-__global__ void __launch_bounds__((N / 16) * L) k3_xpass(Geo g, typename CplxOf<R>::T *__restrict__ yb,
+__global__ void __launch_bounds__((N / 16) * L) k3_xpass(Geo g, long long line_base,
+                                                          typename CplxOf<R>::T *__restrict__ yb,
                                                           const typename CplxOf<R>::T *__restrict__ tw) {
   using C = typename CplxOf<R>::T;
   constexpr int H = N / 2, TX = H / 8, SL = smline_len(H);
   C *S = dyn_smem<C>();
   const int t = threadIdx.x % TX, l = threadIdx.x / TX;
-  const long long line0 = (long long)blockIdx.x * L;
+  const long long line0 = line_base + (long long)blockIdx.x * L;
   const SmLine<C> view{S + l * SL};
   C ux[8], uy[8], uz[8], nx[8], ny[8], nz[8];
   for (int f = 0; f < 6; ++f) {
@@ -407,7 +408,8 @@ __global__ void __launch_bounds__((N / 16) * L) k3_xpass(Geo g, typename CplxOf<
 // (each thread reads back only what it wrote) so that the product accumulators
 // and the prefetched next field fit in 128 registers.
 template <typename R, int N, int WPB>
-__global__ void __launch_bounds__(32 * WPB, 16 / WPB) k3_xpass_w(Geo g, typename CplxOf<R>::T *__restrict__ yb,
+__global__ void __launch_bounds__(32 * WPB, 16 / WPB) k3_xpass_w(Geo g, long long line_base,
+                                                                  typename CplxOf<R>::T *__restrict__ yb,
                                                                   const typename CplxOf<R>::T *__restrict__ tw) {
   using C = typename CplxOf<R>::T;
   constexpr int H = N / 2, TX = H / 8, LPW = 32 / TX;
@@ -416,7 +418,7 @@ __global__ void __launch_bounds__(32 * WPB, 16 / WPB) k3_xpass_w(Geo g, typename
   C *S = dyn_smem<C>();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int t = lane % TX, sub = lane / TX;
-  const long long line = ((long long)blockIdx.x * WPB + warp) * LPW + sub;
+  const long long line = line_base + ((long long)blockIdx.x * WPB + warp) * LPW + sub;
   C *wsm = S + warp * WSM;
   const SmLine<C, N / 2> view{wsm + sub * SL};
   C *park = wsm + LPW * SL + lane;  // park[(a * 8 + m) * 32]
@@ -477,7 +479,7 @@ __global__ void __launch_bounds__(32 * WPB, 16 / WPB) k3_xpass_w(Geo g, typename
 // fwd2: y forward of fields 0..nf-1 at plane z = blockIdx.y, keep retained ky;
 // the next field's loads are issued before the current field is transformed.
 template <typename R, int N, int W>
-__global__ void __launch_bounds__((N / 8) * W) k3_fwd2(Geo g, int nf, const typename CplxOf<R>::T *__restrict__ yb,
+__global__ void __launch_bounds__((N / 8) * W) k3_fwd2(Geo g, int nf, int z0, const typename CplxOf<R>::T *__restrict__ yb,
                                                         typename CplxOf<R>::T *__restrict__ zb,
                                                         const typename CplxOf<R>::T *__restrict__ tw) {
   using C = typename CplxOf<R>::T;
@@ -488,7 +490,7 @@ __global__ void __launch_bounds__((N / 8) * W) k3_fwd2(Geo g, int nf, const type
   const int w = threadIdx.x % W, t = threadIdx.x / W;
   const int kx = blockIdx.x * W + w;
   const bool valid = kx < g.h;
-  const int z = blockIdx.y;
+  const int z = z0 + blockIdx.y;
   const C *in = yb + (long long)z * N * g.hs + kx;
   C *out = zb + (long long)z * g.c * g.hs + kx;
   C xn[8];
@@ -1035,20 +1037,26 @@ struct Launch3 {
           k3_inv1<R, N, WL, false><<<grid, T * WL, SM_L, s>>>(g, (const C *)a.src, (C *)a.zb, tw);
         break;
       }
-      case OP_INV2:
-        k3_inv2<R, N, WY><<<dim3(g.hs / WY, N), T * WY, SM_Y, s>>>(g, a.nf, (const C *)a.zb, (C *)a.yb, tw);
+      case OP_INV2: {
+        const int nz = a.nz > 0 ? a.nz : N;
+        k3_inv2<R, N, WY><<<dim3(g.hs / WY, nz), T * WY, SM_Y, s>>>(g, a.nf, a.z0, (const C *)a.zb, (C *)a.yb, tw);
         break;
+      }
       case OP_XPASS:
         if constexpr (XW) {
-          k3_xpass_w<R, N, XW_WPB><<<(unsigned)((long long)N * N / (XW_WPB * XW_LPW)), 32 * XW_WPB, SM_XW, s>>>(
-              g, (C *)a.yb, tw);
+          const long long lines = (long long)(a.nz > 0 ? a.nz : N) * N;
+          k3_xpass_w<R, N, XW_WPB><<<(unsigned)(lines / (XW_WPB * XW_LPW)), 32 * XW_WPB, SM_XW, s>>>(
+              g, (long long)a.z0 * N, (C *)a.yb, tw);
         } else {
-          k3_xpass<R, N, L><<<(unsigned)((long long)N * N / L), (N / 16) * L, SM_X, s>>>(g, (C *)a.yb, tw);
+          const long long lines = (long long)(a.nz > 0 ? a.nz : N) * N;
+          k3_xpass<R, N, L><<<(unsigned)(lines / L), (N / 16) * L, SM_X, s>>>(g, (long long)a.z0 * N, (C *)a.yb, tw);
         }
         break;
-      case OP_FWD2:
-        k3_fwd2<R, N, WY><<<dim3(g.hs / WY, N), T * WY, SM_Y, s>>>(g, a.nf, (const C *)a.yb, (C *)a.zb, tw);
+      case OP_FWD2: {
+        const int nz = a.nz > 0 ? a.nz : N;
+        k3_fwd2<R, N, WY><<<dim3(g.hs / WY, nz), T * WY, SM_Y, s>>>(g, a.nf, a.z0, (const C *)a.yb, (C *)a.zb, tw);
         break;
+      }
       case OP_FWD1: {
         // persistent: one wave of resident blocks (the kernel walks the tiles)
         const int tiles = g.c * (g.hs / WH);

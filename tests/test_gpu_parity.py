@@ -333,3 +333,23 @@ def test_max_size_3d_1024_two_steps(ns, orc):
     ref = orc.step(3, m, nu, dt, 2, u_small)
     re, rom = orc.diagnostics(3, m, ref)
     assert abs(e - re) < 1e-6 * re and abs(om - rom) < 1e-6 * rom
+
+
+def test_plane_chunk_pipeline_is_bitwise_identical(ns, monkeypatch):
+    # the 3D y-x-y pipeline over plane chunks runs the same kernels on the same
+    # data in another order: results must not change by a bit
+    n = 128
+    u0 = ic(3, n, seed=12)
+    out = []
+    for chunks, look in [("1", "2"), ("8", "1"), ("16", "3")]:
+        monkeypatch.setenv("NS_ZCHUNKS", chunks)
+        monkeypatch.setenv("NS_ZLOOKAHEAD", look)
+        with ns.Solver(3, n, FP32, nu=2e-3, dt=1e-3) as s:
+            s.set_state_spectral(u0)
+            s.step(3)
+            out.append(s.get_state_spectral())
+    assert np.array_equal(out[0], out[1]) and np.array_equal(out[0], out[2])
+    monkeypatch.setenv("NS_ZCHUNKS", "7")  # must divide N
+    with pytest.raises(ns.NSError) as ei:
+        ns.Solver(3, n, FP32)
+    assert ei.value.code == ns.NS_EINVAL
