@@ -339,14 +339,16 @@ void fill_tables(const ns_state *s, std::vector<unsigned char> &tw, std::vector<
     }
     base += nsk::stage_tw_len(L);
   }
-  const int mmax = s->grid.dim * s->g.kc * s->g.kc;
-  ef.resize(sizeof(R) * (mmax + 1));
-  ef2.resize(sizeof(R) * (mmax + 1));
+  // per-axis integrating factors exp(-nu k^2 dt), exp(-nu k^2 dt / 2),
+  // k = 0 .. kc; a mode's factor is the product over its axes
+  const int kmax = s->g.kc;
+  ef.resize(sizeof(R) * (kmax + 1));
+  ef2.resize(sizeof(R) * (kmax + 1));
   R *e = reinterpret_cast<R *>(ef.data());
   R *e2 = reinterpret_cast<R *>(ef2.data());
-  for (int m = 0; m <= mmax; ++m) {
-    e[m] = (R)std::exp(-s->nu * (double)m * s->dt);
-    e2[m] = (R)std::exp(-s->nu * (double)m * s->dt * 0.5);
+  for (int k = 0; k <= kmax; ++k) {
+    e[k] = (R)std::exp(-s->nu * (double)k * k * s->dt);
+    e2[k] = (R)std::exp(-s->nu * (double)k * k * s->dt * 0.5);
   }
 }
 

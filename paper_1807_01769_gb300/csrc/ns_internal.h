@@ -37,8 +37,8 @@ struct Args {
   Geo g;
   const void *tw;  // state precision: exp(-2 pi i j / N) for j < N, then the stage
                    // twiddle tables of length N and of length N/2 (ns_fft.cuh)
-  const void *ef;  // exp(-nu m dt),   m = |k|^2 = 0 .. dim kc^2
-  const void *ef2; // exp(-nu m dt/2)
+  const void *ef;  // exp(-nu k^2 dt),   k = 0 .. kc (per axis)
+  const void *ef2; // exp(-nu k^2 dt/2)
   void *u, *acc;
   const void *F;   // forcing (nullable)
   void *zb, *yb;

@@ -531,26 +531,44 @@ struct StepBufs {
   R dt;
 };
 
-// Lawson IF-RK4 stage update for one mode (see ns.h); returns the next stage input.
+// Asynchronous global -> shared copies of BYTES (4, 8 or 16); a false
+// predicate zero-fills the destination without reading the source.
+__device__ __forceinline__ unsigned smem_addr(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+template <int BYTES>
+__device__ __forceinline__ void cp_async(void *dst_smem, const void *src, bool pred) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;\n" ::"r"(smem_addr(dst_smem)), "l"(src), "n"(BYTES),
+               "r"(pred ? BYTES : 0)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+// Integrating factors of a mode from the per-axis tables: exp(-nu |k|^2 dt)
+// = prod_i exp(-nu k_i^2 dt) (tables indexed by |k_i| = 0 .. kc, computed in
+// FP64 on the host and rounded to the state precision).
+template <typename R>
+__device__ __forceinline__ R axis_factor(const R *__restrict__ t, int k) {
+  return __ldg(t + (k < 0 ? -k : k));
+}
+
+// Lawson IF-RK4 stage update for one mode (see ns.h); e = E, e2 = E2 of the
+// mode; returns the next stage input.
 template <int MODE, typename C, typename R>
-__device__ __forceinline__ C rk_update(C nv, long long idx, int k2, const StepBufs<R> &b) {
+__device__ __forceinline__ C rk_update(C nv, long long idx, R e, R e2, const StepBufs<R> &b) {
   if (MODE == MODE_RK1) {
     const C uu = b.u[idx];
-    const R e = __ldg(b.ef + k2), e2 = __ldg(b.ef2 + k2);
     const R c1 = b.dt * e / (R)6;
     b.acc[idx] = C{e * uu.x + c1 * nv.x, e * uu.y + c1 * nv.y};
     const R h = b.dt / (R)2;
     return C{e2 * (uu.x + h * nv.x), e2 * (uu.y + h * nv.y)};
   } else if (MODE == MODE_RK2) {
     const C uu = b.u[idx], a = b.acc[idx];
-    const R e2 = __ldg(b.ef2 + k2);
     const R c2 = b.dt * e2 / (R)3;
     b.acc[idx] = C{a.x + c2 * nv.x, a.y + c2 * nv.y};
     const R h = b.dt / (R)2;
     return C{e2 * uu.x + h * nv.x, e2 * uu.y + h * nv.y};
   } else if (MODE == MODE_RK3) {
     const C uu = b.u[idx], a = b.acc[idx];
-    const R e = __ldg(b.ef + k2), e2 = __ldg(b.ef2 + k2);
     const R c2 = b.dt * e2 / (R)3;
     b.acc[idx] = C{a.x + c2 * nv.x, a.y + c2 * nv.y};
     const R c3 = b.dt * e2;
@@ -567,36 +585,21 @@ __device__ __forceinline__ C rk_update(C nv, long long idx, int k2, const StepBu
   }
 }
 
-// Asynchronous global -> shared copies of BYTES (4, 8 or 16); a false
-// predicate zero-fills the destination without reading the source.
-__device__ __forceinline__ unsigned smem_addr(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
-template <int BYTES>
-__device__ __forceinline__ void cp_async(void *dst_smem, const void *src, bool pred) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;\n" ::"r"(smem_addr(dst_smem)), "l"(src), "n"(BYTES),
-               "r"(pred ? BYTES : 0)
-               : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
-
 // Lawson IF-RK4 stage update for one mode with its operands already loaded
 // (uu = state, a = accumulator; see rk_update); writes acc / u / dst at gi.
 template <int MODE, typename C, typename R>
-__device__ __forceinline__ C rk_stage(C nv, C uu, C a, int k2, const StepBufs<R> &b, long long gi) {
+__device__ __forceinline__ C rk_stage(C nv, C uu, C a, R e, R e2, const StepBufs<R> &b, long long gi) {
   if (MODE == MODE_RK1) {
-    const R e = __ldg(b.ef + k2), e2 = __ldg(b.ef2 + k2);
     const R c1 = b.dt * e / (R)6;
     b.acc[gi] = C{e * uu.x + c1 * nv.x, e * uu.y + c1 * nv.y};
     const R h = b.dt / (R)2;
     return C{e2 * (uu.x + h * nv.x), e2 * (uu.y + h * nv.y)};
   } else if (MODE == MODE_RK2) {
-    const R e2 = __ldg(b.ef2 + k2);
     const R c2 = b.dt * e2 / (R)3;
     b.acc[gi] = C{a.x + c2 * nv.x, a.y + c2 * nv.y};
     const R h = b.dt / (R)2;
     return C{e2 * uu.x + h * nv.x, e2 * uu.y + h * nv.y};
   } else if (MODE == MODE_RK3) {
-    const R e = __ldg(b.ef + k2), e2 = __ldg(b.ef2 + k2);
     const R c2 = b.dt * e2 / (R)3;
     b.acc[gi] = C{a.x + c2 * nv.x, a.y + c2 * nv.y};
     const R c3 = b.dt * e2;
@@ -653,6 +656,8 @@ __global__ void __launch_bounds__((N / 8) * W) k3_fwd1(Geo g, StepBufs<R> b) {
     const int ky = ktr_of(iy, g.kc, g.c);
     const R kxr = (R)kx, kyr = (R)ky;
     const long long col = (long long)iy * g.hs + kx;
+    const R exy = valid ? axis_factor(b.ef, kx) * axis_factor(b.ef, ky) : (R)0;
+    const R exy2 = valid ? axis_factor(b.ef2, kx) * axis_factor(b.ef2, ky) : (R)0;
     C s0[8], s1[8], s2[8];
 #pragma unroll
     for (int m = 0; m < 8; ++m) {
@@ -709,11 +714,12 @@ __global__ void __launch_bounds__((N / 8) * W) k3_fwd1(Geo g, StepBufs<R> b) {
       }
       C nv[3] = {ax, ay, az};
       C out[3];
+      const R e = exy * axis_factor(b.ef, kz), e2 = exy2 * axis_factor(b.ef2, kz);
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
         const int slot = (c * 6 + rk_slot(m)) * NT + threadIdx.x;
         const long long gi = c * st + idx;
-        out[c] = rk_stage<MODE>(nv[c], NEED_U ? rku[slot] : czero<C>(), NEED_ACC ? rka[slot] : czero<C>(), k2, b, gi);
+        out[c] = rk_stage<MODE>(nv[c], NEED_U ? rku[slot] : czero<C>(), NEED_ACC ? rka[slot] : czero<C>(), e, e2, b, gi);
       }
       s0[m] = out[0];
       s1[m] = out[1];
@@ -897,7 +903,8 @@ __global__ void __launch_bounds__((N / 8) * W) k2_fwd1(Geo g, StepBufs<R> b) {
     C nv = k2 == 0 ? czero<C>() : cscale(s[m], scale);
     const long long idx = (long long)compact_of(n, N, g.kc, g.c) * g.hs + kx;
     if (MODE != MODE_PROJ && b.F != nullptr) nv = cadd(nv, b.F[idx]);
-    s[m] = rk_update<MODE>(nv, idx, k2, b);
+    const R e = axis_factor(b.ef, kx) * axis_factor(b.ef, ky), e2 = axis_factor(b.ef2, kx) * axis_factor(b.ef2, ky);
+    s[m] = rk_update<MODE>(nv, idx, e, e2, b);
   }
   if (INV) {
     for (int f = 0; f < 4; ++f) {
