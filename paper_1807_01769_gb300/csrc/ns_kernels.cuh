@@ -260,7 +260,10 @@ __global__ void __launch_bounds__((N / 8) * W) k3_inv1(Geo g, const typename Cpl
   constexpr bool DB = col_db(N, W, sizeof(C), EXTRA_SMEM);
   const SmCol<C, DB> view{sm + w, P, N * P};
   const long long st = g.st_comp;
-  constexpr int NF = CURL ? 6 : 3;
+  // five transforms for six fields: omega_z = i (kx u_y - ky u_x) has no kz,
+  // so its z inverse is formed from the inverses of u_x and u_y
+  constexpr int NF = CURL ? 5 : 3;
+  C zx[8];
   for (int f = 0; f < NF; ++f) {
     C v[8];
 #pragma unroll
@@ -269,7 +272,7 @@ __global__ void __launch_bounds__((N / 8) * W) k3_inv1(Geo g, const typename Cpl
       C x = czero<C>();
       if (valid && retained(n, N, g.kc)) {
         const long long idx = (long long)compact_of(n, N, g.kc, g.c) * plane + col;
-        if (!CURL || f < 3) {
+        if (f < 3) {
           x = src[f * st + idx];
         } else {
           const R kzr = (R)kfull_of(n, N, g.kc);
@@ -280,16 +283,11 @@ __global__ void __launch_bounds__((N / 8) * W) k3_inv1(Geo g, const typename Cpl
             b = src[st + idx];
             ka = kyr;
             kb = kzr;
-          } else if (f == 4) {  // i (kz ux - kx uz)
+          } else {  // i (kz ux - kx uz)
             a = src[idx];
             b = src[2 * st + idx];
             ka = kzr;
             kb = kxr;
-          } else {  // i (kx uy - ky ux)
-            a = src[st + idx];
-            b = src[idx];
-            ka = kxr;
-            kb = kyr;
           }
           x = cmuli(C{ka * a.x - kb * b.x, ka * a.y - kb * b.y});
         }
@@ -300,6 +298,15 @@ __global__ void __launch_bounds__((N / 8) * W) k3_inv1(Geo g, const typename Cpl
     if (valid) {
 #pragma unroll
       for (int m = 0; m < 8; ++m) zb[f * g.zb_f + (long long)(t + T * m) * plane + col] = v[m];
+    }
+    if (CURL && f == 0) {
+#pragma unroll
+      for (int m = 0; m < 8; ++m) zx[m] = v[m];
+    } else if (CURL && f == 1 && valid) {
+#pragma unroll
+      for (int m = 0; m < 8; ++m)
+        zb[5 * g.zb_f + (long long)(t + T * m) * plane + col] =
+            cmuli(C{kxr * v[m].x - kyr * zx[m].x, kxr * v[m].y - kyr * zx[m].y});
     }
   }
 }
@@ -726,7 +733,10 @@ __global__ void __launch_bounds__((N / 8) * W) k3_fwd1(Geo g, StepBufs<R> b) {
       s2[m] = out[2];
     }
     if (INV) {
-      for (int f = 0; f < 6; ++f) {
+      // omega_z = i (kx u_y - ky u_x) has no kz: its z inverse is formed from
+      // the inverses of u_x and u_y (five transforms for six fields)
+      C zx[8];
+      for (int f = 0; f < 5; ++f) {
         C v[8];
 #pragma unroll
         for (int m = 0; m < 8; ++m) {
@@ -735,13 +745,21 @@ __global__ void __launch_bounds__((N / 8) * W) k3_fwd1(Geo g, StepBufs<R> b) {
           else if (f == 1) v[m] = s1[m];
           else if (f == 2) v[m] = s2[m];
           else if (f == 3) v[m] = cmuli(C{kyr * s2[m].x - kzr * s1[m].x, kyr * s2[m].y - kzr * s1[m].y});
-          else if (f == 4) v[m] = cmuli(C{kzr * s0[m].x - kxr * s2[m].x, kzr * s0[m].y - kxr * s2[m].y});
-          else v[m] = cmuli(C{kxr * s1[m].x - kyr * s0[m].x, kxr * s1[m].y - kyr * s0[m].y});
+          else v[m] = cmuli(C{kzr * s0[m].x - kxr * s2[m].x, kzr * s0[m].y - kxr * s2[m].y});
         }
         fft_line<N, +1>(v, t, b.tw + N, view);
         if (valid) {
 #pragma unroll
           for (int m = 0; m < 8; ++m) b.zb[f * g.zb_f + (long long)(t + T * m) * plane + col] = v[m];
+        }
+        if (f == 0) {
+#pragma unroll
+          for (int m = 0; m < 8; ++m) zx[m] = v[m];
+        } else if (f == 1 && valid) {
+#pragma unroll
+          for (int m = 0; m < 8; ++m)
+            b.zb[5 * g.zb_f + (long long)(t + T * m) * plane + col] =
+                cmuli(C{kxr * v[m].x - kyr * zx[m].x, kxr * v[m].y - kyr * zx[m].y});
         }
       }
     }
