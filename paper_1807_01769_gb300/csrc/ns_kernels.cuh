@@ -74,6 +74,13 @@ __device__ __forceinline__ C *dyn_smem() {
   return reinterpret_cast<C *>(ns_dyn_smem);
 }
 
+// Loads of data read exactly once (pass inputs): kept out of L1 so that the
+// reused twiddle and factor tables stay there.
+template <typename C>
+__device__ __forceinline__ C ld_stream(const C *p) {
+  return __ldcg(p);
+}
+
 __device__ __forceinline__ bool retained(int n, int N, int kc) { return n <= kc || n >= N - kc; }
 __device__ __forceinline__ int compact_of(int n, int N, int kc, int c) { return n <= kc ? n : n - (N - c); }
 __device__ __forceinline__ int kfull_of(int n, int N, int kc) { return n <= kc ? n : n - N; }
@@ -228,7 +235,7 @@ __device__ __forceinline__ void load_line(C (&x)[8], const C *__restrict__ src, 
 #pragma unroll
   for (int m = 0; m < 8; ++m) {
     const int k = t + TX * m;
-    x[m] = k < h ? src[k] : czero<C>();
+    x[m] = k < h ? ld_stream(src + k) : czero<C>();
   }
 }
 
@@ -338,7 +345,7 @@ __global__ void __launch_bounds__((N / 8) * W) k3_inv2(Geo g, int nf, int z0, co
   }
   C xn[8];
 #pragma unroll
-  for (int m = 0; m < 8; ++m) xn[m] = live[m] ? in[(long long)row[m] * g.hs] : czero<C>();
+  for (int m = 0; m < 8; ++m) xn[m] = live[m] ? ld_stream(in + (long long)row[m] * g.hs) : czero<C>();
 #pragma unroll 1
   for (int f = 0; f < nf; ++f) {
     C v[8];
@@ -347,7 +354,7 @@ __global__ void __launch_bounds__((N / 8) * W) k3_inv2(Geo g, int nf, int z0, co
     if (f + 1 < nf) {
       const C *nin = in + (f + 1) * g.zb_f;
 #pragma unroll
-      for (int m = 0; m < 8; ++m) xn[m] = live[m] ? nin[(long long)row[m] * g.hs] : czero<C>();
+      for (int m = 0; m < 8; ++m) xn[m] = live[m] ? ld_stream(nin + (long long)row[m] * g.hs) : czero<C>();
     }
     fft_line<N, +1>(v, t, tw + N, SmCol<C, col_db(N, W, sizeof(C), 0)>{sm + w, P, N * P});
     if (valid) {
@@ -502,7 +509,7 @@ __global__ void __launch_bounds__((N / 8) * W) k3_fwd2(Geo g, int nf, int z0, co
   C *out = zb + (long long)z * g.c * g.hs + kx;
   C xn[8];
 #pragma unroll
-  for (int m = 0; m < 8; ++m) xn[m] = valid ? in[(long long)(t + T * m) * g.hs] : czero<C>();
+  for (int m = 0; m < 8; ++m) xn[m] = valid ? ld_stream(in + (long long)(t + T * m) * g.hs) : czero<C>();
 #pragma unroll 1
   for (int f = 0; f < nf; ++f) {
     C v[8];
@@ -511,7 +518,7 @@ __global__ void __launch_bounds__((N / 8) * W) k3_fwd2(Geo g, int nf, int z0, co
     if (f + 1 < nf) {
       const C *nin = in + (f + 1) * g.yb_f;
 #pragma unroll
-      for (int m = 0; m < 8; ++m) xn[m] = valid ? nin[(long long)(t + T * m) * g.hs] : czero<C>();
+      for (int m = 0; m < 8; ++m) xn[m] = valid ? ld_stream(nin + (long long)(t + T * m) * g.hs) : czero<C>();
     }
     fft_line<N, -1>(v, t, tw + N, SmCol<C, col_db(N, W, sizeof(C), 0)>{sm + w, P, N * P});
     if (valid) {
@@ -669,9 +676,9 @@ __global__ void __launch_bounds__((N / 8) * W) k3_fwd1(Geo g, StepBufs<R> b) {
 #pragma unroll
     for (int m = 0; m < 8; ++m) {
       const long long off = (long long)(t + T * m) * plane + col;
-      s0[m] = valid ? b.zb[off] : czero<C>();
-      s1[m] = valid ? b.zb[g.zb_f + off] : czero<C>();
-      s2[m] = valid ? b.zb[2 * g.zb_f + off] : czero<C>();
+      s0[m] = valid ? ld_stream(b.zb + off) : czero<C>();
+      s1[m] = valid ? ld_stream(b.zb + g.zb_f + off) : czero<C>();
+      s2[m] = valid ? ld_stream(b.zb + 2 * g.zb_f + off) : czero<C>();
     }
     if (NEED_U || NEED_ACC) {
 #pragma unroll
