@@ -139,6 +139,58 @@ def cpu_baseline(n=128, steps=2):
                       f"step is ~{(512 // n) ** 3}x the work"}
 
 
+ENSEMBLE_WORKLOAD = ("64 independent 2D NS runs (vorticity form), sizes drawn uniformly from {128^2, 256^2, 512^2} "
+                     "(splitmix64(1000+i)), FP32, random-phase spectrum peaked at k=8 (E~k^4 exp(-2(k/8)^2)), "
+                     "seeds 0..63, nu=dt=5e-4")
+
+
+def ensemble_bench(steps=50):
+    """Batched 2D ensemble (one persistent launch per pass over all members,
+    autotuned schedule, one CUDA graph per step) against the plain form: the
+    same 64 runs each advanced by its own ns_step graph on the same stream."""
+    import torch
+
+    from paper_1807_01769_gb300 import inputs, ns
+
+    sizes = inputs.ensemble_sizes(64)
+    u0 = [inputs.random_vorticity_2d(n, seed=m, k0=8.0, a=2.0, energy=0.5) for m, n in enumerate(sizes)]
+    pts = sum(n * n for n in sizes)
+    stream = torch.cuda.Stream()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ns.Ensemble(sizes, ns.NS_FP32, nu=5e-4, dt=5e-4, autotune=True) as e:
+        e.set_stream(stream.cuda_stream)
+        for m, u in enumerate(u0):
+            e.set_state_spectral(m, u)
+        e.step(3)
+        e.sync()
+        ev0.record(stream)
+        e.step(steps)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        ms = ev0.elapsed_time(ev1) / steps
+        sched = e.schedule()
+    solvers = [ns.Solver(2, n, ns.NS_FP32, nu=5e-4, dt=5e-4) for n in sizes]
+    for s, u in zip(solvers, u0):
+        s.set_stream(stream.cuda_stream)
+        s.set_state_spectral(u)
+        s.step(3)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    for _ in range(steps):
+        for s in solvers:
+            s.step(1)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms_plain = ev0.elapsed_time(ev1) / steps
+    for s in solvers:
+        s.close()
+    return {"workload": ENSEMBLE_WORKLOAD, "metric": "Mpoint*RK4-steps/s", "steps": steps,
+            "value": pts / (ms / 1e3) / 1e6, "ms_per_step": ms, "plain_value": pts / (ms_plain / 1e3) / 1e6,
+            "plain_ms_per_step": ms_plain, "speedup_vs_plain": ms_plain / ms,
+            "schedule": {"x_blocks_per_sm": sched[0], "y_blocks_per_sm": sched[1],
+                         "task_order": ["member-major", "round-robin"][sched[2]]}}
+
+
 def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
@@ -283,6 +335,8 @@ def run_gb300(args):
         }
         if cpu is not None:
             line["cpu_baseline"] = cpu
+        if ws == 1 and not args.no_ensemble:
+            line["ensemble"] = ensemble_bench()
         print(json.dumps(line), flush=True)
     s.close()
     if ws > 1:
@@ -298,6 +352,7 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--e2e-reps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-ensemble", action="store_true", help="skip the batched 2D ensemble measurement")
     ap.add_argument("--n", type=int, default=512, help="grid size override (profiling of smaller cases only)")
     args = ap.parse_args()
     global N_GRID

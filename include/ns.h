@@ -153,6 +153,47 @@ long long ns_kernel_bytes(const ns_state *s, int id);
 /* Device bytes held by the state. */
 long long ns_device_bytes(const ns_state *s);
 
+/* ------------------------------------------------------------------------
+ * Ensembles of independent 2D runs (vorticity form, same nu and dt, grid
+ * sizes n[m] in {64, 128, 256, 512}, one precision).  Each RK stage is two
+ * persistent launches over the work units of all members (x pass over line
+ * groups; fused y pass = forward, dealias, RK stage, next inverse over kx
+ * tiles), captured in one CUDA graph per step.  Every member follows exactly
+ * the arithmetic of ns_step on its own grid (bitwise the same result).  The
+ * paper runs one problem per process set ("Performance / Scalability"); small
+ * problems are batched here because one alone cannot fill the GPU.
+ * ------------------------------------------------------------------------ */
+typedef struct ns_ensemble ns_ensemble;
+
+/* Create an ensemble on the current device; all states start at zero.
+ * autotune != 0 times the schedule candidates (blocks per SM of each pass:
+ * x in {2, 4, 8}, y in {1, 2, 4}; task order member-major or round robin)
+ * on the zero state and keeps the fastest; otherwise x = 4, y = 2,
+ * member-major.  NS_EUNSUPPORTED for a grid size outside the set above. */
+int ns_ensemble_init(ns_ensemble **out, int count, const int *n, int precision, double nu, double dt, int autotune);
+
+/* Current schedule / set a schedule (task_order 0 = member by member,
+ * 1 = round robin over members).  Set synchronises the ensemble's stream. */
+int ns_ensemble_schedule(const ns_ensemble *e, int *x_blocks_per_sm, int *y_blocks_per_sm, int *task_order);
+int ns_ensemble_set_schedule(ns_ensemble *e, int x_blocks_per_sm, int y_blocks_per_sm, int task_order);
+
+/* Member state in the canonical 2D truncated spectral layout (host complex128
+ * as double pairs, [c][h] of that member's grid).  Synchronise. */
+int ns_ensemble_set_state_spectral(ns_ensemble *e, int member, const double *spec_host);
+int ns_ensemble_get_state_spectral(ns_ensemble *e, int member, double *spec_host);
+
+/* Advance every member nsteps Lawson IF-RK4 steps (asynchronous). */
+int ns_ensemble_step(ns_ensemble *e, int nsteps);
+
+/* Per-member energy and enstrophy (arrays of count doubles), FP64.
+ * Synchronises; NS_ENONFINITE if a member holds NaN or Inf. */
+int ns_ensemble_diagnostics(ns_ensemble *e, double *energy, double *enstrophy);
+
+int ns_ensemble_set_stream(ns_ensemble *e, void *cuda_stream);
+int ns_ensemble_sync(ns_ensemble *e);
+void ns_ensemble_destroy(ns_ensemble *e);
+const char *ns_ensemble_last_error(const ns_ensemble *e);
+
 /* Diagnostics for callers that cannot allocate device memory.
  * The FluidSim paper has no counterpart: this entry point exists for code that
  * must not call cudaMalloc -- a host callback, an allocator hook, a process

@@ -778,16 +778,16 @@ __global__ void __launch_bounds__((N / 8) * W) k3_fwd1(Geo g, StepBufs<R> b) {
 // u_x = i ky psi, u_y = -i kx psi, d_x w = i kx w, d_y w = i ky w with
 // psi = w/|k|^2; otherwise one field (w itself).
 template <typename R, int N, int W, bool VEL>
-__global__ void __launch_bounds__((N / 8) * W) k2_inv1(Geo g, const typename CplxOf<R>::T *__restrict__ src,
-                                                        typename CplxOf<R>::T *__restrict__ yb,
-                                                        const typename CplxOf<R>::T *__restrict__ tw) {
+__device__ __forceinline__ void inv1_2d_unit(const Geo &g, const typename CplxOf<R>::T *__restrict__ src,
+                                             typename CplxOf<R>::T *__restrict__ yb,
+                                             const typename CplxOf<R>::T *__restrict__ tw, int unit,
+                                             typename CplxOf<R>::T *sm) {
   using C = typename CplxOf<R>::T;
   constexpr int T = N / 8;
   constexpr int P = pitch_of(W, sizeof(C));
   constexpr size_t EXTRA_SMEM = 0;
-  C *sm = dyn_smem<C>();
   const int w = threadIdx.x % W, t = threadIdx.x / W;
-  const int kx = blockIdx.x * W + w;
+  const int kx = unit * W + w;
   const bool valid = kx < g.h;
   constexpr bool DB = col_db(N, W, sizeof(C), EXTRA_SMEM);
   const SmCol<C, DB> view{sm + w, P, N * P};
@@ -823,6 +823,14 @@ __global__ void __launch_bounds__((N / 8) * W) k2_inv1(Geo g, const typename Cpl
   }
 }
 
+template <typename R, int N, int W, bool VEL>
+__global__ void __launch_bounds__((N / 8) * W) k2_inv1(Geo g, const typename CplxOf<R>::T *__restrict__ src,
+                                                        typename CplxOf<R>::T *__restrict__ yb,
+                                                        const typename CplxOf<R>::T *__restrict__ tw) {
+  using C = typename CplxOf<R>::T;
+  inv1_2d_unit<R, N, W, VEL>(g, src, yb, tw, blockIdx.x, dyn_smem<C>());
+}
+
 // xpass (2D): lines y; fields u_x, u_y, d_x w, d_y w in; n = -(u . grad w)
 // out (field 0).
 template <typename R, int N, int L>
@@ -855,18 +863,20 @@ __global__ void __launch_bounds__((N / 16) * L) k2_xpass(Geo g, typename CplxOf<
   emit_r2c<C, N, L>(nn, t, l, S, yb, line0, g.h, g.hs, tw);
 }
 
-// xpass (2D), one warp per line group (see k3_xpass_w).
+// xpass (2D), one warp per line group (see k3_xpass_w); `unit` selects the
+// group of WPB * LPW lines.
+// Sw is this warp's own shared region (at least LPW line buffers).
 template <typename R, int N, int WPB>
-__global__ void __launch_bounds__(32 * WPB) k2_xpass_w(Geo g, typename CplxOf<R>::T *__restrict__ yb,
-                                                        const typename CplxOf<R>::T *__restrict__ tw) {
+__device__ __forceinline__ void xpass_2d_unit(const Geo &g, typename CplxOf<R>::T *__restrict__ yb,
+                                              const typename CplxOf<R>::T *__restrict__ tw, int unit,
+                                              typename CplxOf<R>::T *Sw) {
   using C = typename CplxOf<R>::T;
   constexpr int H = N / 2, TX = H / 8, LPW = 32 / TX;
   constexpr int SL = xw_line_len<N, (LPW > 1)>();
-  C *S = dyn_smem<C>();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int t = lane % TX, sub = lane / TX;
-  const long long line = ((long long)blockIdx.x * WPB + warp) * LPW + sub;
-  const SmLine<C, N / 2> view{S + (warp * LPW + sub) * SL};
+  const long long line = ((long long)unit * WPB + warp) * LPW + sub;
+  const SmLine<C, N / 2> view{Sw + sub * SL};
   const C *src = yb + line * g.hs;
   const C wt = __ldg(tw + t);
   C xn[8];
@@ -897,17 +907,26 @@ __global__ void __launch_bounds__(32 * WPB) k2_xpass_w(Geo g, typename CplxOf<R>
   }
 }
 
+template <typename R, int N, int WPB>
+__global__ void __launch_bounds__(32 * WPB) k2_xpass_w(Geo g, typename CplxOf<R>::T *__restrict__ yb,
+                                                        const typename CplxOf<R>::T *__restrict__ tw) {
+  using C = typename CplxOf<R>::T;
+  constexpr int LPW = 32 / (N / 16);
+  xpass_2d_unit<R, N, WPB>(g, yb, tw, blockIdx.x,
+                           dyn_smem<C>() + (threadIdx.x >> 5) * LPW * xw_line_len<N, (LPW > 1)>());
+}
+
 // fwd1 (2D): y forward of field 0, dealias, 1/N^2, forcing, RK stage; INV:
-// the four inverse fields of the next stage input.
+// the four inverse fields of the next stage input.  `unit` is the kx tile.
 template <typename R, int N, int W, int MODE, bool INV>
-__global__ void __launch_bounds__((N / 8) * W) k2_fwd1(Geo g, StepBufs<R> b) {
+__device__ __forceinline__ void fwd1_2d_unit(const Geo &g, const StepBufs<R> &b, int unit,
+                                             typename CplxOf<R>::T *sm) {
   using C = typename CplxOf<R>::T;
   constexpr int T = N / 8;
   constexpr int P = pitch_of(W, sizeof(C));
   constexpr size_t EXTRA_SMEM = 0;
-  C *sm = dyn_smem<C>();
   const int w = threadIdx.x % W, t = threadIdx.x / W;
-  const int kx = blockIdx.x * W + w;
+  const int kx = unit * W + w;
   const bool valid = kx < g.h;
   constexpr bool DB = col_db(N, W, sizeof(C), EXTRA_SMEM);
   const SmCol<C, DB> view{sm + w, P, N * P};
@@ -952,6 +971,13 @@ __global__ void __launch_bounds__((N / 8) * W) k2_fwd1(Geo g, StepBufs<R> b) {
       }
     }
   }
+}
+
+
+template <typename R, int N, int W, int MODE, bool INV>
+__global__ void __launch_bounds__((N / 8) * W) k2_fwd1(Geo g, StepBufs<R> b) {
+  using C = typename CplxOf<R>::T;
+  fwd1_2d_unit<R, N, W, MODE, INV>(g, b, blockIdx.x, dyn_smem<C>());
 }
 
 // ================================================ real lines (set / get) ===

@@ -189,3 +189,9 @@ def random_phys(shape, seed: int) -> np.ndarray:
         r = splitmix64(idx ^ splitmix64(np.uint64(seed + 12345)))
     u = (r >> np.uint64(11)).astype(np.float64) * (1.0 / 9007199254740992.0)
     return (2.0 * u - 1.0).reshape(shape)
+
+
+def ensemble_sizes(count: int = 64, choices=(128, 256, 512), base: int = 1000):
+    """Grid sizes of an ensemble: member i takes choices[splitmix64(base + i) mod len]."""
+    r = splitmix64(np.arange(base, base + count, dtype=np.uint64))
+    return [int(choices[int(v % np.uint64(len(choices)))]) for v in r]

@@ -61,6 +61,17 @@ SIGNATURES = {
     "ns_diagnostics_noalloc": ([ctypes.POINTER(ns_grid), _P, _P, _P], _I),
     "ns_destroy": ([_P], None),
     "ns_last_error": ([_P], ctypes.c_char_p),
+    "ns_ensemble_init": ([ctypes.POINTER(_P), _I, _P, _I, _D, _D, _I], _I),
+    "ns_ensemble_schedule": ([_P, _PI, _PI, _PI], _I),
+    "ns_ensemble_set_schedule": ([_P, _I, _I, _I], _I),
+    "ns_ensemble_set_state_spectral": ([_P, _I, _P], _I),
+    "ns_ensemble_get_state_spectral": ([_P, _I, _P], _I),
+    "ns_ensemble_step": ([_P, _I], _I),
+    "ns_ensemble_diagnostics": ([_P, _P, _P], _I),
+    "ns_ensemble_set_stream": ([_P, _P], _I),
+    "ns_ensemble_sync": ([_P], _I),
+    "ns_ensemble_destroy": ([_P], None),
+    "ns_ensemble_last_error": ([_P], ctypes.c_char_p),
 }
 
 
@@ -227,3 +238,77 @@ class Solver:
 
     def device_bytes(self) -> int:
         return int(lib.ns_device_bytes(self.state))
+
+
+def _echeck(rc: int, ens=None):
+    if rc != NS_OK:
+        msg = lib.ns_ensemble_last_error(ens)
+        raise NSError(rc, msg.decode() if msg else "")
+
+
+class Ensemble:
+    """Independent 2D runs of uneven sizes advanced together:
+    ``Ensemble(sizes, precision, nu, dt, autotune=True)``.  Member states use
+    the canonical 2D spectral layout ``(c, h)`` of their own grid."""
+
+    def __init__(self, sizes, precision: int = NS_FP32, nu: float = 0.0, dt: float = 1e-3, autotune: bool = True):
+        self.sizes = [int(n) for n in sizes]
+        self.shapes = []
+        for n in self.sizes:
+            z = ns_sizes(2, n, precision)
+            self.shapes.append((z["c"], z["h"]))
+        arr = np.ascontiguousarray(self.sizes, dtype=np.int32)
+        out = _P()
+        _echeck(lib.ns_ensemble_init(ctypes.byref(out), len(self.sizes), _ptr(arr), precision, float(nu), float(dt),
+                                     1 if autotune else 0))
+        self.ens = out
+
+    def close(self):
+        if getattr(self, "ens", None):
+            lib.ns_ensemble_destroy(self.ens)
+            self.ens = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def schedule(self):
+        a, b, c = _I(), _I(), _I()
+        _echeck(lib.ns_ensemble_schedule(self.ens, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)), self.ens)
+        return a.value, b.value, c.value
+
+    def set_schedule(self, x_blocks: int, y_blocks: int, order: int) -> None:
+        _echeck(lib.ns_ensemble_set_schedule(self.ens, x_blocks, y_blocks, order), self.ens)
+
+    def set_state_spectral(self, member: int, spec) -> None:
+        s = np.ascontiguousarray(spec, dtype=np.complex128).reshape(self.shapes[member])
+        _echeck(lib.ns_ensemble_set_state_spectral(self.ens, member, _ptr(s)), self.ens)
+
+    def get_state_spectral(self, member: int):
+        out = np.empty(self.shapes[member], np.complex128)
+        _echeck(lib.ns_ensemble_get_state_spectral(self.ens, member, _ptr(out)), self.ens)
+        return out
+
+    def step(self, nsteps: int) -> None:
+        _echeck(lib.ns_ensemble_step(self.ens, int(nsteps)), self.ens)
+
+    def sync(self) -> None:
+        _echeck(lib.ns_ensemble_sync(self.ens), self.ens)
+
+    def set_stream(self, stream_handle) -> None:
+        _echeck(lib.ns_ensemble_set_stream(self.ens, ctypes.c_void_p(stream_handle) if stream_handle else None),
+                self.ens)
+
+    def diagnostics(self):
+        e = np.zeros(len(self.sizes))
+        o = np.zeros(len(self.sizes))
+        _echeck(lib.ns_ensemble_diagnostics(self.ens, _ptr(e), _ptr(o)), self.ens)
+        return e, o

@@ -70,3 +70,27 @@ def test_null_state_calls_return_einval(ns):
     ns.lib.ns_destroy(None)
     assert ns.lib.ns_num_kernels() == 5
     assert [ns.lib.ns_kernel_name(i).decode() for i in range(5)] == ["inv1", "inv2", "xpass", "fwd2", "fwd1"]
+
+
+def test_ensemble_argument_checks(ns):
+    import numpy as np
+
+    with pytest.raises(ns.NSError) as ei:
+        ns.Ensemble([128, 1024], ns.NS_FP32, nu=1e-3, dt=1e-3)
+    assert ei.value.code == ns.NS_EUNSUPPORTED
+    with pytest.raises(ns.NSError) as ei:
+        ns.Ensemble([128], ns.NS_FP32, nu=-1.0, dt=1e-3)
+    assert ei.value.code == ns.NS_EINVAL
+    out = ns.ctypes.c_void_p()
+    sizes = np.array([128], np.int32)
+    assert ns.lib.ns_ensemble_init(ns.ctypes.byref(out), 0, sizes.ctypes.data_as(ns.ctypes.c_void_p), 1, 1e-3, 1e-3,
+                                   0) == ns.NS_EINVAL
+    assert ns.lib.ns_ensemble_step(None, 1) == ns.NS_EINVAL
+
+
+def test_ensemble_sizes_draw():
+    from paper_1807_01769_gb300 import inputs
+
+    s = inputs.ensemble_sizes(64)
+    assert len(s) == 64 and set(s) <= {128, 256, 512}
+    assert s == inputs.ensemble_sizes(64)
