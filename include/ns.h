@@ -119,6 +119,19 @@ int ns_eval_rhs(ns_state *s, double *rhs_host);
  * NS_ENONFINITE (values still written) if either is NaN or Inf. */
 int ns_diagnostics(ns_state *s, double *energy, double *enstrophy);
 
+/* Energy and enstrophy budget terms of the state ("sim.output.spatial_means":
+ * forcing power and dissipation), FP64, w as above:
+ *   3D: out[0] P_E = sum w Re(u_hat* . F_hat)         (energy injection),
+ *       out[1] D_E = nu sum w |k|^2 |u_hat|^2         (energy dissipation),
+ *       out[2] P_Z = sum w |k|^2 Re(u_hat* . F_hat)   (enstrophy injection),
+ *       out[3] D_Z = nu sum w |k|^4 |u_hat|^2         (enstrophy dissipation);
+ *   2D: out[0] P_E = sum w Re(w_hat* F_hat) / |k|^2,  out[1] D_E = nu sum w |w_hat|^2,
+ *       out[2] P_Z = sum w Re(w_hat* F_hat),          out[3] D_Z = nu sum w |k|^2 |w_hat|^2.
+ * F_hat is the stored (dealiased, projected) forcing; zero without one.  The
+ * Galerkin system gives dE/dt = P_E - D_E, and in 2D dOmega/dt = P_Z - D_Z.
+ * Synchronises; NS_ENONFINITE (values still written) on NaN or Inf. */
+int ns_budget(ns_state *s, double *out);
+
 /* Shell energy spectrum ("sim.output.spectra", versus the modulus of the
  * wavenumber): out[m] = sum over modes with round(|k|) = m of the energy
  * density above, m = 0 .. *nbins-1.  *nbins: in = capacity of out, out = bins
@@ -193,6 +206,47 @@ int ns_ensemble_set_stream(ns_ensemble *e, void *cuda_stream);
 int ns_ensemble_sync(ns_ensemble *e);
 void ns_ensemble_destroy(ns_ensemble *e);
 const char *ns_ensemble_last_error(const ns_ensemble *e);
+
+/* Device-side state and forcing exchange (used by the learned closure):
+ *   ns_state_to_phys_device  : the state in physical space (layout as
+ *     ns_get_state, FP64) written to a DEVICE buffer, enqueued on the state's
+ *     stream (no synchronisation);
+ *   ns_set_forcing_phys_device: the forcing replaced by the FFT, dealiasing
+ *     and (3D) projection of a DEVICE physical field (FP64); enqueued.  A state
+ *     created without forcing gets one here. */
+int ns_state_to_phys_device(ns_state *s, double *phys_dev);
+int ns_set_forcing_phys_device(ns_state *s, const double *phys_dev);
+
+/* ------------------------------------------------------------------------
+ * Learned closure network (no counterpart in the paper): four 3x3
+ * convolutions on a periodic height x width grid, channels 1 -> 32 -> 32 ->
+ * 32 -> 1, exact GELU after the first three, BF16 activations and weights with
+ * FP32 accumulation and an FP32 Adam master copy.  Data [batch][y][x], FP32,
+ * device pointers.  Parameters flat: W0 b0 W1 b1 W2 b2 W3 b3, W as
+ * [Cout][Cin][3][3].  Weight gradients are accumulated with atomics (their
+ * last bits depend on the order).
+ * ------------------------------------------------------------------------ */
+typedef struct ns_cnn ns_cnn;
+int ns_cnn_init(ns_cnn **out, int height, int width, int max_batch, unsigned long long seed);
+int ns_cnn_num_params(const ns_cnn *c);
+int ns_cnn_get_params(ns_cnn *c, float *host);
+int ns_cnn_set_params(ns_cnn *c, const float *host);
+/* y = net(x), enqueued on stream (null = legacy default stream). */
+int ns_cnn_forward(ns_cnn *c, const float *x_dev, float *y_dev, int batch, void *stream);
+/* Gradient of mean((net(x) - t)^2) into grad_host (num_params floats) and the
+ * loss; no update; synchronous. */
+int ns_cnn_gradients(ns_cnn *c, const float *x_dev, const float *t_dev, int batch, float *grad_host, float *loss);
+/* One Adam step (beta 0.9 / 0.999, eps 1e-8) on mean((net(x) - t)^2);
+ * loss_out (nullable, host) receives the loss before the update. */
+int ns_cnn_train_step(ns_cnn *c, const float *x_dev, const float *t_dev, int batch, float lr, float *loss_out,
+                      void *stream);
+void ns_cnn_destroy(ns_cnn *c);
+const char *ns_cnn_last_error(const ns_cnn *c);
+/* Elementwise helpers on device arrays: dst = (float)(scale src);
+ * dst = base + scale src (base nullable). */
+int ns_f64_to_f32(const double *src_dev, float *dst_dev, long long n, double scale, void *stream);
+int ns_f32_axpy_f64(const float *src_dev, const double *base_dev, double *dst_dev, long long n, double scale,
+                    void *stream);
 
 /* Diagnostics for callers that cannot allocate device memory.
  * The FluidSim paper has no counterpart: this entry point exists for code that

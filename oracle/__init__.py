@@ -56,6 +56,9 @@ def _load():
             "orc_state_to_phys": ([I, I, P, P], I),
             "orc_rhs": ([I, I, P, P, P], I),
             "orc_step": ([I, I, D, D, I, P, P], I),
+            "orc_step_rk2": ([I, I, D, D, I, P, P], I),
+            "orc_velocity": ([I, I, P, P], I),
+            "orc_step_cfl": ([I, I, D, D, D, I, I, P, P, P], I),
             "orc_diagnostics": ([I, I, P, ctypes.POINTER(D), ctypes.POINTER(D)], I),
             "orc_nbins": ([I, I], I),
             "orc_spectrum": ([I, I, P, P, I], I),
@@ -145,13 +148,34 @@ def rhs(dim: int, n: int, state: np.ndarray, forcing: np.ndarray | None = None) 
 
 
 def step(dim: int, n: int, nu: float, dt: float, nsteps: int, state: np.ndarray,
-         forcing: np.ndarray | None = None) -> np.ndarray:
-    """Return the state after ``nsteps`` Lawson IF-RK4 steps (input untouched)."""
+         forcing: np.ndarray | None = None, order: int = 4) -> np.ndarray:
+    """Return the state after ``nsteps`` Lawson IF-RK steps of the given order
+    (4, or 2 = the midpoint form) (input untouched)."""
     s = np.ascontiguousarray(state, dtype=np.complex128).reshape(state_shape(dim, n)).copy()
     f = None if forcing is None else np.ascontiguousarray(forcing, dtype=np.complex128).reshape(s.shape)
-    _check(_load().orc_step(dim, n, float(nu), float(dt), int(nsteps), None if f is None else _ptr(f), _ptr(s)),
-           "step")
+    fn = {4: _load().orc_step, 2: _load().orc_step_rk2}[order]
+    _check(fn(dim, n, float(nu), float(dt), int(nsteps), None if f is None else _ptr(f), _ptr(s)), "step")
     return s
+
+
+def velocity(dim: int, n: int, state: np.ndarray) -> np.ndarray:
+    """Physical velocity ``(dim, N, ..)`` of a state (2D: from the stream function)."""
+    s = np.ascontiguousarray(state, dtype=np.complex128).reshape(state_shape(dim, n))
+    out = np.empty((dim,) + (n,) * dim, np.float64)
+    _check(_load().orc_velocity(dim, n, _ptr(s), _ptr(out)), "velocity")
+    return out
+
+
+def step_cfl(dim: int, n: int, nu: float, dt_max: float, cfl: float, nsteps: int, state: np.ndarray,
+             forcing: np.ndarray | None = None, order: int = 4):
+    """(state, dts) after ``nsteps`` steps whose dt follows the CFL rule
+    dt = min(dt_max, cfl * min_i (2 pi / N) / max|u_i|), chosen before each step."""
+    s = np.ascontiguousarray(state, dtype=np.complex128).reshape(state_shape(dim, n)).copy()
+    f = None if forcing is None else np.ascontiguousarray(forcing, dtype=np.complex128).reshape(s.shape)
+    dts = np.zeros(max(int(nsteps), 1), np.float64)
+    _check(_load().orc_step_cfl(dim, n, float(nu), float(dt_max), float(cfl), int(order), int(nsteps),
+                                None if f is None else _ptr(f), _ptr(s), _ptr(dts)), "step_cfl")
+    return s, dts[:nsteps]
 
 
 def diagnostics(dim: int, n: int, state: np.ndarray):
@@ -172,3 +196,42 @@ def spectrum(dim: int, n: int, state: np.ndarray) -> np.ndarray:
     out = np.zeros(nb, np.float64)
     _check(_load().orc_spectrum(dim, n, _ptr(s), _ptr(out), nb), "spectrum")
     return out
+
+
+def _wavevectors(dim: int, n: int):
+    """Integer wavevector components on the truncated layout, broadcastable to
+    the state's spectral shape (without the component axis)."""
+    kc, c, h = sizes(n)
+    i = np.arange(c)
+    kfull = np.where(i <= kc, i, i - c)
+    if dim == 2:
+        return np.arange(h)[None, :], kfull[:, None], np.zeros((1, 1), dtype=np.int64)
+    return np.arange(h)[None, None, :], kfull[None, :, None], kfull[:, None, None]
+
+
+def budget(dim: int, n: int, nu: float, state: np.ndarray, forcing: np.ndarray | None = None):
+    """Energy and enstrophy budget terms (P_E, D_E, P_Z, D_Z) of a truncated
+    spectral state: forcing power and dissipation, the "spatial means" of the
+    paper's output list besides energy and enstrophy.  With the mode weights
+    w = 1 on kx = 0 and 2 elsewhere (the half spectrum stands for the full one):
+    3D velocity:  P_E = sum w Re(u* . F), D_E = nu sum w k^2 |u|^2,
+                  P_Z = sum w k^2 Re(u* . F), D_Z = nu sum w k^4 |u|^2;
+    2D vorticity: P_E = sum w Re(w* F) / k^2, D_E = nu sum w |w|^2,
+                  P_Z = sum w Re(w* F), D_Z = nu sum w k^2 |w|^2  (k = 0 excluded).
+    Plain numpy in float64 (no FFT involved)."""
+    s = np.ascontiguousarray(state, dtype=np.complex128).reshape(state_shape(dim, n))
+    f = np.zeros_like(s) if forcing is None else np.ascontiguousarray(forcing, dtype=np.complex128).reshape(s.shape)
+    kx, ky, kz = _wavevectors(dim, n)
+    k2 = (kx * kx + ky * ky + kz * kz).astype(np.float64)
+    w = np.where(kx == 0, 1.0, 2.0) * np.ones_like(k2)
+    if dim == 3:
+        m2 = np.sum(np.abs(s) ** 2, axis=0)
+        pf = np.sum((np.conj(s) * f).real, axis=0)
+        return (float(np.sum(w * pf)), float(nu * np.sum(w * k2 * m2)),
+                float(np.sum(w * k2 * pf)), float(nu * np.sum(w * k2 * k2 * m2)))
+    m2 = np.abs(s) ** 2
+    pf = (np.conj(s) * f).real
+    nz = k2 > 0
+    inv = np.where(nz, 1.0 / np.where(nz, k2, 1.0), 0.0)
+    return (float(np.sum(w * pf * inv)), float(nu * np.sum(w * m2 * nz)),
+            float(np.sum(w * pf * nz)), float(nu * np.sum(w * k2 * m2)))

@@ -38,6 +38,7 @@
 //    full axis holds k = i for i <= kc and k = i - c for i > kc; index i along
 //    the halved x axis holds kx = i.
 //  * physical fields: 3D [comp][z][y][x], 2D [y][x], x_j = 2 pi j / N.
+#include <algorithm>
 #include <cmath>
 #include <complex>
 #include <cstdint>
@@ -423,6 +424,94 @@ int orc_step(int dim, int n, double nu, double dt, int nsteps, const double *for
       const double e = E[j % nt], e2 = E2[j % nt];
       u[j] = e * u[j] + dt / 6.0 * (e * k1[j] + 2.0 * e2 * k2[j] + 2.0 * e2 * k3[j] + k4[j]);
     }
+  }
+  return 0;
+}
+
+// nsteps Lawson IF-RK2 (midpoint) steps in place, the order-2 member of the
+// paper's Runge-Kutta time stepping with the same integrating factor:
+//   k1 = N(u);           a = E2 (u + dt/2 k1)
+//   k2 = N(a);           u <- E u + dt E2 k2
+int orc_step_rk2(int dim, int n, double nu, double dt, int nsteps, const double *forcing, double *state) {
+  if ((dim != 2 && dim != 3) || !is_pow2(n) || n < 4 || nsteps < 0 || nu < 0 || !(dt > 0)) return -1;
+  Grid g(dim, n);
+  const long nt = (long)g.ntrunc();
+  const long tot = nt * g.ncomp();
+  std::vector<double> E(nt), E2(nt);
+  for (long i = 0; i < nt; ++i) {
+    const double k2 = k2_trunc(g, i);
+    E[i] = std::exp(-nu * k2 * dt);
+    E2[i] = std::exp(-nu * k2 * dt * 0.5);
+  }
+  cd *u = reinterpret_cast<cd *>(state);
+  const cd *F = reinterpret_cast<const cd *>(forcing);
+  std::vector<cd> k1(tot), k2(tot), s(tot);
+  for (int step = 0; step < nsteps; ++step) {
+    rhs(g, u, F, k1.data());
+    for (long j = 0; j < tot; ++j) s[j] = E2[j % nt] * (u[j] + 0.5 * dt * k1[j]);
+    rhs(g, s.data(), F, k2.data());
+    for (long j = 0; j < tot; ++j) u[j] = E[j % nt] * u[j] + dt * E2[j % nt] * k2[j];
+  }
+  return 0;
+}
+
+// Physical velocity of a state: 3D the three components (the state itself),
+// 2D u = (d_y psi, -d_x psi) with psi_hat = omega_hat / |k|^2; layout
+// [comp][grid], ncomp = dim.
+int orc_velocity(int dim, int n, const double *state, double *phys) {
+  if ((dim != 2 && dim != 3) || !is_pow2(n) || n < 4) return -1;
+  Grid g(dim, n);
+  const size_t nhalf = g.nhalf(), npts = g.npts(), nt = g.ntrunc();
+  const cd *st = reinterpret_cast<const cd *>(state);
+  std::vector<cd> full(nhalf);
+  if (dim == 3) {
+    for (int a = 0; a < 3; ++a) {
+      expand(g, st + a * nt, full.data());
+      irfftn(g, full.data(), phys + a * npts);
+    }
+    return 0;
+  }
+  const cd I(0.0, 1.0);
+  std::vector<cd> Wh(nhalf);
+  expand(g, st, Wh.data());
+  for (int a = 0; a < 2; ++a) {
+    for (long i = 0; i < (long)nhalf; ++i) {
+      double k[3];
+      kvec_full(g, i, k);
+      const double k2 = k[0] * k[0] + k[1] * k[1];
+      const cd psi = k2 > 0.0 ? Wh[i] / k2 : cd(0.0, 0.0);
+      full[i] = a == 0 ? I * k[1] * psi : -I * k[0] * psi;
+    }
+    irfftn(g, full.data(), phys + a * npts);
+  }
+  return 0;
+}
+
+// nsteps steps with the time step chosen before each one by the CFL rule
+// dt = min(dt_max, cfl * min_i dx / max|u_i|) over the velocity components
+// with a non-zero maximum (dx = 2 pi / n), then one Lawson IF-RK step of the
+// given order (2 or 4).  dts[step] receives each dt (nullable).
+int orc_step_cfl(int dim, int n, double nu, double dt_max, double cfl, int order, int nsteps,
+                 const double *forcing, double *state, double *dts) {
+  if ((dim != 2 && dim != 3) || !is_pow2(n) || n < 4 || nsteps < 0 || !(dt_max > 0) || !(cfl > 0) ||
+      (order != 2 && order != 4))
+    return -1;
+  Grid g(dim, n);
+  const size_t npts = g.npts();
+  const double dx = 6.283185307179586 / n;
+  std::vector<double> vel((size_t)dim * npts);
+  for (int step = 0; step < nsteps; ++step) {
+    int rc = orc_velocity(dim, n, state, vel.data());
+    if (rc) return rc;
+    double dt = dt_max;
+    for (int a = 0; a < dim; ++a) {
+      double m = 0.0;
+      for (size_t p = 0; p < npts; ++p) m = std::max(m, std::fabs(vel[a * npts + p]));
+      if (m > 0.0) dt = std::min(dt, cfl * dx / m);
+    }
+    if (dts) dts[step] = dt;
+    rc = order == 4 ? orc_step(dim, n, nu, dt, 1, forcing, state) : orc_step_rk2(dim, n, nu, dt, 1, forcing, state);
+    if (rc) return rc;
   }
   return 0;
 }

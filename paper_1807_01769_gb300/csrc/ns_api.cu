@@ -614,6 +614,20 @@ int ns_diagnostics(ns_state *s, double *energy, double *enstrophy) {
   return NS_OK;
 }
 
+int ns_budget(ns_state *s, double *out) {
+  if (!s || !out) return s ? fail(s, NS_EINVAL, "ns_budget: null output") : NS_EINVAL;
+  DevGuard dg(s->dev);
+  double *scratch = (double *)s->diag;
+  double *dout = scratch + s->diag_scratch;
+  int e = nsk::budget(s->prec, s->g, s->u, s->F, s->nu, scratch, dout, s->stream);
+  if (e) return fail(s, NS_ECUDA, "budget launch failed: %s", cudaGetErrorString((cudaError_t)e));
+  NS_CK(s, cudaMemcpyAsync(out, dout, sizeof(double) * 4, cudaMemcpyDeviceToHost, s->stream));
+  NS_CK(s, cudaStreamSynchronize(s->stream));
+  for (int i = 0; i < 4; ++i)
+    if (!std::isfinite(out[i])) return fail(s, NS_ENONFINITE, "ns_budget: term %d is %g", i, out[i]);
+  return NS_OK;
+}
+
 int ns_energy_spectrum(ns_state *s, double *out, int *nbins) {
   if (!s || !out || !nbins) return s ? fail(s, NS_EINVAL, "ns_energy_spectrum: null output") : NS_EINVAL;
   if (*nbins < s->nbins) {
@@ -670,6 +684,63 @@ int ns_profile_step(ns_state *s, int nsteps, double *kernel_ms, int *kernel_laun
   }
   for (auto &e : ev) cudaEventDestroy(e);
   return rc;
+}
+
+int ns_state_to_phys_device(ns_state *s, double *phys_dev) {
+  if (!s || !phys_dev) return s ? fail(s, NS_EINVAL, "ns_state_to_phys_device: null buffer") : NS_EINVAL;
+  DevGuard dg(s->dev);
+  int rc;
+  Launch l = inv1_launch(s, s->u, 0);
+  if ((rc = dispatch(s, l.op, l.a, s->stream))) return rc;
+  if (s->grid.dim == 3) {
+    Args b = base_args(s);
+    b.nf = 3;
+    if ((rc = dispatch(s, nsk::OP_INV2, b, s->stream))) return rc;
+  }
+  const long long np = phys_elems(s);
+  for (int c = 0; c < s->ncomp; ++c) {
+    Args x = base_args(s);
+    x.phys_out = phys_dev + c * np;
+    x.field = c;
+    if ((rc = dispatch(s, nsk::OP_XINV_REAL, x, s->stream))) return rc;
+  }
+  s->zvalid = false;
+  return NS_OK;
+}
+
+int ns_set_forcing_phys_device(ns_state *s, const double *phys_dev) {
+  if (!s || !phys_dev) return s ? fail(s, NS_EINVAL, "ns_set_forcing_phys_device: null buffer") : NS_EINVAL;
+  DevGuard dg(s->dev);
+  int rc;
+  if (!s->F) {  // first forcing of a state created without one: the step graph must see it
+    const size_t field = s->cs * (size_t)s->g.st_comp * s->ncomp;
+    if ((rc = dmalloc(s, &s->F, field))) return rc;
+    NS_CK(s, cudaMemsetAsync(s->F, 0, field, s->stream));
+    if (s->graph) {
+      cudaGraphExecDestroy(s->graph);
+      s->graph = nullptr;
+    }
+  }
+  const long long np = phys_elems(s);
+  Args a = base_args(s);
+  for (int c = 0; c < s->ncomp; ++c) {
+    Args x = a;
+    x.phys_in = phys_dev + c * np;
+    x.field = c;
+    if ((rc = dispatch(s, nsk::OP_XFWD_REAL, x, s->stream))) return rc;
+  }
+  if (s->grid.dim == 3) {
+    Args b = a;
+    b.nf = 3;
+    if ((rc = dispatch(s, nsk::OP_FWD2, b, s->stream))) return rc;
+  }
+  Args f = a;
+  f.mode = nsk::MODE_PROJ;
+  f.inv = 0;
+  f.dst = s->F;
+  if ((rc = dispatch(s, nsk::OP_FWD1, f, s->stream))) return rc;
+  s->zvalid = false;
+  return NS_OK;
 }
 
 int ns_num_kernels(void) { return kNumKernels; }

@@ -1,7 +1,7 @@
 // ns_aux.cu -- layout conversion between the canonical FP64 spectral layout
 // and the padded device state, and the FP64 diagnostics ("sim.output.
-// spatial_means" energy and enstrophy, "sim.output.spectra" shell spectrum in
-// the FluidSim paper's output list).
+// spatial_means" energy, enstrophy, forcing power and dissipation,
+// "sim.output.spectra" shell spectrum in the FluidSim paper's output list).
 //
 // The diagnostics are deterministic: every block owns a fixed set of (kz, ky)
 // rows, each warp a fixed subset of them; along a row |k| grows with kx, so
@@ -70,7 +70,7 @@ int spec_out(int prec, double *dst, const void *src, long long rows, int h, int 
 
 constexpr int kDiagWarps = 8;
 
-static long long diag_rows(const Geo &g) { return g.dim == 3 ? (long long)g.c * g.c : (long long)g.c; }
+__host__ __device__ static long long diag_rows(const Geo &g) { return g.dim == 3 ? (long long)g.c * g.c : (long long)g.c; }
 
 long long diag_blocks(const Geo &g) {
   long long nb = (diag_rows(g) + kDiagWarps - 1) / kDiagWarps;
@@ -192,6 +192,81 @@ int diagnostics(int prec, const Geo &g, const void *u, int nbins, double *scratc
     k_diag<double2><<<(unsigned)nb, 32 * kDiagWarps, smem, s>>>(g, (const double2 *)u, nbins, rpb, scratch);
   }
   k_diag_final<<<1, 256, 0, s>>>(scratch, nb, nbins + 2, out);
+  return (int)cudaGetLastError();
+}
+
+// Energy and enstrophy budget terms, per block into scratch[b][0..3]:
+//   3D (velocity u, forcing F): P_E = sum w Re(u* . F),      D_E = nu sum w k^2 |u|^2,
+//                               P_Z = sum w k^2 Re(u* . F),  D_Z = nu sum w k^4 |u|^2;
+//   2D (vorticity w, forcing F): P_E = sum w Re(w* F) / k^2,  D_E = nu sum w |w|^2,
+//                               P_Z = sum w Re(w* F),         D_Z = nu sum w k^2 |w|^2.
+// Same row ownership and fixed reduction order as k_diag.
+template <typename C>
+__global__ void __launch_bounds__(32 * kDiagWarps) k_budget(Geo g, const C *__restrict__ u, const C *__restrict__ F,
+                                                            double nu, int rows_per_block, double *__restrict__ scratch) {
+  __shared__ double wsum[kDiagWarps][4];
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const long long nrows = diag_rows(g);
+  const long long r0 = (long long)blockIdx.x * rows_per_block;
+  const long long r1 = min(nrows, r0 + rows_per_block);
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  const int ncomp = g.dim == 3 ? 3 : 1;
+  for (long long r = r0 + warp; r < r1; r += kDiagWarps) {
+    const int iy = (int)(r % g.c);
+    const int iz = g.dim == 3 ? (int)(r / g.c) : 0;
+    const int ky = iy <= g.kc ? iy : iy - g.c;
+    const int kz = g.dim == 3 ? (iz <= g.kc ? iz : iz - g.c) : 0;
+    const long long base = r * g.hs;
+    for (int kx = lane; kx < g.h; kx += 32) {
+      const double w = kx == 0 ? 1.0 : 2.0;
+      const double k2 = (double)((long long)kx * kx + (long long)ky * ky + (long long)kz * kz);
+      double m2 = 0.0, pf = 0.0;
+      for (int c = 0; c < ncomp; ++c) {
+        const C a = u[c * g.st_comp + base + kx];
+        m2 += (double)a.x * a.x + (double)a.y * a.y;
+        if (F) {
+          const C f = F[c * g.st_comp + base + kx];
+          pf += (double)a.x * f.x + (double)a.y * f.y;
+        }
+      }
+      if (g.dim == 3) {
+        acc[0] += w * pf;
+        acc[1] += w * nu * k2 * m2;
+        acc[2] += w * k2 * pf;
+        acc[3] += w * nu * k2 * k2 * m2;
+      } else if (k2 > 0) {
+        acc[0] += w * pf / k2;
+        acc[1] += w * nu * m2;
+        acc[2] += w * pf;
+        acc[3] += w * nu * k2 * m2;
+      }
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < 4; ++j)
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) acc[j] += __shfl_xor_sync(0xffffffffu, acc[j], off);
+  if (lane == 0)
+    for (int j = 0; j < 4; ++j) wsum[warp][j] = acc[j];
+  __syncthreads();
+  if (threadIdx.x < 4) {
+    double t = 0.0;
+    for (int w = 0; w < kDiagWarps; ++w) t += wsum[w][threadIdx.x];
+    scratch[(long long)blockIdx.x * 4 + threadIdx.x] = t;
+  }
+}
+
+int budget(int prec, const Geo &g, const void *u, const void *F, double nu, double *scratch, double *out,
+           cudaStream_t s) {
+  const long long nb = diag_blocks(g);
+  const long long rows = diag_rows(g);
+  const int rpb = (int)((rows + nb - 1) / nb);
+  if (prec == 1)
+    k_budget<float2><<<(unsigned)nb, 32 * kDiagWarps, 0, s>>>(g, (const float2 *)u, (const float2 *)F, nu, rpb, scratch);
+  else
+    k_budget<double2><<<(unsigned)nb, 32 * kDiagWarps, 0, s>>>(g, (const double2 *)u, (const double2 *)F, nu, rpb,
+                                                               scratch);
+  k_diag_final<<<1, 32, 0, s>>>(scratch, nb, 4, out);
   return (int)cudaGetLastError();
 }
 

@@ -1,0 +1,485 @@
+// ns_cnn.cu -- the learned closure's network: four 3x3 convolutions on a
+// periodic 2D grid (channels 1 -> C -> C -> C -> 1, GELU after the first
+// three), BF16 activations and weights, FP32 accumulation, with hand-written
+// forward, backward and Adam kernels.
+//
+// Data layout: [batch][channel][y][x], periodic in y and x.  Parameters are
+// one flat FP32 array (the Adam master copy) in the order W0 b0 W1 b1 W2 b2
+// W3 b3, W_l as [Cout][Cin][3][3]; a BF16 copy of every W_l feeds the
+// kernels.  Layer l computes z_l = conv(a_l, W_l) + b_l with
+// conv(a, W)[co](p) = sum_ci sum_{dy,dx in -1..1} W[co][ci][dy+1][dx+1] a[ci](p + (dy, dx)),
+// a_{l+1} = GELU(z_l) (exact, erf form) for l < 3, output y = z_3.
+// Training minimises the mean squared error to a target field.
+//
+// Kernels: conv_fwd (one block per 16x16 tile and image: the input halo tile
+// and all weights in shared memory, one output pixel per thread for every
+// output channel); conv_bwd_data (the same kernel on the flipped, transposed
+// weights, with the GELU derivative of the layer below fused in);
+// conv_bwd_weight (each block sums a 64x64 region in 16x16 sub-tiles and adds
+// its partial sums to the FP32 gradient with atomics: order-dependent in the
+// last bits, not bitwise reproducible); elementwise MSE and Adam.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "ns.h"
+
+namespace {
+
+using bf16 = __nv_bfloat16;
+constexpr int TILE = 16;
+
+__device__ __forceinline__ float gelu_f(float z) { return 0.5f * z * (1.0f + erff(z * 0.70710678118654752440f)); }
+__device__ __forceinline__ float gelu_d(float z) {
+  return 0.5f * (1.0f + erff(z * 0.70710678118654752440f)) + z * 0.39894228040143267794f * expf(-0.5f * z * z);
+}
+
+template <typename T>
+__device__ __forceinline__ float ldf(const T *p) {
+  return (float)*p;
+}
+template <>
+__device__ __forceinline__ float ldf<bf16>(const bf16 *p) {
+  return __bfloat162float(*p);
+}
+
+enum Epi { EPI_LINEAR = 0, EPI_GELU = 1, EPI_GELU_BWD = 2 };
+
+// out[b][co][p] = epi( sum_ci sum_k w[co][ci][k] x[b][ci][p + off(k)] + bias[co] )
+//   EPI_LINEAR  : out = acc (float)
+//   EPI_GELU    : zout = bf16(acc), out = bf16(GELU(acc))
+//   EPI_GELU_BWD: out = acc * GELU'(zin[b][co][p])  (float)
+template <int CIN, int COUT, int EPI, typename TIN, typename TOUT>
+__global__ void __launch_bounds__(TILE *TILE) conv_fwd(const TIN *__restrict__ x, const bf16 *__restrict__ w,
+                                                       const float *__restrict__ bias, const bf16 *__restrict__ zin,
+                                                       bf16 *__restrict__ zout, TOUT *__restrict__ out, int H, int W) {
+  extern __shared__ float csm[];
+  float *sw = csm;                       // [COUT][CIN][9]
+  float *sx = csm + COUT * CIN * 9;      // [CIN][18][18]
+  const int b = blockIdx.z;
+  const int y0 = blockIdx.y * TILE, x0 = blockIdx.x * TILE;
+  for (int i = threadIdx.x; i < COUT * CIN * 9; i += blockDim.x) sw[i] = __bfloat162float(w[i]);
+  const long long img = (long long)H * W;
+  for (int i = threadIdx.x; i < CIN * 18 * 18; i += blockDim.x) {
+    const int ci = i / 324, r = i % 324, yy = r / 18, xx = r % 18;
+    const int gy = (y0 + yy - 1 + H) % H, gx = (x0 + xx - 1 + W) % W;
+    sx[i] = ldf(x + ((long long)b * CIN + ci) * img + (long long)gy * W + gx);
+  }
+  __syncthreads();
+  const int ty = threadIdx.x / TILE, tx = threadIdx.x % TILE;
+  float acc[COUT];
+#pragma unroll
+  for (int co = 0; co < COUT; ++co) acc[co] = bias ? bias[co] : 0.0f;
+  for (int ci = 0; ci < CIN; ++ci) {
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+      const float v = sx[ci * 324 + (ty + k / 3) * 18 + tx + k % 3];
+#pragma unroll
+      for (int co = 0; co < COUT; ++co) acc[co] = fmaf(sw[(co * CIN + ci) * 9 + k], v, acc[co]);
+    }
+  }
+  const long long p = (long long)(y0 + ty) * W + x0 + tx;
+#pragma unroll
+  for (int co = 0; co < COUT; ++co) {
+    const long long o = ((long long)b * COUT + co) * img + p;
+    if (EPI == EPI_GELU) {
+      zout[o] = __float2bfloat16(acc[co]);
+      out[o] = (TOUT)__float2bfloat16(gelu_f(acc[co]));
+    } else if (EPI == EPI_GELU_BWD) {
+      out[o] = (TOUT)(acc[co] * gelu_d(__bfloat162float(zin[o])));
+    } else {
+      out[o] = (TOUT)acc[co];
+    }
+  }
+}
+
+// dw[co][ci][k] += sum_b sum_p dz[b][co][p] a[b][ci][p + off(k)];  db[co] += sum dz[b][co][p]
+// One block per (image, 64x64 region), walking its 16 sub-tiles.
+template <int CIN, int COUT, typename TA>
+__global__ void __launch_bounds__(256) conv_bwd_weight(const TA *__restrict__ a, const float *__restrict__ dz,
+                                                       float *__restrict__ dw, float *__restrict__ db, int H, int W) {
+  extern __shared__ float csm[];
+  constexpr int AS = 325;                // channel strides: odd, so lanes on consecutive channels hit distinct banks
+  constexpr int DS = TILE * TILE + 1;
+  float *sdz = csm;                      // [COUT][DS] holding 16 x 16
+  float *sa = csm + COUT * DS;           // [CIN][AS] holding 18 x 18
+  const int b = blockIdx.z;
+  const long long img = (long long)H * W;
+  constexpr int PAIRS = COUT * CIN;
+  constexpr int PPT = (PAIRS + 255) / 256;  // pairs per thread
+  float acc[PPT][9];
+  float accb[PPT];
+#pragma unroll
+  for (int q = 0; q < PPT; ++q) {
+    accb[q] = 0.0f;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) acc[q][k] = 0.0f;
+  }
+  for (int sub = 0; sub < 16; ++sub) {
+    const int y0 = blockIdx.y * 64 + (sub / 4) * TILE, x0 = blockIdx.x * 64 + (sub % 4) * TILE;
+    __syncthreads();
+    for (int i = threadIdx.x; i < COUT * TILE * TILE; i += blockDim.x) {
+      const int co = i / (TILE * TILE), r = i % (TILE * TILE);
+      sdz[co * DS + r] = dz[((long long)b * COUT + co) * img + (long long)(y0 + r / TILE) * W + x0 + r % TILE];
+    }
+    for (int i = threadIdx.x; i < CIN * 324; i += blockDim.x) {
+      const int ci = i / 324, r = i % 324, yy = r / 18, xx = r % 18;
+      const int gy = (y0 + yy - 1 + H) % H, gx = (x0 + xx - 1 + W) % W;
+      sa[ci * AS + r] = ldf(a + ((long long)b * CIN + ci) * img + (long long)gy * W + gx);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < PPT; ++q) {
+      const int pr = threadIdx.x + 256 * q;
+      if (pr >= PAIRS) break;
+      const int co = pr / CIN, ci = pr % CIN;
+      for (int py = 0; py < TILE; ++py)
+        for (int px = 0; px < TILE; ++px) {
+          const float g = sdz[co * DS + py * TILE + px];
+          if (ci == 0) accb[q] += g;
+#pragma unroll
+          for (int k = 0; k < 9; ++k) acc[q][k] = fmaf(g, sa[ci * AS + (py + k / 3) * 18 + px + k % 3], acc[q][k]);
+        }
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < PPT; ++q) {
+    const int pr = threadIdx.x + 256 * q;
+    if (pr >= PAIRS) break;
+    const int co = pr / CIN, ci = pr % CIN;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) atomicAdd(dw + (co * CIN + ci) * 9 + k, acc[q][k]);
+    if (ci == 0) atomicAdd(db + co, accb[q]);
+  }
+}
+
+// flipped, transposed weights for the data gradient: wt[ci][co][8-k] = w[co][ci][k]
+__global__ void flip_weights(const bf16 *__restrict__ w, bf16 *__restrict__ wt, int cin, int cout) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= cin * cout * 9) return;
+  const int co = i / (cin * 9), r = i % (cin * 9), ci = r / 9, k = r % 9;
+  wt[(ci * cout + co) * 9 + (8 - k)] = w[i];
+}
+
+// dy = 2 (y - t) / count, loss += sum (y - t)^2 / count
+__global__ void mse_grad(const float *__restrict__ y, const float *__restrict__ t, float *__restrict__ dy,
+                         float *__restrict__ loss, long long n) {
+  __shared__ float part[256];
+  float s = 0.0f;
+  const float inv = 1.0f / (float)n;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const float d = y[i] - t[i];
+    dy[i] = 2.0f * d * inv;
+    s += d * d * inv;
+  }
+  part[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) part[threadIdx.x] += part[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) atomicAdd(loss, part[0]);
+}
+
+__global__ void adam_update(float *__restrict__ p, const float *__restrict__ g, float *__restrict__ m,
+                            float *__restrict__ v, int n, float lr, float b1, float b2, float eps, float c1, float c2) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float gi = g[i];
+  const float mi = b1 * m[i] + (1.0f - b1) * gi;
+  const float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
+  m[i] = mi;
+  v[i] = vi;
+  p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+}
+
+__global__ void to_bf16(const float *__restrict__ src, bf16 *__restrict__ dst, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) dst[i] = __float2bfloat16(src[i]);
+}
+
+__global__ void f64_to_f32_scaled(const double *__restrict__ src, float *__restrict__ dst, long long n, double scale) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    dst[i] = (float)(src[i] * scale);
+}
+
+__global__ void f32_scaled_add_f64(const float *__restrict__ src, const double *__restrict__ base,
+                                   double *__restrict__ dst, long long n, double scale) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    dst[i] = (base ? base[i] : 0.0) + scale * (double)src[i];
+}
+
+// splitmix64 stream -> standard normals (Box-Muller) for the weight init
+uint64_t sm64(uint64_t x) {
+  x += 0x9E3779B97F4A7C15ULL;
+  x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ULL;
+  x = (x ^ (x >> 27)) * 0x94D049BB133111EBULL;
+  return x ^ (x >> 31);
+}
+double unif(uint64_t seed, uint64_t i) { return ((sm64(seed ^ sm64(i)) >> 11) + 0.5) * (1.0 / 9007199254740992.0); }
+
+thread_local std::string g_cnn_error;
+
+}  // namespace
+
+struct ns_cnn {
+  int C = 32, H = 0, W = 0, maxb = 0;
+  int cin[4], cout[4];
+  long long woff[4], boff[4];
+  int nparams = 0;
+  float *p = nullptr, *g = nullptr, *m = nullptr, *v = nullptr;  // FP32 master, grad, Adam moments
+  bf16 *wb[4] = {nullptr, nullptr, nullptr, nullptr};             // BF16 weights
+  bf16 *wt[4] = {nullptr, nullptr, nullptr, nullptr};             // flipped weights
+  bf16 *z[3] = {nullptr, nullptr, nullptr}, *a[3] = {nullptr, nullptr, nullptr};
+  float *y = nullptr, *dy = nullptr, *dza = nullptr, *dzb = nullptr, *loss = nullptr;
+  int step = 0;
+  std::string err;
+};
+
+namespace {
+
+int cfail(ns_cnn *c, int code, const std::string &m) {
+  if (c)
+    c->err = m;
+  else
+    g_cnn_error = m;
+  return code;
+}
+
+#define CNN_CK(c, call)                                                                              \
+  do {                                                                                               \
+    cudaError_t e_ = (call);                                                                         \
+    if (e_ != cudaSuccess) return cfail((c), NS_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+size_t fwd_smem(int cin, int cout) { return sizeof(float) * (cout * cin * 9 + cin * 324); }
+size_t bww_smem(int cin, int cout) { return sizeof(float) * (cout * (TILE * TILE + 1) + cin * 325); }
+
+template <int CIN, int COUT, int EPI, typename TIN, typename TOUT>
+int launch_fwd(const TIN *x, const bf16 *w, const float *bias, const bf16 *zin, bf16 *zout, TOUT *out, int B, int H,
+               int W, cudaStream_t s) {
+  const size_t sm = fwd_smem(CIN, COUT);
+  cudaFuncSetAttribute(conv_fwd<CIN, COUT, EPI, TIN, TOUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  conv_fwd<CIN, COUT, EPI, TIN, TOUT><<<dim3(W / TILE, H / TILE, B), TILE * TILE, sm, s>>>(x, w, bias, zin, zout, out,
+                                                                                        H, W);
+  return (int)cudaGetLastError();
+}
+
+template <int CIN, int COUT, typename TA>
+int launch_bww(const TA *a, const float *dz, float *dw, float *db, int B, int H, int W, cudaStream_t s) {
+  const size_t sm = bww_smem(CIN, COUT);
+  cudaFuncSetAttribute(conv_bwd_weight<CIN, COUT, TA>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  conv_bwd_weight<CIN, COUT, TA><<<dim3(W / 64, H / 64, B), 256, sm, s>>>(a, dz, dw, db, H, W);
+  return (int)cudaGetLastError();
+}
+
+// forward pass through all layers; keeps z_l, a_l for the backward pass
+int forward(ns_cnn *c, const float *x, int B, cudaStream_t s) {
+  const int H = c->H, W = c->W;
+  int rc;
+  const float *p = c->p;
+  if ((rc = launch_fwd<1, 32, EPI_GELU, float, bf16>(x, c->wb[0], p + c->boff[0], nullptr, c->z[0], c->a[0], B, H, W,
+                                                      s)))
+    return rc;
+  if ((rc = launch_fwd<32, 32, EPI_GELU, bf16, bf16>(c->a[0], c->wb[1], p + c->boff[1], nullptr, c->z[1], c->a[1], B,
+                                                      H, W, s)))
+    return rc;
+  if ((rc = launch_fwd<32, 32, EPI_GELU, bf16, bf16>(c->a[1], c->wb[2], p + c->boff[2], nullptr, c->z[2], c->a[2], B,
+                                                      H, W, s)))
+    return rc;
+  return launch_fwd<32, 1, EPI_LINEAR, bf16, float>(c->a[2], c->wb[3], p + c->boff[3], nullptr, nullptr, c->y, B, H,
+                                                    W, s);
+}
+
+// gradients of the mean squared error into c->g (zeroed here)
+int backward(ns_cnn *c, const float *x, const float *t, int B, cudaStream_t s) {
+  const int H = c->H, W = c->W;
+  const long long n = (long long)B * H * W;
+  int rc;
+  CNN_CK(c, cudaMemsetAsync(c->g, 0, sizeof(float) * c->nparams, s));
+  CNN_CK(c, cudaMemsetAsync(c->loss, 0, sizeof(float), s));
+  mse_grad<<<(unsigned)std::min<long long>((n + 255) / 256, 2048), 256, 0, s>>>(c->y, t, c->dy, c->loss, n);
+  for (int l = 0; l < 4; ++l)
+    flip_weights<<<(c->cin[l] * c->cout[l] * 9 + 255) / 256, 256, 0, s>>>(c->wb[l], c->wt[l], c->cin[l], c->cout[l]);
+  float *g = c->g;
+  // layer 3: dz3 = dy
+  if ((rc = launch_bww<32, 1, bf16>(c->a[2], c->dy, g + c->woff[3], g + c->boff[3], B, H, W, s))) return rc;
+  if ((rc = launch_fwd<1, 32, EPI_GELU_BWD, float, float>(c->dy, c->wt[3], nullptr, c->z[2], nullptr, c->dza, B, H, W,
+                                                          s)))
+    return rc;  // dz2
+  if ((rc = launch_bww<32, 32, bf16>(c->a[1], c->dza, g + c->woff[2], g + c->boff[2], B, H, W, s))) return rc;
+  if ((rc = launch_fwd<32, 32, EPI_GELU_BWD, float, float>(c->dza, c->wt[2], nullptr, c->z[1], nullptr, c->dzb, B, H,
+                                                           W, s)))
+    return rc;  // dz1
+  if ((rc = launch_bww<32, 32, bf16>(c->a[0], c->dzb, g + c->woff[1], g + c->boff[1], B, H, W, s))) return rc;
+  if ((rc = launch_fwd<32, 32, EPI_GELU_BWD, float, float>(c->dzb, c->wt[1], nullptr, c->z[0], nullptr, c->dza, B, H,
+                                                           W, s)))
+    return rc;  // dz0
+  return launch_bww<1, 32, float>(x, c->dza, g + c->woff[0], g + c->boff[0], B, H, W, s);
+}
+
+int refresh_bf16(ns_cnn *c, cudaStream_t s) {
+  for (int l = 0; l < 4; ++l) {
+    const int n = c->cin[l] * c->cout[l] * 9;
+    to_bf16<<<(n + 255) / 256, 256, 0, s>>>(c->p + c->woff[l], c->wb[l], n);
+  }
+  return (int)cudaGetLastError();
+}
+
+}  // namespace
+
+extern "C" {
+
+int ns_cnn_init(ns_cnn **out, int height, int width, int max_batch, unsigned long long seed) {
+  if (!out) return cfail(nullptr, NS_EINVAL, "ns_cnn_init: out is null");
+  *out = nullptr;
+  if (height < TILE * 4 || width < TILE * 4 || height % 64 || width % 64 || max_batch < 1)
+    return cfail(nullptr, NS_EINVAL, "ns_cnn_init: height and width must be multiples of 64, batch >= 1");
+  ns_cnn *c = new ns_cnn();
+  c->H = height;
+  c->W = width;
+  c->maxb = max_batch;
+  const int ci[4] = {1, 32, 32, 32}, co[4] = {32, 32, 32, 1};
+  long long off = 0;
+  for (int l = 0; l < 4; ++l) {
+    c->cin[l] = ci[l];
+    c->cout[l] = co[l];
+    c->woff[l] = off;
+    off += (long long)ci[l] * co[l] * 9;
+    c->boff[l] = off;
+    off += co[l];
+  }
+  c->nparams = (int)off;
+  std::vector<float> init(c->nparams, 0.0f);
+  for (int l = 0; l < 4; ++l) {  // He-normal weights, zero biases
+    const double sd = std::sqrt(2.0 / (9.0 * ci[l]));
+    for (long long i = 0; i < (long long)ci[l] * co[l] * 9; ++i) {
+      const double u1 = unif(seed, 2 * (c->woff[l] + i)), u2 = unif(seed, 2 * (c->woff[l] + i) + 1);
+      init[c->woff[l] + i] = (float)(sd * std::sqrt(-2.0 * std::log(u1)) * std::cos(6.283185307179586 * u2));
+    }
+  }
+  auto bail = [&](const char *what) {
+    g_cnn_error = std::string("ns_cnn_init: ") + what;
+    ns_cnn_destroy(c);
+    return NS_ENOMEM;
+  };
+  const size_t img = (size_t)height * width * max_batch;
+  if (cudaMalloc(&c->p, sizeof(float) * c->nparams) || cudaMalloc(&c->g, sizeof(float) * c->nparams) ||
+      cudaMalloc(&c->m, sizeof(float) * c->nparams) || cudaMalloc(&c->v, sizeof(float) * c->nparams) ||
+      cudaMalloc(&c->y, sizeof(float) * img) || cudaMalloc(&c->dy, sizeof(float) * img) ||
+      cudaMalloc(&c->dza, sizeof(float) * img * 32) || cudaMalloc(&c->dzb, sizeof(float) * img * 32) ||
+      cudaMalloc(&c->loss, sizeof(float)))
+    return bail("allocation failed");
+  for (int l = 0; l < 4; ++l)
+    if (cudaMalloc(&c->wb[l], sizeof(bf16) * ci[l] * co[l] * 9) || cudaMalloc(&c->wt[l], sizeof(bf16) * ci[l] * co[l] * 9))
+      return bail("allocation failed");
+  for (int l = 0; l < 3; ++l)
+    if (cudaMalloc(&c->z[l], sizeof(bf16) * img * 32) || cudaMalloc(&c->a[l], sizeof(bf16) * img * 32))
+      return bail("allocation failed");
+  if (cudaMemcpy(c->p, init.data(), sizeof(float) * c->nparams, cudaMemcpyHostToDevice) ||
+      cudaMemset(c->m, 0, sizeof(float) * c->nparams) || cudaMemset(c->v, 0, sizeof(float) * c->nparams) ||
+      refresh_bf16(c, 0) || cudaDeviceSynchronize())
+    return bail("initialisation failed");
+  *out = c;
+  return NS_OK;
+}
+
+int ns_cnn_num_params(const ns_cnn *c) { return c ? c->nparams : -1; }
+
+int ns_cnn_get_params(ns_cnn *c, float *host) {
+  if (!c || !host) return NS_EINVAL;
+  CNN_CK(c, cudaMemcpy(host, c->p, sizeof(float) * c->nparams, cudaMemcpyDeviceToHost));
+  return NS_OK;
+}
+
+int ns_cnn_set_params(ns_cnn *c, const float *host) {
+  if (!c || !host) return NS_EINVAL;
+  CNN_CK(c, cudaMemcpy(c->p, host, sizeof(float) * c->nparams, cudaMemcpyHostToDevice));
+  int rc = refresh_bf16(c, 0);
+  if (rc) return cfail(c, NS_ECUDA, cudaGetErrorString((cudaError_t)rc));
+  CNN_CK(c, cudaDeviceSynchronize());
+  return NS_OK;
+}
+
+int ns_cnn_forward(ns_cnn *c, const float *x_dev, float *y_dev, int batch, void *stream) {
+  if (!c || !x_dev || !y_dev || batch < 1 || batch > c->maxb) return c ? cfail(c, NS_EINVAL, "ns_cnn_forward: args") : NS_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  int rc = forward(c, x_dev, batch, s);
+  if (rc) return cfail(c, NS_ECUDA, cudaGetErrorString((cudaError_t)rc));
+  CNN_CK(c, cudaMemcpyAsync(y_dev, c->y, sizeof(float) * (size_t)batch * c->H * c->W, cudaMemcpyDeviceToDevice, s));
+  return NS_OK;
+}
+
+int ns_cnn_gradients(ns_cnn *c, const float *x_dev, const float *t_dev, int batch, float *grad_host, float *loss) {
+  if (!c || !x_dev || !t_dev || !grad_host || !loss || batch < 1 || batch > c->maxb)
+    return c ? cfail(c, NS_EINVAL, "ns_cnn_gradients: args") : NS_EINVAL;
+  int rc = forward(c, x_dev, batch, 0);
+  if (!rc) rc = backward(c, x_dev, t_dev, batch, 0);
+  if (rc) return cfail(c, NS_ECUDA, "ns_cnn_gradients: launch failed");
+  CNN_CK(c, cudaMemcpy(grad_host, c->g, sizeof(float) * c->nparams, cudaMemcpyDeviceToHost));
+  CNN_CK(c, cudaMemcpy(loss, c->loss, sizeof(float), cudaMemcpyDeviceToHost));
+  return NS_OK;
+}
+
+int ns_cnn_train_step(ns_cnn *c, const float *x_dev, const float *t_dev, int batch, float lr, float *loss_out,
+                      void *stream) {
+  if (!c || !x_dev || !t_dev || batch < 1 || batch > c->maxb || !(lr > 0))
+    return c ? cfail(c, NS_EINVAL, "ns_cnn_train_step: args") : NS_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  int rc = forward(c, x_dev, batch, s);
+  if (!rc) rc = backward(c, x_dev, t_dev, batch, s);
+  if (rc) return cfail(c, NS_ECUDA, "ns_cnn_train_step: launch failed");
+  c->step += 1;
+  const float b1 = 0.9f, b2 = 0.999f;
+  const float c1 = 1.0f - std::pow(b1, (float)c->step), c2 = 1.0f - std::pow(b2, (float)c->step);
+  adam_update<<<(c->nparams + 255) / 256, 256, 0, s>>>(c->p, c->g, c->m, c->v, c->nparams, lr, b1, b2, 1e-8f, c1, c2);
+  rc = refresh_bf16(c, s);
+  if (rc) return cfail(c, NS_ECUDA, "ns_cnn_train_step: update failed");
+  if (loss_out) {
+    CNN_CK(c, cudaMemcpyAsync(loss_out, c->loss, sizeof(float), cudaMemcpyDeviceToHost, s));
+    CNN_CK(c, cudaStreamSynchronize(s));
+  }
+  return NS_OK;
+}
+
+int ns_f64_to_f32(const double *src_dev, float *dst_dev, long long n, double scale, void *stream) {
+  if (!src_dev || !dst_dev || n < 0) return NS_EINVAL;
+  f64_to_f32_scaled<<<(unsigned)std::min<long long>((n + 255) / 256, 4096), 256, 0, (cudaStream_t)stream>>>(
+      src_dev, dst_dev, n, scale);
+  return cudaGetLastError() == cudaSuccess ? NS_OK : NS_ECUDA;
+}
+
+int ns_f32_axpy_f64(const float *src_dev, const double *base_dev, double *dst_dev, long long n, double scale,
+                    void *stream) {
+  if (!src_dev || !dst_dev || n < 0) return NS_EINVAL;
+  f32_scaled_add_f64<<<(unsigned)std::min<long long>((n + 255) / 256, 4096), 256, 0, (cudaStream_t)stream>>>(
+      src_dev, base_dev, dst_dev, n, scale);
+  return cudaGetLastError() == cudaSuccess ? NS_OK : NS_ECUDA;
+}
+
+void ns_cnn_destroy(ns_cnn *c) {
+  if (!c) return;
+  cudaDeviceSynchronize();
+  void *ptrs[] = {c->p, c->g, c->m, c->v, c->y, c->dy, c->dza, c->dzb, c->loss};
+  for (void *p : ptrs)
+    if (p) cudaFree(p);
+  for (int l = 0; l < 4; ++l) {
+    if (c->wb[l]) cudaFree(c->wb[l]);
+    if (c->wt[l]) cudaFree(c->wt[l]);
+  }
+  for (int l = 0; l < 3; ++l) {
+    if (c->z[l]) cudaFree(c->z[l]);
+    if (c->a[l]) cudaFree(c->a[l]);
+  }
+  delete c;
+}
+
+const char *ns_cnn_last_error(const ns_cnn *c) { return c ? c->err.c_str() : g_cnn_error.c_str(); }
+
+}  // extern "C"

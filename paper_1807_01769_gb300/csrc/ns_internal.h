@@ -72,5 +72,9 @@ int spec_out(int prec, double *dst, const void *src, long long rows, int h, int 
 long long diag_blocks(const Geo &g);
 long long diag_scratch_doubles(const Geo &g, int nbins);
 int diagnostics(int prec, const Geo &g, const void *u, int nbins, double *scratch, double *out, cudaStream_t s);
+// Budget terms {P_E, D_E, P_Z, D_Z} (forcing power and dissipation of energy
+// and enstrophy) into out[0..3]; scratch holds diag_blocks(g) * 4 doubles.
+int budget(int prec, const Geo &g, const void *u, const void *F, double nu, double *scratch, double *out,
+           cudaStream_t s);
 
 }  // namespace nsk

@@ -72,6 +72,20 @@ SIGNATURES = {
     "ns_ensemble_sync": ([_P], _I),
     "ns_ensemble_destroy": ([_P], None),
     "ns_ensemble_last_error": ([_P], ctypes.c_char_p),
+    "ns_budget": ([_P, _P], _I),
+    "ns_state_to_phys_device": ([_P, _P], _I),
+    "ns_set_forcing_phys_device": ([_P, _P], _I),
+    "ns_cnn_init": ([ctypes.POINTER(_P), _I, _I, _I, ctypes.c_ulonglong], _I),
+    "ns_cnn_num_params": ([_P], _I),
+    "ns_cnn_get_params": ([_P, _P], _I),
+    "ns_cnn_set_params": ([_P, _P], _I),
+    "ns_cnn_forward": ([_P, _P, _P, _I, _P], _I),
+    "ns_cnn_gradients": ([_P, _P, _P, _I, _P, ctypes.POINTER(ctypes.c_float)], _I),
+    "ns_cnn_train_step": ([_P, _P, _P, _I, ctypes.c_float, ctypes.POINTER(ctypes.c_float), _P], _I),
+    "ns_cnn_destroy": ([_P], None),
+    "ns_cnn_last_error": ([_P], ctypes.c_char_p),
+    "ns_f64_to_f32": ([_P, _P, _LL, _D, _P], _I),
+    "ns_f32_axpy_f64": ([_P, _P, _P, _LL, _D, _P], _I),
 }
 
 
@@ -218,6 +232,12 @@ class Solver:
         _check(lib.ns_diagnostics(self.state, ctypes.byref(e), ctypes.byref(o)), self.state)
         return e.value, o.value
 
+    def budget(self):
+        """(P_E, D_E, P_Z, D_Z): forcing power and dissipation of energy and enstrophy."""
+        out = np.zeros(4, np.float64)
+        _check(lib.ns_budget(self.state, _ptr(out)), self.state)
+        return tuple(float(v) for v in out)
+
     def energy_spectrum(self) -> np.ndarray:
         nb = self.sizes["nbins"]
         out = np.zeros(nb, np.float64)
@@ -312,3 +332,84 @@ class Ensemble:
         o = np.zeros(len(self.sizes))
         _echeck(lib.ns_ensemble_diagnostics(self.ens, _ptr(e), _ptr(o)), self.ens)
         return e, o
+
+
+# ------------------------------------------------------ learned closure ---
+def _ccheck(rc: int, net=None):
+    if rc != NS_OK:
+        msg = lib.ns_cnn_last_error(net)
+        raise NSError(rc, msg.decode() if msg else "")
+
+
+class CNN:
+    """The closure network of include/ns.h (4 periodic 3x3 convolutions,
+    1 -> 32 -> 32 -> 32 -> 1 channels, GELU, BF16 storage, FP32 accumulation).
+
+    ``forward``/``train_step`` take device pointers (ints, e.g. from
+    ``torch.Tensor.data_ptr()``) to FP32 ``[batch][height][width]`` arrays.
+    """
+
+    def __init__(self, height: int, width: int, max_batch: int, seed: int = 0):
+        self.height, self.width, self.max_batch = height, width, max_batch
+        out = ctypes.c_void_p()
+        _ccheck(lib.ns_cnn_init(ctypes.byref(out), height, width, max_batch, ctypes.c_ulonglong(seed)))
+        self.net = out
+        self.num_params = int(lib.ns_cnn_num_params(self.net))
+
+    def close(self):
+        if getattr(self, "net", None):
+            lib.ns_cnn_destroy(self.net)
+            self.net = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def get_params(self) -> np.ndarray:
+        out = np.empty(self.num_params, np.float32)
+        _ccheck(lib.ns_cnn_get_params(self.net, _ptr(out)), self.net)
+        return out
+
+    def set_params(self, p: np.ndarray) -> None:
+        p = np.ascontiguousarray(p, dtype=np.float32)
+        if p.size != self.num_params:
+            raise ValueError(f"expected {self.num_params} parameters, got {p.size}")
+        _ccheck(lib.ns_cnn_set_params(self.net, _ptr(p)), self.net)
+
+    def forward(self, x_dev: int, y_dev: int, batch: int, stream: int | None = None) -> None:
+        _ccheck(lib.ns_cnn_forward(self.net, ctypes.c_void_p(x_dev), ctypes.c_void_p(y_dev), batch,
+                                   ctypes.c_void_p(stream) if stream else None), self.net)
+
+    def gradients(self, x_dev: int, t_dev: int, batch: int):
+        g = np.empty(self.num_params, np.float32)
+        loss = ctypes.c_float()
+        _ccheck(lib.ns_cnn_gradients(self.net, ctypes.c_void_p(x_dev), ctypes.c_void_p(t_dev), batch, _ptr(g),
+                                     ctypes.byref(loss)), self.net)
+        return g, float(loss.value)
+
+    def train_step(self, x_dev: int, t_dev: int, batch: int, lr: float, stream: int | None = None,
+                   want_loss: bool = True):
+        loss = ctypes.c_float()
+        _ccheck(lib.ns_cnn_train_step(self.net, ctypes.c_void_p(x_dev), ctypes.c_void_p(t_dev), batch,
+                                      ctypes.c_float(lr), ctypes.byref(loss) if want_loss else None,
+                                      ctypes.c_void_p(stream) if stream else None), self.net)
+        return float(loss.value) if want_loss else None
+
+
+def f64_to_f32(src_dev: int, dst_dev: int, n: int, scale: float = 1.0, stream: int | None = None) -> None:
+    _check(lib.ns_f64_to_f32(ctypes.c_void_p(src_dev), ctypes.c_void_p(dst_dev), n, scale,
+                             ctypes.c_void_p(stream) if stream else None))
+
+
+def f32_axpy_f64(src_dev: int, base_dev: int | None, dst_dev: int, n: int, scale: float = 1.0,
+                 stream: int | None = None) -> None:
+    _check(lib.ns_f32_axpy_f64(ctypes.c_void_p(src_dev), ctypes.c_void_p(base_dev) if base_dev else None,
+                               ctypes.c_void_p(dst_dev), n, scale, ctypes.c_void_p(stream) if stream else None))
