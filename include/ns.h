@@ -107,6 +107,29 @@ int ns_get_state_spectral(ns_state *s, double *spec_host);
  * work is enqueued on the state's stream (a captured CUDA graph per step). */
 int ns_step(ns_state *s, int nsteps);
 
+/* Time-stepping scheme ("sim.time_stepping": Runge-Kutta of order 2 or 4 with
+ * the exact integrating factor for viscosity): order 4 (default) is the
+ * Lawson IF-RK4 step above; order 2 the Lawson IF-RK2 midpoint step
+ *   a = E2 (u + dt/2 N(u)),  u <- E u + dt E2 N(a).
+ * NS_EINVAL for any other order.  Synchronises; the next ns_step captures a
+ * new step graph. */
+int ns_set_scheme(ns_state *s, int order);
+
+/* CFL-adaptive time step ("sim.time_stepping" determines dt from the CFL
+ * criterion): with cfl > 0 every step first takes
+ *   dt = min(dt_init, cfl * (2 pi / N) / max_i max_x |u_i(x)|)
+ * over the velocity components with a non-zero maximum (dt_init = the dt of
+ * ns_init), the maxima taken on the grid points by the first x pass of the
+ * step, and integrates with it; dt and the integrating factors are updated on
+ * the device inside the step graph, so stepping stays asynchronous.  cfl = 0
+ * returns to the constant dt_init.  NS_EINVAL for cfl < 0 or not finite.
+ * Synchronises. */
+int ns_set_cfl(ns_state *s, double cfl);
+
+/* Simulated time (sum of the steps taken since ns_init) and the dt of the
+ * last step (the constant dt without CFL).  Synchronises when CFL is on. */
+int ns_get_time(ns_state *s, double *t, double *dt);
+
 /* One evaluation of the nonlinear term N(state) (forcing included), written
  * to a host buffer in the canonical spectral layout.  Synchronises. */
 int ns_eval_rhs(ns_state *s, double *rhs_host);

@@ -74,6 +74,12 @@ struct ns_state {
   long long bytes = 0;
   bool zvalid = false;
   cudaGraphExec_t graph = nullptr;
+  // time stepping: Lawson IF-RK of order 4 or 2; CFL-adaptive dt when cfl > 0
+  // (dt then lives in ctl = {dt, t, dt_max, cfl} on the device, dt_max = dt)
+  int order = 4;
+  double cfl = 0, t = 0;
+  unsigned long long *umax = nullptr;
+  double *ctl = nullptr;
   // 3D step schedule: the y inverse, x pass and y forward of a stage run as a
   // pipeline over zchunks plane chunks on three forked streams, the y inverse
   // at most zlook chunks ahead of the x pass
@@ -118,7 +124,9 @@ int dmalloc(ns_state *s, void **p, size_t bytes) {
 
 int dispatch(ns_state *s, int op, const Args &a, cudaStream_t st) {
   int rc;
-  if (s->grid.dim == 3)
+  if (op == nsk::OP_CFL)
+    rc = nsk::cfl_update(s->prec, s->g, s->nu, s->umax, s->ctl, s->ef, s->ef2, st);
+  else if (s->grid.dim == 3)
     rc = s->prec == NS_FP32 ? nsk::dispatch3_f32(op, a, st) : nsk::dispatch3_f64(op, a, st);
   else
     rc = s->prec == NS_FP32 ? nsk::dispatch2_f32(op, a, st) : nsk::dispatch2_f64(op, a, st);
@@ -141,6 +149,7 @@ Args base_args(ns_state *s) {
   a.zb = s->zb;
   a.yb = s->yb;
   a.dt = s->dt;
+  a.dtp = s->cfl > 0 ? s->ctl : nullptr;
   a.nsm = s->nsm;
   return a;
 }
@@ -159,17 +168,23 @@ Launch inv1_launch(ns_state *s, const void *src, int curl) {
   return {nsk::OP_INV1, 0, a};
 }
 
-void stage_launches(ns_state *s, int mode, bool inv, void *dst, std::vector<Launch> &out) {
+// One RK stage; with cfl_stage the x pass also records max |u_i| and the CFL
+// kernel sets dt (and the factor tables) before the stage's fwd1.
+void stage_launches(ns_state *s, int mode, bool inv, void *dst, std::vector<Launch> &out, bool cfl_stage = false) {
   Args a = base_args(s);
+  Args x = a;
+  if (cfl_stage) x.umax = s->umax;
   if (s->grid.dim == 3) {
     Args b = a;
     b.nf = 6;
     out.push_back({nsk::OP_INV2, 1, b});
-    out.push_back({nsk::OP_XPASS, 2, a});
+    out.push_back({nsk::OP_XPASS, 2, x});
+    if (cfl_stage) out.push_back({nsk::OP_CFL, 2, a});
     b.nf = 3;
     out.push_back({nsk::OP_FWD2, 3, b});
   } else {
-    out.push_back({nsk::OP_XPASS, 2, a});
+    out.push_back({nsk::OP_XPASS, 2, x});
+    if (cfl_stage) out.push_back({nsk::OP_CFL, 2, a});
   }
   Args f = a;
   f.mode = mode;
@@ -178,9 +193,16 @@ void stage_launches(ns_state *s, int mode, bool inv, void *dst, std::vector<Laun
   out.push_back({nsk::OP_FWD1, 4, f});
 }
 
+// RK stage modes of one step: Lawson IF-RK4 (four stages) or IF-RK2 midpoint (two)
+std::vector<int> stage_modes(const ns_state *s) {
+  if (s->order == 2) return {nsk::MODE_M1, nsk::MODE_M2};
+  return {nsk::MODE_RK1, nsk::MODE_RK2, nsk::MODE_RK3, nsk::MODE_RK4};
+}
+
 std::vector<Launch> step_launches(ns_state *s) {
   std::vector<Launch> v;
-  for (int st = 1; st <= 4; ++st) stage_launches(s, st, true, nullptr, v);
+  const std::vector<int> modes = stage_modes(s);
+  for (size_t i = 0; i < modes.size(); ++i) stage_launches(s, modes[i], true, nullptr, v, i == 0 && s->cfl > 0);
   return v;
 }
 
@@ -196,7 +218,9 @@ int run_launches(ns_state *s, const std::vector<Launch> &v, cudaStream_t st) {
 int capture_pipelined_step(ns_state *s) {
   const int K = s->zchunks, D = s->zlook, N = s->grid.n, nzc = N / K;
   cudaEvent_t *evA = s->pev.data(), *evB = evA + K, *evC = evB + K, start = evC[K];
-  for (int st = 1; st <= 4; ++st) {
+  const std::vector<int> modes = stage_modes(s);
+  for (size_t si = 0; si < modes.size(); ++si) {
+    const bool cfl_stage = si == 0 && s->cfl > 0;
     NS_CK(s, cudaEventRecord(start, s->cap));
     for (int i = 0; i < 3; ++i) NS_CK(s, cudaStreamWaitEvent(s->pipe[i], start, 0));
     for (int c = 0; c < K; ++c) {
@@ -210,7 +234,9 @@ int capture_pipelined_step(ns_state *s) {
       if ((rc = dispatch(s, nsk::OP_INV2, b, s->pipe[0]))) return rc;
       NS_CK(s, cudaEventRecord(evA[c], s->pipe[0]));
       NS_CK(s, cudaStreamWaitEvent(s->pipe[1], evA[c], 0));
-      if ((rc = dispatch(s, nsk::OP_XPASS, a, s->pipe[1]))) return rc;
+      Args x = a;
+      if (cfl_stage) x.umax = s->umax;
+      if ((rc = dispatch(s, nsk::OP_XPASS, x, s->pipe[1]))) return rc;
       NS_CK(s, cudaEventRecord(evB[c], s->pipe[1]));
       NS_CK(s, cudaStreamWaitEvent(s->pipe[2], evB[c], 0));
       b.nf = 3;
@@ -220,10 +246,12 @@ int capture_pipelined_step(ns_state *s) {
     NS_CK(s, cudaStreamWaitEvent(s->cap, evA[K - 1], 0));
     NS_CK(s, cudaStreamWaitEvent(s->cap, evB[K - 1], 0));
     NS_CK(s, cudaStreamWaitEvent(s->cap, evC[K - 1], 0));
+    int rc;
+    if (cfl_stage && (rc = dispatch(s, nsk::OP_CFL, base_args(s), s->cap))) return rc;
     Args f = base_args(s);
-    f.mode = st;
+    f.mode = modes[si];
     f.inv = 1;
-    int rc = dispatch(s, nsk::OP_FWD1, f, s->cap);
+    rc = dispatch(s, nsk::OP_FWD1, f, s->cap);
     if (rc) return rc;
   }
   return NS_OK;
@@ -297,7 +325,7 @@ int phys_to_spec(ns_state *s, const double *host, void *dst) {
 
 void free_all(ns_state *s) {
   if (s->graph) cudaGraphExecDestroy(s->graph);
-  void *ptrs[] = {s->tw, s->ef, s->ef2, s->u, s->acc, s->F, s->zb, s->yb, s->staging, s->diag};
+  void *ptrs[] = {s->tw, s->ef, s->ef2, s->u, s->acc, s->F, s->zb, s->yb, s->staging, s->diag, s->umax, s->ctl};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   if (s->own) cudaStreamDestroy(s->own);
@@ -351,6 +379,17 @@ void fill_tables(const ns_state *s, std::vector<unsigned char> &tw, std::vector<
     e2[k] = (R)std::exp(-s->nu * (double)k * k * s->dt * 0.5);
   }
 }
+
+// Constant-dt factor tables refilled from the host (leaving CFL stepping).
+template <typename R>
+int upload_factor_tables(ns_state *s) {
+  std::vector<unsigned char> tw, ef, ef2;
+  fill_tables<R>(s, tw, ef, ef2);
+  NS_CK(s, cudaMemcpy(s->ef, ef.data(), ef.size(), cudaMemcpyHostToDevice));
+  NS_CK(s, cudaMemcpy(s->ef2, ef2.data(), ef2.size(), cudaMemcpyHostToDevice));
+  return NS_OK;
+}
+
 
 }  // namespace
 
@@ -575,6 +614,66 @@ int ns_step(ns_state *s, int nsteps) {
   }
   for (int i = 0; i < nsteps; ++i) NS_CK(s, cudaGraphLaunch(s->graph, s->stream));
   s->zvalid = true;
+  if (s->cfl <= 0) s->t += nsteps * s->dt;
+  return NS_OK;
+}
+
+int ns_set_scheme(ns_state *s, int order) {
+  if (!s) return NS_EINVAL;
+  if (order != 2 && order != 4) return fail(s, NS_EINVAL, "ns_set_scheme: order must be 2 or 4 (got %d)", order);
+  if (order == s->order) return NS_OK;
+  DevGuard dg(s->dev);
+  NS_CK(s, cudaStreamSynchronize(s->stream));
+  s->order = order;
+  if (s->graph) {
+    cudaGraphExecDestroy(s->graph);
+    s->graph = nullptr;
+  }
+  return NS_OK;
+}
+
+int ns_set_cfl(ns_state *s, double cfl) {
+  if (!s) return NS_EINVAL;
+  if (!(cfl >= 0) || !std::isfinite(cfl)) return fail(s, NS_EINVAL, "ns_set_cfl: cfl must be finite and >= 0");
+  DevGuard dg(s->dev);
+  NS_CK(s, cudaStreamSynchronize(s->stream));
+  int rc;
+  if (cfl > 0) {
+    if (!s->ctl) {
+      if ((rc = dmalloc(s, (void **)&s->umax, sizeof(unsigned long long) * 3 * nsk::kUmaxSlots))) return rc;
+      if ((rc = dmalloc(s, (void **)&s->ctl, sizeof(double) * 4))) return rc;
+    }
+    double t = s->t;
+    if (s->cfl > 0) NS_CK(s, cudaMemcpy(&t, s->ctl + 1, sizeof(double), cudaMemcpyDeviceToHost));
+    const double ctl[4] = {s->dt, t, s->dt, cfl};
+    NS_CK(s, cudaMemset(s->umax, 0, sizeof(unsigned long long) * 3 * nsk::kUmaxSlots));
+    NS_CK(s, cudaMemcpy(s->ctl, ctl, sizeof ctl, cudaMemcpyHostToDevice));
+  } else if (s->cfl > 0) {  // back to the constant dt: time from the device, tables for dt
+    NS_CK(s, cudaMemcpy(&s->t, s->ctl + 1, sizeof(double), cudaMemcpyDeviceToHost));
+    rc = s->prec == NS_FP32 ? upload_factor_tables<float>(s) : upload_factor_tables<double>(s);
+    if (rc) return rc;
+  }
+  s->cfl = cfl;
+  if (s->graph) {
+    cudaGraphExecDestroy(s->graph);
+    s->graph = nullptr;
+  }
+  return NS_OK;
+}
+
+int ns_get_time(ns_state *s, double *t, double *dt) {
+  if (!s || !t || !dt) return s ? fail(s, NS_EINVAL, "ns_get_time: null output") : NS_EINVAL;
+  DevGuard dg(s->dev);
+  if (s->cfl > 0) {
+    double ctl[2];
+    NS_CK(s, cudaMemcpyAsync(ctl, s->ctl, sizeof ctl, cudaMemcpyDeviceToHost, s->stream));
+    NS_CK(s, cudaStreamSynchronize(s->stream));
+    *dt = ctl[0];
+    *t = ctl[1];
+  } else {
+    *dt = s->dt;
+    *t = s->t;
+  }
   return NS_OK;
 }
 
@@ -758,16 +857,17 @@ long long ns_kernel_bytes(const ns_state *s, int id) {
       case 1: return cs * (6 * Z + 6 * Y);
       case 2: return cs * (6 * Y + 3 * Y);
       case 3: return cs * (3 * Y + 3 * Z);
-      default:  // 3 fields in, 6 out, plus the RK operands averaged over the four
-                // stages (state-sized reads 18 T, writes 12 T per step)
-        return cs * (9 * Z + (15 * T) / 2 + (f ? 3 * T : 0));
+      default:  // 3 fields in, 6 out, plus the RK operands averaged over the
+                // stages (RK4: state-sized reads 18 T, writes 12 T per step over
+                // four stages; RK2: reads 6 T, writes 3 T over two)
+        return cs * (9 * Z + (s->order == 2 ? (9 * T) / 2 : (15 * T) / 2) + (f ? 3 * T : 0));
     }
   }
   const long long T = c * h, Y = N * h;
   switch (id) {
     case 0: return cs * (T + 4 * Y);
     case 2: return cs * (4 * Y + Y);
-    case 4: return cs * (Y + 4 * Y + (5 * T) / 2 + (f ? T : 0));
+    case 4: return cs * (Y + 4 * Y + (s->order == 2 ? (3 * T) / 2 : (5 * T) / 2) + (f ? T : 0));
     default: return 0;
   }
 }

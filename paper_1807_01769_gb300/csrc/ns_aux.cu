@@ -195,6 +195,52 @@ int diagnostics(int prec, const Geo &g, const void *u, int nbins, double *scratc
   return (int)cudaGetLastError();
 }
 
+// CFL time step ("sim.time_stepping" chooses dt from the CFL criterion): one
+// block; warp 0 reduces the x pass maxima, the block refills the tables.
+template <typename R>
+__global__ void __launch_bounds__(256) k_cfl(Geo g, double nu, unsigned long long *__restrict__ umax,
+                                             double *__restrict__ ctl, R *__restrict__ ef, R *__restrict__ ef2) {
+  __shared__ double sdt;
+  if (threadIdx.x < 32) {
+    const int lane = threadIdx.x;
+    const double dx = 6.283185307179586 / g.N;
+    const double cfl = ctl[3];
+    double dt = ctl[2];
+    const int ncomp = g.dim;  // velocity components the x pass saw
+    for (int c = 0; c < ncomp; ++c) {
+      unsigned long long *slot = umax + c * kUmaxSlots;
+      double m = 0.0;
+      for (int j = lane; j < kUmaxSlots; j += 32) {
+        m = fmax(m, __longlong_as_double((long long)slot[j]));
+        slot[j] = 0ull;
+      }
+      for (int off = 16; off > 0; off >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, off));
+      if (m > 0.0) dt = fmin(dt, cfl * dx / m);
+    }
+    if (lane == 0) {
+      ctl[0] = dt;
+      ctl[1] += dt;
+      sdt = dt;
+    }
+  }
+  __syncthreads();
+  const double dt = sdt;
+  for (int k = threadIdx.x; k <= g.kc; k += blockDim.x) {
+    const double k2 = (double)k * (double)k;
+    ef[k] = (R)exp(-nu * k2 * dt);
+    ef2[k] = (R)exp(-nu * k2 * dt * 0.5);
+  }
+}
+
+int cfl_update(int prec, const Geo &g, double nu, unsigned long long *umax, double *ctl, void *ef, void *ef2,
+               cudaStream_t s) {
+  if (prec == 1)
+    k_cfl<float><<<1, 256, 0, s>>>(g, nu, umax, ctl, (float *)ef, (float *)ef2);
+  else
+    k_cfl<double><<<1, 256, 0, s>>>(g, nu, umax, ctl, (double *)ef, (double *)ef2);
+  return (int)cudaGetLastError();
+}
+
 // Energy and enstrophy budget terms, per block into scratch[b][0..3]:
 //   3D (velocity u, forcing F): P_E = sum w Re(u* . F),      D_E = nu sum w k^2 |u|^2,
 //                               P_Z = sum w k^2 Re(u* . F),  D_Z = nu sum w k^4 |u|^2;

@@ -29,9 +29,16 @@ enum Op {
   OP_FWD1 = 5,      // last forward axis, dealias, normalise, project, forcing, RK stage, (opt.) next inverse
   OP_XFWD_REAL = 6, // real lines (FP64 staging) -> half spectrum in x
   OP_XINV_REAL = 7, // half spectrum in x -> real lines (FP64 staging)
+  OP_CFL = 8,       // CFL time step from the x pass maxima; factor tables for it (ns_aux.cu)
 };
 
-enum Mode { MODE_RK1 = 1, MODE_RK2 = 2, MODE_RK3 = 3, MODE_RK4 = 4, MODE_RHS = 5, MODE_PROJ = 6 };
+// Slots per velocity component for the x pass maxima of |u_i| (blocks spread
+// their atomic maxima over the slots by block index).
+constexpr int kUmaxSlots = 64;
+
+// RK1..RK4: the four Lawson IF-RK4 stages; M1, M2: the two stages of the
+// Lawson IF-RK2 (midpoint) step; RHS / PROJ: write the term itself.
+enum Mode { MODE_RK1 = 1, MODE_RK2 = 2, MODE_RK3 = 3, MODE_RK4 = 4, MODE_RHS = 5, MODE_PROJ = 6, MODE_M1 = 7, MODE_M2 = 8 };
 
 struct Args {
   Geo g;
@@ -52,6 +59,8 @@ struct Args {
   int mode;    // OP_FWD1
   int inv;     // OP_FWD1: 1 = fuse the next stage's first inverse axis
   double dt;
+  const double *dtp;         // OP_FWD1: time step in device memory (nullable: use dt)
+  unsigned long long *umax;  // OP_XPASS: [dim][kUmaxSlots] maxima of |u_i| as double bits (nullable)
   int nsm;     // streaming multiprocessors of the device (persistent grids)
   int z0, nz;  // 3D OP_INV2 / OP_XPASS / OP_FWD2: planes z0 .. z0+nz-1 (nz = 0: all)
 };
@@ -72,6 +81,12 @@ int spec_out(int prec, double *dst, const void *src, long long rows, int h, int 
 long long diag_blocks(const Geo &g);
 long long diag_scratch_doubles(const Geo &g, int nbins);
 int diagnostics(int prec, const Geo &g, const void *u, int nbins, double *scratch, double *out, cudaStream_t s);
+// CFL step (one block): dt = min(dt_max, cfl * (2 pi / N) / max_i max|u_i|)
+// over components with a non-zero maximum; ctl = {dt, t, dt_max, cfl}: writes
+// dt, adds it to t, clears the maxima and refills the factor tables
+// ef[k] = exp(-nu k^2 dt), ef2[k] = exp(-nu k^2 dt / 2), k = 0 .. kc.
+int cfl_update(int prec, const Geo &g, double nu, unsigned long long *umax, double *ctl, void *ef, void *ef2,
+               cudaStream_t s);
 // Budget terms {P_E, D_E, P_Z, D_Z} (forcing power and dissipation of energy
 // and enstrophy) into out[0..3]; scratch holds diag_blocks(g) * 4 doubles.
 int budget(int prec, const Geo &g, const void *u, const void *F, double nu, double *scratch, double *out,

@@ -365,12 +365,29 @@ __global__ void __launch_bounds__((N / 8) * W) k3_inv2(Geo g, int nf, int z0, co
   }
 }
 
+// Largest |value| of the packed real pairs v[0..7] over the warp, merged into
+// *slot by an atomic maximum on the bit pattern (non-negative doubles order
+// like their bits read as unsigned integers).  The lanes of a block narrower
+// than a warp are lanes 0 .. blockDim.x - 1 (a power of two).
+template <typename C>
+__device__ __forceinline__ void umax_merge(const C (&v)[8], unsigned long long *slot) {
+  double m = 0.0;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) m = fmax(m, fmax(fabs((double)v[i].x), fabs((double)v[i].y)));
+  const int width = blockDim.x < 32 ? (int)blockDim.x : 32;
+  const unsigned mask = width == 32 ? 0xffffffffu : ((1u << width) - 1u);
+  for (int off = 16; off > 0; off >>= 1)
+    if (off < width) m = fmax(m, __shfl_xor_sync(mask, m, off));
+  if ((threadIdx.x & 31) == 0) atomicMax(slot, (unsigned long long)__double_as_longlong(m));
+}
+
 // xpass (3D): lines (z, y); fields u_x, u_y, u_z, w_x, w_y, w_z in, n = u x w out
 // (written over fields 0..2 of the same lines).
 template <typename R, int N, int L>
 __global__ void __launch_bounds__((N / 16) * L) k3_xpass(Geo g, long long line_base,
                                                           typename CplxOf<R>::T *__restrict__ yb,
-                                                          const typename CplxOf<R>::T *__restrict__ tw) {
+                                                          const typename CplxOf<R>::T *__restrict__ tw,
+                                                          unsigned long long *__restrict__ umax) {
   using C = typename CplxOf<R>::T;
   constexpr int H = N / 2, TX = H / 8, SL = smline_len(H);
   C *S = dyn_smem<C>();
@@ -386,6 +403,7 @@ __global__ void __launch_bounds__((N / 16) * L) k3_xpass(Geo g, long long line_b
 #pragma unroll
     for (int m = 0; m < 8; ++m) v[m] = c2r_pre<C, N>(S + l * SL, t + TX * m, tw);
     fft_line<H, +1>(v, t, tw + N + stage_tw_len(N), view);
+    if (umax != nullptr && f < 3) umax_merge(v, umax + f * kUmaxSlots + blockIdx.x % kUmaxSlots);
 #pragma unroll
     for (int m = 0; m < 8; ++m) {
       switch (f) {
@@ -424,7 +442,8 @@ __global__ void __launch_bounds__((N / 16) * L) k3_xpass(Geo g, long long line_b
 template <typename R, int N, int WPB>
 __global__ void __launch_bounds__(32 * WPB, 16 / WPB) k3_xpass_w(Geo g, long long line_base,
                                                                   typename CplxOf<R>::T *__restrict__ yb,
-                                                                  const typename CplxOf<R>::T *__restrict__ tw) {
+                                                                  const typename CplxOf<R>::T *__restrict__ tw,
+                                                                  unsigned long long *__restrict__ umax) {
   using C = typename CplxOf<R>::T;
   constexpr int H = N / 2, TX = H / 8, LPW = 32 / TX;
   constexpr int SL = xw_line_len<N, (LPW > 1)>();
@@ -449,6 +468,7 @@ __global__ void __launch_bounds__(32 * WPB, 16 / WPB) k3_xpass_w(Geo g, long lon
     if (f < 5) load_line<C, TX>(xn, src + (f + 1) * g.yb_f, t, g.h);  // prefetch the next field
     fft_line<H, +1, C, SmLine<C, N / 2>, SYNC_WARP>(v, t, tw + N + stage_tw_len(N), view);
     if (f < 3) {
+      if (umax != nullptr) umax_merge(v, umax + f * kUmaxSlots + blockIdx.x % kUmaxSlots);
 #pragma unroll
       for (int m = 0; m < 8; ++m) park[(f * 8 + m) * 32] = v[m];
     } else if (f == 3) {  // w_x:  n_y = u_z w_x,  n_z = -u_y w_x
@@ -543,7 +563,17 @@ struct StepBufs {
   C *yb;
   C *dst;
   R dt;
+  const double *dtp;  // time step in device memory (CFL stepping), nullable
 };
+
+// The step buffers with dt taken from device memory when it lives there.
+template <typename R>
+__device__ __forceinline__ StepBufs<R> step_dt(const StepBufs<R> &p) {
+  StepBufs<R> b = p;
+  if (p.dtp != nullptr) b.dt = (R)*p.dtp;
+  return b;
+}
+
 
 // Asynchronous global -> shared copies of BYTES (4, 8 or 16); a false
 // predicate zero-fills the destination without reading the source.
@@ -565,8 +595,52 @@ __device__ __forceinline__ R axis_factor(const R *__restrict__ t, int k) {
   return __ldg(t + (k < 0 ? -k : k));
 }
 
-// Lawson IF-RK4 stage update for one mode (see ns.h); e = E, e2 = E2 of the
-// mode; returns the next stage input.
+// Lawson IF-RK stage update for one mode with its operands already loaded
+// (uu = state, a = accumulator); writes acc / u / dst at gi and returns the
+// next stage input.  RK4 (stages RK1..RK4, k_s = N of the stage input):
+//   RK1: acc = E u + dt/6 E k1,     next = E2 (u + dt/2 k1)
+//   RK2: acc += dt/3 E2 k2,         next = E2 u + dt/2 k2
+//   RK3: acc += dt/3 E2 k3,         next = E u + dt E2 k3
+//   RK4: u = acc + dt/6 k4,         next = u
+// RK2 midpoint (M1, M2): next = E2 (u + dt/2 k1);  u = E u + dt E2 k2.
+template <int MODE, typename C, typename R>
+__device__ __forceinline__ C rk_stage(C nv, C uu, C a, R e, R e2, const StepBufs<R> &b, long long gi) {
+  if (MODE == MODE_RK1) {
+    const R c1 = b.dt * e / (R)6;
+    b.acc[gi] = C{e * uu.x + c1 * nv.x, e * uu.y + c1 * nv.y};
+    const R h = b.dt / (R)2;
+    return C{e2 * (uu.x + h * nv.x), e2 * (uu.y + h * nv.y)};
+  } else if (MODE == MODE_RK2) {
+    const R c2 = b.dt * e2 / (R)3;
+    b.acc[gi] = C{a.x + c2 * nv.x, a.y + c2 * nv.y};
+    const R h = b.dt / (R)2;
+    return C{e2 * uu.x + h * nv.x, e2 * uu.y + h * nv.y};
+  } else if (MODE == MODE_RK3) {
+    const R c2 = b.dt * e2 / (R)3;
+    b.acc[gi] = C{a.x + c2 * nv.x, a.y + c2 * nv.y};
+    const R c3 = b.dt * e2;
+    return C{e * uu.x + c3 * nv.x, e * uu.y + c3 * nv.y};
+  } else if (MODE == MODE_RK4) {
+    const R c4 = b.dt / (R)6;
+    const C un = C{a.x + c4 * nv.x, a.y + c4 * nv.y};
+    b.u[gi] = un;
+    return un;
+  } else if (MODE == MODE_M1) {  // RK2 midpoint, stage 1: next = E2 (u + dt/2 N)
+    const R h = b.dt / (R)2;
+    return C{e2 * (uu.x + h * nv.x), e2 * (uu.y + h * nv.y)};
+  } else if (MODE == MODE_M2) {  // RK2 stage 2: u <- E u + dt E2 N
+    const R c = b.dt * e2;
+    const C un = C{e * uu.x + c * nv.x, e * uu.y + c * nv.y};
+    b.u[gi] = un;
+    return un;
+  } else {
+    b.dst[gi] = nv;
+    return czero<C>();
+  }
+}
+
+// Lawson IF-RK stage update for one mode (see ns.h), loading its operands;
+// e = E, e2 = E2 of the mode; returns the next stage input.
 template <int MODE, typename C, typename R>
 __device__ __forceinline__ C rk_update(C nv, long long idx, R e, R e2, const StepBufs<R> &b) {
   if (MODE == MODE_RK1) {
@@ -593,38 +667,10 @@ __device__ __forceinline__ C rk_update(C nv, long long idx, R e, R e2, const Ste
     const C un = C{a.x + c4 * nv.x, a.y + c4 * nv.y};
     b.u[idx] = un;
     return un;
+  } else if (MODE == MODE_M1 || MODE == MODE_M2) {
+    return rk_stage<MODE>(nv, b.u[idx], czero<C>(), e, e2, b, idx);
   } else {  // MODE_RHS, MODE_PROJ: write the term itself
     b.dst[idx] = nv;
-    return czero<C>();
-  }
-}
-
-// Lawson IF-RK4 stage update for one mode with its operands already loaded
-// (uu = state, a = accumulator; see rk_update); writes acc / u / dst at gi.
-template <int MODE, typename C, typename R>
-__device__ __forceinline__ C rk_stage(C nv, C uu, C a, R e, R e2, const StepBufs<R> &b, long long gi) {
-  if (MODE == MODE_RK1) {
-    const R c1 = b.dt * e / (R)6;
-    b.acc[gi] = C{e * uu.x + c1 * nv.x, e * uu.y + c1 * nv.y};
-    const R h = b.dt / (R)2;
-    return C{e2 * (uu.x + h * nv.x), e2 * (uu.y + h * nv.y)};
-  } else if (MODE == MODE_RK2) {
-    const R c2 = b.dt * e2 / (R)3;
-    b.acc[gi] = C{a.x + c2 * nv.x, a.y + c2 * nv.y};
-    const R h = b.dt / (R)2;
-    return C{e2 * uu.x + h * nv.x, e2 * uu.y + h * nv.y};
-  } else if (MODE == MODE_RK3) {
-    const R c2 = b.dt * e2 / (R)3;
-    b.acc[gi] = C{a.x + c2 * nv.x, a.y + c2 * nv.y};
-    const R c3 = b.dt * e2;
-    return C{e * uu.x + c3 * nv.x, e * uu.y + c3 * nv.y};
-  } else if (MODE == MODE_RK4) {
-    const R c4 = b.dt / (R)6;
-    const C un = C{a.x + c4 * nv.x, a.y + c4 * nv.y};
-    b.u[gi] = un;
-    return un;
-  } else {
-    b.dst[gi] = nv;
     return czero<C>();
   }
 }
@@ -641,8 +687,9 @@ __host__ __device__ constexpr int rk_slot(int m) { return m < 3 ? m : m - 2; }
 // its retained modes are copied with cp.async into thread-private shared slots
 // [operand][comp][6][threads]; they land while the three forward transforms run.
 template <typename R, int N, int W, int MODE, bool INV>
-__global__ void __launch_bounds__((N / 8) * W) k3_fwd1(Geo g, StepBufs<R> b) {
+__global__ void __launch_bounds__((N / 8) * W) k3_fwd1(Geo g, StepBufs<R> bp) {
   using C = typename CplxOf<R>::T;
+  const StepBufs<R> b = step_dt(bp);
   constexpr int T = N / 8;
   constexpr int P = pitch_of(W, sizeof(C));
   constexpr int NT = T * W;
@@ -650,7 +697,7 @@ __global__ void __launch_bounds__((N / 8) * W) k3_fwd1(Geo g, StepBufs<R> b) {
   // shared memory, and a larger carve-out would shrink the L1 that serves the
   // table and twiddle loads
   constexpr size_t EXTRA_SMEM = kSmemMax;  // forces a single buffer below
-  constexpr bool NEED_U = MODE == MODE_RK1 || MODE == MODE_RK2 || MODE == MODE_RK3;
+  constexpr bool NEED_U = MODE == MODE_RK1 || MODE == MODE_RK2 || MODE == MODE_RK3 || MODE == MODE_M1 || MODE == MODE_M2;
   constexpr bool NEED_ACC = MODE == MODE_RK2 || MODE == MODE_RK3 || MODE == MODE_RK4;
   C *sm = dyn_smem<C>();
   C *rku = sm + N * P;  // [3][6][NT]
@@ -835,7 +882,8 @@ __global__ void __launch_bounds__((N / 8) * W) k2_inv1(Geo g, const typename Cpl
 // out (field 0).
 template <typename R, int N, int L>
 __global__ void __launch_bounds__((N / 16) * L) k2_xpass(Geo g, typename CplxOf<R>::T *__restrict__ yb,
-                                                          const typename CplxOf<R>::T *__restrict__ tw) {
+                                                          const typename CplxOf<R>::T *__restrict__ tw,
+                                                          unsigned long long *__restrict__ umax) {
   using C = typename CplxOf<R>::T;
   constexpr int H = N / 2, TX = H / 8, SL = smline_len(H);
   C *S = dyn_smem<C>();
@@ -851,6 +899,7 @@ __global__ void __launch_bounds__((N / 16) * L) k2_xpass(Geo g, typename CplxOf<
 #pragma unroll
     for (int m = 0; m < 8; ++m) v[m] = c2r_pre<C, N>(S + l * SL, t + TX * m, tw);
     fft_line<H, +1>(v, t, tw + N + stage_tw_len(N), view);
+    if (umax != nullptr && f < 2) umax_merge(v, umax + f * kUmaxSlots + blockIdx.x % kUmaxSlots);
 #pragma unroll
     for (int m = 0; m < 8; ++m) {
       if (f == 0) ux[m] = v[m];
@@ -869,7 +918,7 @@ __global__ void __launch_bounds__((N / 16) * L) k2_xpass(Geo g, typename CplxOf<
 template <typename R, int N, int WPB>
 __device__ __forceinline__ void xpass_2d_unit(const Geo &g, typename CplxOf<R>::T *__restrict__ yb,
                                               const typename CplxOf<R>::T *__restrict__ tw, int unit,
-                                              typename CplxOf<R>::T *Sw) {
+                                              typename CplxOf<R>::T *Sw, unsigned long long *umax = nullptr) {
   using C = typename CplxOf<R>::T;
   constexpr int H = N / 2, TX = H / 8, LPW = 32 / TX;
   constexpr int SL = xw_line_len<N, (LPW > 1)>();
@@ -889,6 +938,7 @@ __device__ __forceinline__ void xpass_2d_unit(const Geo &g, typename CplxOf<R>::
     for (int m = 0; m < 8; ++m) v[m] = c2r_pre_reg<C, N, TX>(xn, m, t, wt);
     if (f < 3) load_line<C, TX>(xn, src + (f + 1) * g.yb_f, t, g.h);
     fft_line<H, +1, C, SmLine<C, N / 2>, SYNC_WARP>(v, t, tw + N + stage_tw_len(N), view);
+    if (umax != nullptr && f < 2) umax_merge(v, umax + f * kUmaxSlots + unit % kUmaxSlots);
 #pragma unroll
     for (int m = 0; m < 8; ++m) {
       if (f == 0) ux[m] = v[m];
@@ -909,11 +959,12 @@ __device__ __forceinline__ void xpass_2d_unit(const Geo &g, typename CplxOf<R>::
 
 template <typename R, int N, int WPB>
 __global__ void __launch_bounds__(32 * WPB) k2_xpass_w(Geo g, typename CplxOf<R>::T *__restrict__ yb,
-                                                        const typename CplxOf<R>::T *__restrict__ tw) {
+                                                        const typename CplxOf<R>::T *__restrict__ tw,
+                                                        unsigned long long *__restrict__ umax) {
   using C = typename CplxOf<R>::T;
   constexpr int LPW = 32 / (N / 16);
   xpass_2d_unit<R, N, WPB>(g, yb, tw, blockIdx.x,
-                           dyn_smem<C>() + (threadIdx.x >> 5) * LPW * xw_line_len<N, (LPW > 1)>());
+                           dyn_smem<C>() + (threadIdx.x >> 5) * LPW * xw_line_len<N, (LPW > 1)>(), umax);
 }
 
 // fwd1 (2D): y forward of field 0, dealias, 1/N^2, forcing, RK stage; INV:
@@ -977,7 +1028,7 @@ __device__ __forceinline__ void fwd1_2d_unit(const Geo &g, const StepBufs<R> &b,
 template <typename R, int N, int W, int MODE, bool INV>
 __global__ void __launch_bounds__((N / 8) * W) k2_fwd1(Geo g, StepBufs<R> b) {
   using C = typename CplxOf<R>::T;
-  fwd1_2d_unit<R, N, W, MODE, INV>(g, b, blockIdx.x, dyn_smem<C>());
+  fwd1_2d_unit<R, N, W, MODE, INV>(g, step_dt(b), blockIdx.x, dyn_smem<C>());
 }
 
 // ================================================ real lines (set / get) ===
@@ -1043,6 +1094,7 @@ inline StepBufs<R> step_bufs(const Args &a) {
   b.yb = (C *)a.yb;
   b.dst = (C *)a.dst;
   b.dt = (R)a.dt;
+  b.dtp = a.dtp;
   return b;
 }
 
@@ -1086,6 +1138,8 @@ struct Launch3 {
         set_smem(k3_fwd1<R, N, WH, MODE_RK4, true>, SM_F1);
         set_smem(k3_fwd1<R, N, WH, MODE_RHS, false>, SM_F1);
         set_smem(k3_fwd1<R, N, WH, MODE_PROJ, false>, SM_F1);
+        set_smem(k3_fwd1<R, N, WH, MODE_M1, true>, SM_F1);
+        set_smem(k3_fwd1<R, N, WH, MODE_M2, true>, SM_F1);
         break;
       case OP_INV1: {
         const dim3 grid(g.c * (g.hs / WL));
@@ -1104,10 +1158,11 @@ struct Launch3 {
         if constexpr (XW) {
           const long long lines = (long long)(a.nz > 0 ? a.nz : N) * N;
           k3_xpass_w<R, N, XW_WPB><<<(unsigned)(lines / (XW_WPB * XW_LPW)), 32 * XW_WPB, SM_XW, s>>>(
-              g, (long long)a.z0 * N, (C *)a.yb, tw);
+              g, (long long)a.z0 * N, (C *)a.yb, tw, a.umax);
         } else {
           const long long lines = (long long)(a.nz > 0 ? a.nz : N) * N;
-          k3_xpass<R, N, L><<<(unsigned)(lines / L), (N / 16) * L, SM_X, s>>>(g, (long long)a.z0 * N, (C *)a.yb, tw);
+          k3_xpass<R, N, L><<<(unsigned)(lines / L), (N / 16) * L, SM_X, s>>>(g, (long long)a.z0 * N, (C *)a.yb, tw,
+                                                                               a.umax);
         }
         break;
       case OP_FWD2: {
@@ -1131,6 +1186,8 @@ struct Launch3 {
           case MODE_RK3: k3_fwd1<R, N, WH, MODE_RK3, true><<<grid, T * WH, SM_F1, s>>>(g, b); break;
           case MODE_RK4: k3_fwd1<R, N, WH, MODE_RK4, true><<<grid, T * WH, SM_F1, s>>>(g, b); break;
           case MODE_RHS: k3_fwd1<R, N, WH, MODE_RHS, false><<<grid, T * WH, SM_F1, s>>>(g, b); break;
+          case MODE_M1: k3_fwd1<R, N, WH, MODE_M1, true><<<grid, T * WH, SM_F1, s>>>(g, b); break;
+          case MODE_M2: k3_fwd1<R, N, WH, MODE_M2, true><<<grid, T * WH, SM_F1, s>>>(g, b); break;
           default: k3_fwd1<R, N, WH, MODE_PROJ, false><<<grid, T * WH, SM_F1, s>>>(g, b); break;
         }
         break;
@@ -1183,6 +1240,8 @@ struct Launch2 {
         set_smem(k2_fwd1<R, N, WH, MODE_RK4, true>, SM_H);
         set_smem(k2_fwd1<R, N, WH, MODE_RHS, false>, SM_H);
         set_smem(k2_fwd1<R, N, WH, MODE_PROJ, false>, SM_H);
+        set_smem(k2_fwd1<R, N, WH, MODE_M1, true>, SM_H);
+        set_smem(k2_fwd1<R, N, WH, MODE_M2, true>, SM_H);
         break;
       case OP_INV1:
         if (a.curl)
@@ -1192,9 +1251,9 @@ struct Launch2 {
         break;
       case OP_XPASS:
         if constexpr (XW2) {
-          k2_xpass_w<R, N, XW_WPB><<<N / (XW_WPB * XW_LPW), 32 * XW_WPB, SM_XW, s>>>(g, (C *)a.yb, tw);
+          k2_xpass_w<R, N, XW_WPB><<<N / (XW_WPB * XW_LPW), 32 * XW_WPB, SM_XW, s>>>(g, (C *)a.yb, tw, a.umax);
         } else {
-          k2_xpass<R, N, L><<<N / L, (N / 16) * L, SM_X, s>>>(g, (C *)a.yb, tw);
+          k2_xpass<R, N, L><<<N / L, (N / 16) * L, SM_X, s>>>(g, (C *)a.yb, tw, a.umax);
         }
         break;
       case OP_FWD1: {
@@ -1206,6 +1265,8 @@ struct Launch2 {
           case MODE_RK3: k2_fwd1<R, N, WH, MODE_RK3, true><<<grid, T * WH, SM_H, s>>>(g, b); break;
           case MODE_RK4: k2_fwd1<R, N, WH, MODE_RK4, true><<<grid, T * WH, SM_H, s>>>(g, b); break;
           case MODE_RHS: k2_fwd1<R, N, WH, MODE_RHS, false><<<grid, T * WH, SM_H, s>>>(g, b); break;
+          case MODE_M1: k2_fwd1<R, N, WH, MODE_M1, true><<<grid, T * WH, SM_H, s>>>(g, b); break;
+          case MODE_M2: k2_fwd1<R, N, WH, MODE_M2, true><<<grid, T * WH, SM_H, s>>>(g, b); break;
           default: k2_fwd1<R, N, WH, MODE_PROJ, false><<<grid, T * WH, SM_H, s>>>(g, b); break;
         }
         break;

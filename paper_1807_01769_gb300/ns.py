@@ -73,6 +73,9 @@ SIGNATURES = {
     "ns_ensemble_destroy": ([_P], None),
     "ns_ensemble_last_error": ([_P], ctypes.c_char_p),
     "ns_budget": ([_P, _P], _I),
+    "ns_set_scheme": ([_P, _I], _I),
+    "ns_set_cfl": ([_P, _D], _I),
+    "ns_get_time": ([_P, _PD, _PD], _I),
     "ns_state_to_phys_device": ([_P, _P], _I),
     "ns_set_forcing_phys_device": ([_P, _P], _I),
     "ns_cnn_init": ([ctypes.POINTER(_P), _I, _I, _I, ctypes.c_ulonglong], _I),
@@ -231,6 +234,20 @@ class Solver:
         e, o = _D(), _D()
         _check(lib.ns_diagnostics(self.state, ctypes.byref(e), ctypes.byref(o)), self.state)
         return e.value, o.value
+
+    def set_scheme(self, order: int) -> None:
+        """Lawson IF-RK of order 4 (default) or 2 (midpoint)."""
+        _check(lib.ns_set_scheme(self.state, int(order)), self.state)
+
+    def set_cfl(self, cfl: float) -> None:
+        """CFL-adaptive dt (capped by the initial dt); 0 = constant dt."""
+        _check(lib.ns_set_cfl(self.state, float(cfl)), self.state)
+
+    def time(self):
+        """(simulated time, dt of the last step)."""
+        t, dt = _D(), _D()
+        _check(lib.ns_get_time(self.state, ctypes.byref(t), ctypes.byref(dt)), self.state)
+        return t.value, dt.value
 
     def budget(self):
         """(P_E, D_E, P_Z, D_Z): forcing power and dissipation of energy and enstrophy."""
