@@ -42,11 +42,17 @@ template <typename R, int N>
 __host__ __device__ constexpr int w_heavy() {
   return cmin(wmax<R>(), cmax(1, (sizeof(R) == 4 ? 512 : 256) / (N / 8)));
 }
-// columns per tile of the y passes: 512-thread blocks so that two independent
-// blocks share an SM
+// columns per tile of the y passes.  Inverse: 512-thread blocks so that two
+// independent blocks share an SM.  Forward: up to 1024-thread blocks for
+// 128-byte row segments (measured at 512^3 FP32: fwd2 0.533 -> 0.451 ms per
+// launch with 16 columns, while inv2 slows from 0.832 to 0.904 ms).
 template <typename R, int N>
-__host__ __device__ constexpr int w_ypass() {
+__host__ __device__ constexpr int w_yinv() {
   return cmin(wmax<R>(), cmax(1, 512 / (N / 8)));
+}
+template <typename R, int N>
+__host__ __device__ constexpr int w_yfwd() {
+  return cmin(wmax<R>(), cmax(1, 1024 / (N / 8)));
 }
 // lines per block of the x kernels (N/16 threads per line)
 template <typename R, int N>
@@ -566,12 +572,15 @@ struct StepBufs {
   const double *dtp;  // time step in device memory (CFL stepping), nullable
 };
 
-// The step buffers with dt taken from device memory when it lives there.
+// The time step of a stage update: read from device memory at each use when
+// it lives there (CFL stepping; a volatile load, so that no register holds it
+// across the kernel), else the launch argument.
 template <typename R>
-__device__ __forceinline__ StepBufs<R> step_dt(const StepBufs<R> &p) {
-  StepBufs<R> b = p;
-  if (p.dtp != nullptr) b.dt = (R)*p.dtp;
-  return b;
+__device__ __forceinline__ R stage_dt(const StepBufs<R> &b) {
+  if (b.dtp == nullptr) return b.dt;
+  double v;
+  asm volatile("ld.global.nc.f64 %0, [%1];" : "=d"(v) : "l"(b.dtp));
+  return (R)v;
 }
 
 
@@ -605,31 +614,32 @@ __device__ __forceinline__ R axis_factor(const R *__restrict__ t, int k) {
 // RK2 midpoint (M1, M2): next = E2 (u + dt/2 k1);  u = E u + dt E2 k2.
 template <int MODE, typename C, typename R>
 __device__ __forceinline__ C rk_stage(C nv, C uu, C a, R e, R e2, const StepBufs<R> &b, long long gi) {
+  const R dt = (MODE == MODE_RHS || MODE == MODE_PROJ) ? (R)0 : stage_dt(b);
   if (MODE == MODE_RK1) {
-    const R c1 = b.dt * e / (R)6;
+    const R c1 = dt * e / (R)6;
     b.acc[gi] = C{e * uu.x + c1 * nv.x, e * uu.y + c1 * nv.y};
-    const R h = b.dt / (R)2;
+    const R h = dt / (R)2;
     return C{e2 * (uu.x + h * nv.x), e2 * (uu.y + h * nv.y)};
   } else if (MODE == MODE_RK2) {
-    const R c2 = b.dt * e2 / (R)3;
+    const R c2 = dt * e2 / (R)3;
     b.acc[gi] = C{a.x + c2 * nv.x, a.y + c2 * nv.y};
-    const R h = b.dt / (R)2;
+    const R h = dt / (R)2;
     return C{e2 * uu.x + h * nv.x, e2 * uu.y + h * nv.y};
   } else if (MODE == MODE_RK3) {
-    const R c2 = b.dt * e2 / (R)3;
+    const R c2 = dt * e2 / (R)3;
     b.acc[gi] = C{a.x + c2 * nv.x, a.y + c2 * nv.y};
-    const R c3 = b.dt * e2;
+    const R c3 = dt * e2;
     return C{e * uu.x + c3 * nv.x, e * uu.y + c3 * nv.y};
   } else if (MODE == MODE_RK4) {
-    const R c4 = b.dt / (R)6;
+    const R c4 = dt / (R)6;
     const C un = C{a.x + c4 * nv.x, a.y + c4 * nv.y};
     b.u[gi] = un;
     return un;
   } else if (MODE == MODE_M1) {  // RK2 midpoint, stage 1: next = E2 (u + dt/2 N)
-    const R h = b.dt / (R)2;
+    const R h = dt / (R)2;
     return C{e2 * (uu.x + h * nv.x), e2 * (uu.y + h * nv.y)};
   } else if (MODE == MODE_M2) {  // RK2 stage 2: u <- E u + dt E2 N
-    const R c = b.dt * e2;
+    const R c = dt * e2;
     const C un = C{e * uu.x + c * nv.x, e * uu.y + c * nv.y};
     b.u[gi] = un;
     return un;
@@ -643,27 +653,28 @@ __device__ __forceinline__ C rk_stage(C nv, C uu, C a, R e, R e2, const StepBufs
 // e = E, e2 = E2 of the mode; returns the next stage input.
 template <int MODE, typename C, typename R>
 __device__ __forceinline__ C rk_update(C nv, long long idx, R e, R e2, const StepBufs<R> &b) {
+  const R dt = (MODE == MODE_RHS || MODE == MODE_PROJ) ? (R)0 : stage_dt(b);
   if (MODE == MODE_RK1) {
     const C uu = b.u[idx];
-    const R c1 = b.dt * e / (R)6;
+    const R c1 = dt * e / (R)6;
     b.acc[idx] = C{e * uu.x + c1 * nv.x, e * uu.y + c1 * nv.y};
-    const R h = b.dt / (R)2;
+    const R h = dt / (R)2;
     return C{e2 * (uu.x + h * nv.x), e2 * (uu.y + h * nv.y)};
   } else if (MODE == MODE_RK2) {
     const C uu = b.u[idx], a = b.acc[idx];
-    const R c2 = b.dt * e2 / (R)3;
+    const R c2 = dt * e2 / (R)3;
     b.acc[idx] = C{a.x + c2 * nv.x, a.y + c2 * nv.y};
-    const R h = b.dt / (R)2;
+    const R h = dt / (R)2;
     return C{e2 * uu.x + h * nv.x, e2 * uu.y + h * nv.y};
   } else if (MODE == MODE_RK3) {
     const C uu = b.u[idx], a = b.acc[idx];
-    const R c2 = b.dt * e2 / (R)3;
+    const R c2 = dt * e2 / (R)3;
     b.acc[idx] = C{a.x + c2 * nv.x, a.y + c2 * nv.y};
-    const R c3 = b.dt * e2;
+    const R c3 = dt * e2;
     return C{e * uu.x + c3 * nv.x, e * uu.y + c3 * nv.y};
   } else if (MODE == MODE_RK4) {
     const C a = b.acc[idx];
-    const R c4 = b.dt / (R)6;
+    const R c4 = dt / (R)6;
     const C un = C{a.x + c4 * nv.x, a.y + c4 * nv.y};
     b.u[idx] = un;
     return un;
@@ -687,9 +698,8 @@ __host__ __device__ constexpr int rk_slot(int m) { return m < 3 ? m : m - 2; }
 // its retained modes are copied with cp.async into thread-private shared slots
 // [operand][comp][6][threads]; they land while the three forward transforms run.
 template <typename R, int N, int W, int MODE, bool INV>
-__global__ void __launch_bounds__((N / 8) * W) k3_fwd1(Geo g, StepBufs<R> bp) {
+__global__ void __launch_bounds__((N / 8) * W) k3_fwd1(Geo g, StepBufs<R> b) {
   using C = typename CplxOf<R>::T;
-  const StepBufs<R> b = step_dt(bp);
   constexpr int T = N / 8;
   constexpr int P = pitch_of(W, sizeof(C));
   constexpr int NT = T * W;
@@ -1028,7 +1038,7 @@ __device__ __forceinline__ void fwd1_2d_unit(const Geo &g, const StepBufs<R> &b,
 template <typename R, int N, int W, int MODE, bool INV>
 __global__ void __launch_bounds__((N / 8) * W) k2_fwd1(Geo g, StepBufs<R> b) {
   using C = typename CplxOf<R>::T;
-  fwd1_2d_unit<R, N, W, MODE, INV>(g, step_dt(b), blockIdx.x, dyn_smem<C>());
+  fwd1_2d_unit<R, N, W, MODE, INV>(g, b, blockIdx.x, dyn_smem<C>());
 }
 
 // ================================================ real lines (set / get) ===
@@ -1105,9 +1115,9 @@ struct Launch3 {
   static constexpr int WL = w_light<R, N>();
   static constexpr int WH = w_heavy<R, N>();
   static constexpr int L = x_lines<R, N>();
-  static constexpr int WY = w_ypass<R, N>();
+  static constexpr int WYI = w_yinv<R, N>(), WYF = w_yfwd<R, N>();
   static constexpr size_t SM_L = col_smem(N, WL, sizeof(C), 0);
-  static constexpr size_t SM_Y = col_smem(N, WY, sizeof(C), 0);
+  static constexpr size_t SM_YI = col_smem(N, WYI, sizeof(C), 0), SM_YF = col_smem(N, WYF, sizeof(C), 0);
   // persistent fwd1: exchange tile(s) + RK operand slots (2 operands x 3 comps x 6 per thread)
   static constexpr size_t SM_F1 = col_tile_bytes(N, WH, sizeof(C)) + (size_t)36 * T * WH * sizeof(C);
   static_assert(SM_F1 <= kSmemMax, "fwd1 shared memory");
@@ -1127,8 +1137,8 @@ struct Launch3 {
         if constexpr (XW) set_smem(k3_xpass_w<R, N, XW_WPB>, SM_XW);
         set_smem(k3_inv1<R, N, WL, true>, SM_L);
         set_smem(k3_inv1<R, N, WL, false>, SM_L);
-        set_smem(k3_inv2<R, N, WY>, SM_Y);
-        set_smem(k3_fwd2<R, N, WY>, SM_Y);
+        set_smem(k3_inv2<R, N, WYI>, SM_YI);
+        set_smem(k3_fwd2<R, N, WYF>, SM_YF);
         set_smem(k3_xpass<R, N, L>, SM_X);
         set_smem(k_xfwd_real<R, N, L>, SM_X);
         set_smem(k_xinv_real<R, N, L>, SM_X);
@@ -1151,7 +1161,7 @@ struct Launch3 {
       }
       case OP_INV2: {
         const int nz = a.nz > 0 ? a.nz : N;
-        k3_inv2<R, N, WY><<<dim3(g.hs / WY, nz), T * WY, SM_Y, s>>>(g, a.nf, a.z0, (const C *)a.zb, (C *)a.yb, tw);
+        k3_inv2<R, N, WYI><<<dim3(g.hs / WYI, nz), T * WYI, SM_YI, s>>>(g, a.nf, a.z0, (const C *)a.zb, (C *)a.yb, tw);
         break;
       }
       case OP_XPASS:
@@ -1167,7 +1177,7 @@ struct Launch3 {
         break;
       case OP_FWD2: {
         const int nz = a.nz > 0 ? a.nz : N;
-        k3_fwd2<R, N, WY><<<dim3(g.hs / WY, nz), T * WY, SM_Y, s>>>(g, a.nf, a.z0, (const C *)a.yb, (C *)a.zb, tw);
+        k3_fwd2<R, N, WYF><<<dim3(g.hs / WYF, nz), T * WYF, SM_YF, s>>>(g, a.nf, a.z0, (const C *)a.yb, (C *)a.zb, tw);
         break;
       }
       case OP_FWD1: {
