@@ -593,6 +593,12 @@ __device__ __forceinline__ void cp_async(void *dst_smem, const void *src, bool p
                "r"(pred ? BYTES : 0)
                : "memory");
 }
+// 16 bytes, cached in L2 only (streamed operands that would evict L1 data).
+__device__ __forceinline__ void cp_async_cg16(void *dst_smem, const void *src, bool pred) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(smem_addr(dst_smem)), "l"(src),
+               "r"(pred ? 16 : 0)
+               : "memory");
+}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
@@ -738,17 +744,24 @@ __global__ void __launch_bounds__((N / 8) * W) k3_fwd1(Geo g, StepBufs<R> b) {
       s2[m] = valid ? ld_stream(b.zb + 2 * g.zb_f + off) : czero<C>();
     }
     if (NEED_U || NEED_ACC) {
+      // 16-byte L2-only copies: an 8-byte element type copies the slots of a
+      // column pair (kx even, kx + 1: adjacent threads and adjacent slots)
+      // from the even thread; kx + 1 < hs always, its value unused if >= h
+      constexpr bool PAIR = sizeof(C) == 8;
+      static_assert(!PAIR || W % 2 == 0, "column pairs");
+      if (!PAIR || (w & 1) == 0) {
 #pragma unroll
-      for (int m = 0; m < 8; ++m) {
-        if (m == 3 || m == 4) continue;
-        const int n = t + T * m;
-        const bool ok = valid && retained(n, N, g.kc);
-        const long long idx = ok ? (long long)compact_of(n, N, g.kc, g.c) * plane + col : 0;
+        for (int m = 0; m < 8; ++m) {
+          if (m == 3 || m == 4) continue;
+          const int n = t + T * m;
+          const bool ok = valid && retained(n, N, g.kc);
+          const long long idx = ok ? (long long)compact_of(n, N, g.kc, g.c) * plane + col : 0;
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
-          const int slot = (c * 6 + rk_slot(m)) * NT + threadIdx.x;
-          if (NEED_U) cp_async<sizeof(C)>(rku + slot, b.u + c * st + idx, ok);
-          if (NEED_ACC) cp_async<sizeof(C)>(rka + slot, b.acc + c * st + idx, ok);
+          for (int c = 0; c < 3; ++c) {
+            const int slot = (c * 6 + rk_slot(m)) * NT + threadIdx.x;
+            if (NEED_U) cp_async_cg16(rku + slot, b.u + c * st + idx, ok);
+            if (NEED_ACC) cp_async_cg16(rka + slot, b.acc + c * st + idx, ok);
+          }
         }
       }
       cp_async_commit();
@@ -756,7 +769,10 @@ __global__ void __launch_bounds__((N / 8) * W) k3_fwd1(Geo g, StepBufs<R> b) {
     fft_line<N, -1>(s0, t, b.tw + N, view);
     fft_line<N, -1>(s1, t, b.tw + N, view);
     fft_line<N, -1>(s2, t, b.tw + N, view);
-    if (NEED_U || NEED_ACC) cp_async_wait_all();
+    if (NEED_U || NEED_ACC) {
+      cp_async_wait_all();
+      __syncwarp();  // the partner's copies into this thread's slots are visible
+    }
 #pragma unroll
     for (int m = 0; m < 8; ++m) {
       const int n = t + T * m;
