@@ -104,7 +104,11 @@ int ns_set_state_spectral(ns_state *s, const double *spec_host);
 int ns_get_state_spectral(ns_state *s, double *spec_host);
 
 /* Advance nsteps >= 0 Lawson IF-RK4 steps.  Asynchronous: returns after the
- * work is enqueued on the state's stream (a captured CUDA graph per step). */
+ * work is enqueued on the state's stream (a captured CUDA graph per step).
+ * While the caller captures that stream into a graph of its own, the step's
+ * kernels are enqueued one by one instead, so the caller's graph holds them;
+ * the constant-dt time counter of ns_get_time then counts the capture, not
+ * its replays. */
 int ns_step(ns_state *s, int nsteps);
 
 /* Time-stepping scheme ("sim.time_stepping": Runge-Kutta of order 2 or 4 with

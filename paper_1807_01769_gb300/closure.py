@@ -196,9 +196,13 @@ def a_priori(tr: Trained, X: np.ndarray, T: np.ndarray) -> dict:
 
 class ClosureSolver:
     """Coarse 2D solve with the network's prediction added to the forcing
-    before every step; all work enqueued on one CUDA stream."""
+    before every step; all work enqueued on one CUDA stream.  With
+    ``use_graph`` one corrected step (state to physical space, network,
+    forcing update, RK4 step) is captured once into a CUDA graph and
+    replayed."""
 
-    def __init__(self, cfg: KolmogorovConfig, tr: Trained, check_every: int = 50, blowup: float = 100.0):
+    def __init__(self, cfg: KolmogorovConfig, tr: Trained, check_every: int = 50, blowup: float = 100.0,
+                 use_graph: bool = True):
         import torch
 
         self.cfg, self.tr = cfg, tr
@@ -216,6 +220,8 @@ class ClosureSolver:
         self.fell_back = False
         self._good = None
         self._omega0 = None
+        self.use_graph = use_graph
+        self._graph = None
 
     def close(self):
         self.solver.close()
@@ -238,6 +244,44 @@ class ClosureSolver:
         ns.f32_axpy_f64(self.y.data_ptr(), self.F.data_ptr(), self.f.data_ptr(), self.n2, self.tr.t_scale, st)
         ns._check(ns.lib.ns_set_forcing_phys_device(s, ns.ctypes.c_void_p(self.f.data_ptr())), s)
 
+    def _corrected_step(self):
+        self._correct()
+        self.solver.step(1)
+
+    def _capture(self):
+        """Record one corrected step into a CUDA graph (after an eager step
+        has done every lazy set-up: kernel attributes, the step graph)."""
+        import torch
+
+        self._corrected_step()
+        self.stream.synchronize()
+        g = torch.cuda.CUDAGraph()
+        cap = torch.cuda.Stream()
+        self.solver.set_stream(cap.cuda_stream)
+        saved = self.stream
+        self.stream = cap
+        try:
+            with torch.cuda.graph(g, stream=cap, capture_error_mode="thread_local"):
+                self._corrected_step()
+        finally:
+            self.stream = saved
+            self.solver.set_stream(saved.cuda_stream)
+        self._graph = g
+
+    def _run_corrected(self, n: int):
+        import torch
+
+        if not self.use_graph:
+            for _ in range(n):
+                self._corrected_step()
+            return
+        if self._graph is None:
+            self._capture()
+            n -= 1  # the eager warm-up step of the capture advanced the state
+        with torch.cuda.stream(self.stream):
+            for _ in range(n):
+                self._graph.replay()
+
     def _plain_forcing(self):
         s = self.solver.state
         ns._check(ns.lib.ns_set_forcing_phys_device(s, ns.ctypes.c_void_p(self.F.data_ptr())), s)
@@ -249,9 +293,7 @@ class ClosureSolver:
             if self.fell_back:
                 self.solver.step(chunk)
             else:
-                for _ in range(chunk):
-                    self._correct()
-                    self.solver.step(1)
+                self._run_corrected(chunk)
             done += chunk
             if not self.fell_back:
                 try:
@@ -328,21 +370,24 @@ def step_times(cfg: KolmogorovConfig, tr: Trained, nsteps: int = 200) -> dict:
     wf = inputs.random_vorticity_2d(cfg.n_fine, 1, k0=cfg.ic_k0, energy=cfg.ic_energy)
     with coarse_solver(cfg) as plain, fine_solver(cfg) as fine:
         closed = ClosureSolver(cfg, tr, check_every=10 ** 9)
+        eager = ClosureSolver(cfg, tr, check_every=10 ** 9, use_graph=False)
         try:
-            for name, s, init in (("plain_coarse", plain, w), ("closure_coarse", closed, w), ("fine", fine, wf)):
+            for name, s, init in (("plain_coarse", plain, w), ("closure_coarse", closed, w),
+                                  ("closure_coarse_eager", eager, w), ("fine", fine, wf)):
                 s.set_state_spectral(init)
                 s.step(10)
                 torch.cuda.synchronize()
                 t0 = time.perf_counter()
                 s.step(nsteps)
-                if name == "closure_coarse":
-                    closed.stream.synchronize()
+                if isinstance(s, ClosureSolver):
+                    s.stream.synchronize()
                 else:
                     s.sync()
                 torch.cuda.synchronize()
                 out[name + "_ms"] = 1e3 * (time.perf_counter() - t0) / nsteps
         finally:
             closed.close()
+            eager.close()
     return out
 
 

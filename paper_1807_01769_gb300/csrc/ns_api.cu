@@ -607,6 +607,22 @@ int ns_step(ns_state *s, int nsteps) {
   if (nsteps == 0) return NS_OK;
   DevGuard dg(s->dev);
   int rc;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  NS_CK(s, cudaStreamIsCapturing(s->stream, &cap));
+  if (cap == cudaStreamCaptureStatusActive) {
+    // the caller is recording its own graph: enqueue the step's kernels
+    // themselves (a graph launch cannot be captured)
+    if (!s->zvalid) {
+      Launch l = inv1_launch(s, s->u, 1);
+      if ((rc = dispatch(s, l.op, l.a, s->stream))) return rc;
+    }
+    const std::vector<Launch> v = step_launches(s);
+    for (int i = 0; i < nsteps; ++i)
+      if ((rc = run_launches(s, v, s->stream))) return rc;
+    s->zvalid = true;
+    if (s->cfl <= 0) s->t += nsteps * s->dt;
+    return NS_OK;
+  }
   if ((rc = build_graph(s))) return rc;
   if (!s->zvalid) {
     Launch l = inv1_launch(s, s->u, 1);
