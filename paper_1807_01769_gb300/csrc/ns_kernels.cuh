@@ -716,8 +716,9 @@ __global__ void __launch_bounds__((N / 8) * W) k3_fwd1(Geo g, StepBufs<R> b) {
   constexpr bool NEED_U = MODE == MODE_RK1 || MODE == MODE_RK2 || MODE == MODE_RK3 || MODE == MODE_M1 || MODE == MODE_M2;
   constexpr bool NEED_ACC = MODE == MODE_RK2 || MODE == MODE_RK3 || MODE == MODE_RK4;
   C *sm = dyn_smem<C>();
-  C *rku = sm + N * P;  // [3][6][NT]
-  C *rka = rku + 18 * NT;     // [3][6][NT]
+  // operand slots [3][6][NT] each; a stage with one operand allocates one set
+  C *rku = sm + N * P;
+  C *rka = (NEED_U && NEED_ACC) ? rku + 18 * NT : rku;
   const int w = threadIdx.x % W, t = threadIdx.x / W;
   const int nkt = g.hs / W;
   const int ntiles = g.c * nkt;
@@ -1134,8 +1135,11 @@ struct Launch3 {
   static constexpr int WYI = w_yinv<R, N>(), WYF = w_yfwd<R, N>();
   static constexpr size_t SM_L = col_smem(N, WL, sizeof(C), 0);
   static constexpr size_t SM_YI = col_smem(N, WYI, sizeof(C), 0), SM_YF = col_smem(N, WYF, sizeof(C), 0);
-  // persistent fwd1: exchange tile(s) + RK operand slots (2 operands x 3 comps x 6 per thread)
+  // persistent fwd1: exchange tile + RK operand slots (3 comps x 6 per thread
+  // for each operand: two for RK2/RK3, one for the other stages; the smaller
+  // allocation leaves more of the SM's L1, which fwd1 is sensitive to)
   static constexpr size_t SM_F1 = col_tile_bytes(N, WH, sizeof(C)) + (size_t)36 * T * WH * sizeof(C);
+  static constexpr size_t SM_F1S = col_tile_bytes(N, WH, sizeof(C)) + (size_t)18 * T * WH * sizeof(C);
   static_assert(SM_F1 <= kSmemMax, "fwd1 shared memory");
   static constexpr size_t SM_X = (size_t)L * smline_len(N / 2) * sizeof(C);
   // warp-per-line x pass when a line fits in one warp
@@ -1158,14 +1162,14 @@ struct Launch3 {
         set_smem(k3_xpass<R, N, L>, SM_X);
         set_smem(k_xfwd_real<R, N, L>, SM_X);
         set_smem(k_xinv_real<R, N, L>, SM_X);
-        set_smem(k3_fwd1<R, N, WH, MODE_RK1, true>, SM_F1);
+        set_smem(k3_fwd1<R, N, WH, MODE_RK1, true>, SM_F1S);
         set_smem(k3_fwd1<R, N, WH, MODE_RK2, true>, SM_F1);
         set_smem(k3_fwd1<R, N, WH, MODE_RK3, true>, SM_F1);
-        set_smem(k3_fwd1<R, N, WH, MODE_RK4, true>, SM_F1);
-        set_smem(k3_fwd1<R, N, WH, MODE_RHS, false>, SM_F1);
-        set_smem(k3_fwd1<R, N, WH, MODE_PROJ, false>, SM_F1);
-        set_smem(k3_fwd1<R, N, WH, MODE_M1, true>, SM_F1);
-        set_smem(k3_fwd1<R, N, WH, MODE_M2, true>, SM_F1);
+        set_smem(k3_fwd1<R, N, WH, MODE_RK4, true>, SM_F1S);
+        set_smem(k3_fwd1<R, N, WH, MODE_RHS, false>, SM_F1S);
+        set_smem(k3_fwd1<R, N, WH, MODE_PROJ, false>, SM_F1S);
+        set_smem(k3_fwd1<R, N, WH, MODE_M1, true>, SM_F1S);
+        set_smem(k3_fwd1<R, N, WH, MODE_M2, true>, SM_F1S);
         break;
       case OP_INV1: {
         const dim3 grid(g.c * (g.hs / WL));
@@ -1207,14 +1211,14 @@ struct Launch3 {
         const int grid = cmin(tiles, per_sm * (a.nsm > 0 ? a.nsm : 1));
         const StepBufs<R> b = step_bufs<R>(a);
         switch (a.mode) {
-          case MODE_RK1: k3_fwd1<R, N, WH, MODE_RK1, true><<<grid, T * WH, SM_F1, s>>>(g, b); break;
+          case MODE_RK1: k3_fwd1<R, N, WH, MODE_RK1, true><<<grid, T * WH, SM_F1S, s>>>(g, b); break;
           case MODE_RK2: k3_fwd1<R, N, WH, MODE_RK2, true><<<grid, T * WH, SM_F1, s>>>(g, b); break;
           case MODE_RK3: k3_fwd1<R, N, WH, MODE_RK3, true><<<grid, T * WH, SM_F1, s>>>(g, b); break;
-          case MODE_RK4: k3_fwd1<R, N, WH, MODE_RK4, true><<<grid, T * WH, SM_F1, s>>>(g, b); break;
-          case MODE_RHS: k3_fwd1<R, N, WH, MODE_RHS, false><<<grid, T * WH, SM_F1, s>>>(g, b); break;
-          case MODE_M1: k3_fwd1<R, N, WH, MODE_M1, true><<<grid, T * WH, SM_F1, s>>>(g, b); break;
-          case MODE_M2: k3_fwd1<R, N, WH, MODE_M2, true><<<grid, T * WH, SM_F1, s>>>(g, b); break;
-          default: k3_fwd1<R, N, WH, MODE_PROJ, false><<<grid, T * WH, SM_F1, s>>>(g, b); break;
+          case MODE_RK4: k3_fwd1<R, N, WH, MODE_RK4, true><<<grid, T * WH, SM_F1S, s>>>(g, b); break;
+          case MODE_RHS: k3_fwd1<R, N, WH, MODE_RHS, false><<<grid, T * WH, SM_F1S, s>>>(g, b); break;
+          case MODE_M1: k3_fwd1<R, N, WH, MODE_M1, true><<<grid, T * WH, SM_F1S, s>>>(g, b); break;
+          case MODE_M2: k3_fwd1<R, N, WH, MODE_M2, true><<<grid, T * WH, SM_F1S, s>>>(g, b); break;
+          default: k3_fwd1<R, N, WH, MODE_PROJ, false><<<grid, T * WH, SM_F1S, s>>>(g, b); break;
         }
         break;
       }
