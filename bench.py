@@ -124,7 +124,7 @@ def traffic_from_profiles(kernel: str):
     return None
 
 
-def cpu_baseline(n=128, steps=2):
+def cpu_baseline(n=256, steps=2):
     """The FP64 oracle as it stands, on this host's cores: a bounded sample
     (`steps` RK4 steps of the same recipe on an n^3 grid)."""
     import oracle
