@@ -43,21 +43,26 @@ __host__ __device__ constexpr int w_heavy() {
   return cmin(wmax<R>(), cmax(1, (sizeof(R) == 4 ? 512 : 256) / (N / 8)));
 }
 // columns per tile of the y passes.  Inverse: 512-thread blocks so that two
-// independent blocks share an SM.  Forward: up to 1024-thread blocks for
-// 128-byte row segments (measured at 512^3 FP32: fwd2 0.533 -> 0.451 ms per
-// launch with 16 columns, while inv2 slows from 0.832 to 0.904 ms).
+// independent blocks share an SM, except that FP32 1024-point columns take
+// 1024 threads for 8 columns (64-byte rows; 1024^3: 9.83 -> 9.59 ms).  Forward:
+// up to 1024-thread blocks for 128-byte row segments (measured at 512^3 FP32:
+// fwd2 0.533 -> 0.451 ms per launch with 16 columns, while inv2 slows from
+// 0.832 to 0.904 ms).
 template <typename R, int N>
 __host__ __device__ constexpr int w_yinv() {
-  return cmin(wmax<R>(), cmax(1, 512 / (N / 8)));
+  return cmin(wmax<R>(), cmax(1, (sizeof(R) == 4 && N >= 1024 ? 1024 : 512) / (N / 8)));
 }
 template <typename R, int N>
 __host__ __device__ constexpr int w_yfwd() {
   return cmin(wmax<R>(), cmax(1, 1024 / (N / 8)));
 }
-// lines per block of the x kernels (N/16 threads per line)
+// lines per block of the x kernels (N/16 threads per line); lines longer
+// than a warp in FP32: one line per block, whose barriers then span only that
+// line's warps (measured at 1024^3: x pass 18.6 ms with 4 lines per block,
+// 16.7 ms with 2, 16.4 ms with 1)
 template <typename R, int N>
 __host__ __device__ constexpr int x_lines() {
-  return cmin(N, cmax(1, (sizeof(R) == 4 ? 256 : 128) / (N / 16)));
+  return cmin(N, cmax(1, (sizeof(R) == 4 ? (N / 16 > 32 ? 64 : 256) : 128) / (N / 16)));
 }
 __host__ __device__ constexpr int pitch_of(int W, int csize) { return (W * csize < 128) ? W + 1 : W; }
 
@@ -114,7 +119,7 @@ __device__ __forceinline__ void stage_lines(C *S, const C *__restrict__ src, lon
   constexpr int SL = smline_len(H);
   for (int idx = threadIdx.x; idx < L * H; idx += blockDim.x) {
     const int ll = idx / H, k = idx % H;
-    S[ll * SL + k + (k >> 3)] = k < h ? src[(line0 + ll) * hs + k] : czero<C>();
+    S[ll * SL + k + (k >> 3)] = k < h ? ld_stream(src + (line0 + ll) * hs + k) : czero<C>();
   }
 }
 
@@ -389,45 +394,78 @@ __device__ __forceinline__ void umax_merge(const C (&v)[8], unsigned long long *
 
 // xpass (3D): lines (z, y); fields u_x, u_y, u_z, w_x, w_y, w_z in, n = u x w out
 // (written over fields 0..2 of the same lines).
+// Lines longer than a warp (N/16 > 32 lanes): the Hermitian partners come
+// through shared memory, so the exchanges synchronise the block.  As in the
+// warp-per-line kernel the three velocity fields are parked in thread-private
+// shared slots [field][m][thread], which keeps the kernel at 128 registers
+// (FP32) and two 256-thread blocks per SM.
+template <typename R>
+__host__ __device__ constexpr int xpass_blocks_min(int threads) {
+  return sizeof(R) == 4 ? cmax(1, 512 / threads) : 1;
+}
 template <typename R, int N, int L>
-__global__ void __launch_bounds__((N / 16) * L) k3_xpass(Geo g, long long line_base,
-                                                          typename CplxOf<R>::T *__restrict__ yb,
-                                                          const typename CplxOf<R>::T *__restrict__ tw,
-                                                          unsigned long long *__restrict__ umax) {
+__global__ void __launch_bounds__((N / 16) * L, xpass_blocks_min<R>((N / 16) * L))
+    k3_xpass(Geo g, long long line_base, typename CplxOf<R>::T *__restrict__ yb,
+             const typename CplxOf<R>::T *__restrict__ tw, unsigned long long *__restrict__ umax) {
   using C = typename CplxOf<R>::T;
-  constexpr int H = N / 2, TX = H / 8, SL = smline_len(H);
+  constexpr int H = N / 2, TX = H / 8, SL = smline_len(H), NTH = TX * L;
   C *S = dyn_smem<C>();
+  C *park = S + L * SL + threadIdx.x;  // park[(f * 8 + m) * NTH]
   const int t = threadIdx.x % TX, l = threadIdx.x / TX;
   const long long line0 = line_base + (long long)blockIdx.x * L;
   const SmLine<C> view{S + l * SL};
-  C ux[8], uy[8], uz[8], nx[8], ny[8], nz[8];
+  C nx[8], ny[8], nz[8];
+  // the block's L lines of a field are L * H = 8 NTH entries: thread entry j
+  // is idx = threadIdx.x + NTH j (line idx / H, index idx % H); the next
+  // field's entries are loaded into xn while the current field is transformed
+  static_assert(L * H == 8 * NTH, "staging map");
+  C xn[8];
+  auto load_field = [&](const C *src) {
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int idx = threadIdx.x + NTH * j, ll = idx / H, k = idx % H;
+      xn[j] = k < g.h ? ld_stream(src + (line0 + ll) * g.hs + k) : czero<C>();
+    }
+  };
+  load_field(yb);
+#pragma unroll 1
   for (int f = 0; f < 6; ++f) {
     __syncthreads();
-    stage_lines<C, H, L>(S, yb + f * g.yb_f, line0, g.h, g.hs);
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int idx = threadIdx.x + NTH * j, ll = idx / H, k = idx % H;
+      S[ll * SL + k + (k >> 3)] = xn[j];
+    }
+    if (f < 5) load_field(yb + (f + 1) * g.yb_f);
     __syncthreads();
     C v[8];
 #pragma unroll
     for (int m = 0; m < 8; ++m) v[m] = c2r_pre<C, N>(S + l * SL, t + TX * m, tw);
     fft_line<H, +1>(v, t, tw + N + stage_tw_len(N), view);
     if (umax != nullptr && f < 3) umax_merge(v, umax + f * kUmaxSlots + blockIdx.x % kUmaxSlots);
+    if (f < 3) {
 #pragma unroll
-    for (int m = 0; m < 8; ++m) {
-      switch (f) {
-        case 0: ux[m] = v[m]; break;
-        case 1: uy[m] = v[m]; break;
-        case 2: uz[m] = v[m]; break;
-        case 3:  // w_x:  n_y = u_z w_x,  n_z = -u_y w_x
-          ny[m] = pmul(uz[m], v[m]);
-          nz[m] = pmul(C{-uy[m].x, -uy[m].y}, v[m]);
-          break;
-        case 4:  // w_y:  n_x = -u_z w_y, n_z += u_x w_y
-          nx[m] = pmul(C{-uz[m].x, -uz[m].y}, v[m]);
-          nz[m] = pfma(ux[m], v[m], nz[m]);
-          break;
-        default:  // w_z: n_x += u_y w_z, n_y -= u_x w_z
-          nx[m] = pfma(uy[m], v[m], nx[m]);
-          ny[m] = pfms(ux[m], v[m], ny[m]);
-          break;
+      for (int m = 0; m < 8; ++m) park[(f * 8 + m) * NTH] = v[m];
+    } else if (f == 3) {  // w_x:  n_y = u_z w_x,  n_z = -u_y w_x
+#pragma unroll
+      for (int m = 0; m < 8; ++m) {
+        const C uy = park[(8 + m) * NTH], uz = park[(16 + m) * NTH];
+        ny[m] = pmul(uz, v[m]);
+        nz[m] = pmul(C{-uy.x, -uy.y}, v[m]);
+      }
+    } else if (f == 4) {  // w_y:  n_x = -u_z w_y, n_z += u_x w_y
+#pragma unroll
+      for (int m = 0; m < 8; ++m) {
+        const C ux = park[m * NTH], uz = park[(16 + m) * NTH];
+        nx[m] = pmul(C{-uz.x, -uz.y}, v[m]);
+        nz[m] = pfma(ux, v[m], nz[m]);
+      }
+    } else {  // w_z: n_x += u_y w_z, n_y -= u_x w_z
+#pragma unroll
+      for (int m = 0; m < 8; ++m) {
+        const C ux = park[m * NTH], uy = park[(8 + m) * NTH];
+        nx[m] = pfma(uy, v[m], nx[m]);
+        ny[m] = pfms(ux, v[m], ny[m]);
       }
     }
   }
@@ -1142,6 +1180,7 @@ struct Launch3 {
   static constexpr size_t SM_F1S = col_tile_bytes(N, WH, sizeof(C)) + (size_t)18 * T * WH * sizeof(C);
   static_assert(SM_F1 <= kSmemMax, "fwd1 shared memory");
   static constexpr size_t SM_X = (size_t)L * smline_len(N / 2) * sizeof(C);
+  static constexpr size_t SM_XP = SM_X + (size_t)24 * (N / 16) * L * sizeof(C);  // + parked velocity fields
   // warp-per-line x pass when a line fits in one warp
   static constexpr bool XW = N / 16 <= 32;
   static constexpr int XW_WPB = 4;
@@ -1159,7 +1198,7 @@ struct Launch3 {
         set_smem(k3_inv1<R, N, WL, false>, SM_L);
         set_smem(k3_inv2<R, N, WYI>, SM_YI);
         set_smem(k3_fwd2<R, N, WYF>, SM_YF);
-        set_smem(k3_xpass<R, N, L>, SM_X);
+        if constexpr (!XW) set_smem(k3_xpass<R, N, L>, SM_XP);
         set_smem(k_xfwd_real<R, N, L>, SM_X);
         set_smem(k_xinv_real<R, N, L>, SM_X);
         set_smem(k3_fwd1<R, N, WH, MODE_RK1, true>, SM_F1S);
@@ -1191,8 +1230,8 @@ struct Launch3 {
               g, (long long)a.z0 * N, (C *)a.yb, tw, a.umax);
         } else {
           const long long lines = (long long)(a.nz > 0 ? a.nz : N) * N;
-          k3_xpass<R, N, L><<<(unsigned)(lines / L), (N / 16) * L, SM_X, s>>>(g, (long long)a.z0 * N, (C *)a.yb, tw,
-                                                                               a.umax);
+          k3_xpass<R, N, L><<<(unsigned)(lines / L), (N / 16) * L, SM_XP, s>>>(g, (long long)a.z0 * N, (C *)a.yb, tw,
+                                                                                a.umax);
         }
         break;
       case OP_FWD2: {
@@ -1247,6 +1286,7 @@ struct Launch2 {
   static constexpr size_t SM_L = col_smem(N, WL, sizeof(C), 0);
   static constexpr size_t SM_H = col_smem(N, WH, sizeof(C), 0);
   static constexpr size_t SM_X = (size_t)L * smline_len(N / 2) * sizeof(C);
+  static constexpr size_t SM_XP = SM_X + (size_t)24 * (N / 16) * L * sizeof(C);  // + parked velocity fields
   static constexpr int XW_WPB = 4;
   static constexpr int XW_LPW = N / 16 <= 32 ? 32 / (N / 16) : 1;
   // warp-per-line x pass when a line fits in one warp and there are enough lines
