@@ -58,6 +58,24 @@ def dist_env():
     return ws, rank, local
 
 
+def reduce_max(x: float, ws: int, device) -> float:
+    """The largest of the ranks' values (the job's time is its slowest rank's)."""
+    if ws <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(ws: int, points: int, steps: int, ms: float) -> float:
+    """Whole-job Mpoint*steps/s: every rank advances its own replica of `points`
+    grid points by `steps` steps in `ms` milliseconds (weak scaling)."""
+    return ws * points * steps / (ms / 1e3) / 1e6
+
+
 class ClockSampler:
     """nvidia-smi clocks / throttle reasons sampled during the timed region."""
 
@@ -191,6 +209,53 @@ def ensemble_bench(steps=50):
                          "task_order": ["member-major", "round-robin"][sched[2]]}}
 
 
+# The grids the paper times (Performance section: sequential and Beskow runs),
+# with its best published rate for each in Mpoint*steps/s (CPU; context only).
+PAPER_SHAPES = [
+    (2, 512, "fp64", 4.85), (2, 512, "fp32", 4.85),
+    (2, 1024, "fp64", 45.6), (2, 1024, "fp32", 45.6),
+    (2, 2048, "fp64", 82.2), (2, 2048, "fp32", 82.2),
+    (3, 128, "fp64", 77.7), (3, 128, "fp32", 77.7),
+    (3, 1024, "fp32", 493.7),
+]
+
+
+def paper_shapes(target_s=0.25):
+    """Mpoint*RK4-steps/s of the GPU path on the paper's grid sizes (random
+    initial fields of the 2D and 3D recipes, nu = 1e-3, dt = 1e-3), CUDA events
+    on a dedicated stream after two warm-up steps."""
+    import torch
+    from paper_1807_01769_gb300 import inputs, ns
+
+    out = []
+    stream = torch.cuda.Stream()
+    for dim, n, prec, paper in PAPER_SHAPES:
+        p = ns.NS_FP64 if prec == "fp64" else ns.NS_FP32
+        u0 = (inputs.random_vorticity_2d(n, seed=0, k0=8.0, a=1.0, energy=0.5) if dim == 2
+              else inputs.random_velocity_3d(n, seed=0, k0=4.0, a=2.0, energy=0.5))
+        with ns.Solver(dim, n, p, nu=1e-3, dt=1e-3) as s:
+            s.set_stream(stream.cuda_stream)
+            s.set_state_spectral(u0)
+            s.step(2)
+            torch.cuda.synchronize()
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ev0.record(stream)
+            s.step(1)
+            ev1.record(stream)
+            torch.cuda.synchronize()
+            k = max(3, min(500, int(target_s * 1e3 / max(ev0.elapsed_time(ev1), 1e-3))))
+            ev0.record(stream)
+            s.step(k)
+            ev1.record(stream)
+            torch.cuda.synchronize()
+            ms = ev0.elapsed_time(ev1) / k
+            e, _ = s.diagnostics()
+        out.append({"grid": f"{n}^{dim}", "dtype": prec, "steps": k, "ms_per_step": ms,
+                    "value": n ** dim / (ms / 1e3) / 1e6, "paper_best_cpu": paper, "energy_after": e})
+    return {"metric": "Mpoint*RK4-steps/s", "note": "paper_best_cpu: the paper's best CPU rate for the grid "
+            "(sequential for 2D 512^2, Beskow MPI runs otherwise), for context", "runs": out}
+
+
 def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
@@ -266,10 +331,7 @@ def run_gb300(args):
     barrier()
     clk = clocks.stop()
     ms = ev0.elapsed_time(ev1)
-    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-    if ws > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
+    ms_max = reduce_max(ms, ws, "cuda")
     e, om = s.diagnostics()
     if not (np.isfinite(e) and np.isfinite(om)):
         raise RuntimeError("non-finite state after the timed steps")
@@ -298,16 +360,12 @@ def run_gb300(args):
         s.get_state_spectral_ptr(h_out.data_ptr())
         spec = s.energy_spectrum()
     torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - t0
-    t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
-    if ws > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    e2e_s = float(t.item())
+    e2e_s = reduce_max(time.perf_counter() - t0, ws, "cuda")
     launches_per_step = sum(v[1] for k, v in prof.items()) // 3
 
     if rank == 0:
         pts = N_GRID ** 3
-        value = ws * pts * args.steps / (ms_max / 1e3) / 1e6
+        value = job_value(ws, pts, args.steps, ms_max)
         step_bytes = MODEL_BYTES_PER_POINT * pts
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -325,7 +383,7 @@ def run_gb300(args):
                             "algorithmic_gbs": v[2] / (v[0] / v[1] / 1e3) / 1e9}
                         for k, v in prof.items() if v[1] > 0},
             "clocks": clk,
-            "e2e": {"value": ws * pts * JOB_STEPS * e2e_reps / e2e_s / 1e6, "unit": UNIT,
+            "e2e": {"value": job_value(ws, pts, JOB_STEPS * e2e_reps, e2e_s * 1e3), "unit": UNIT,
                     "h2d_bytes_per_step": spec_bytes / JOB_STEPS,
                     "d2h_bytes_per_step": (spec_bytes + spec.nbytes) / JOB_STEPS,
                     "job": f"H2D of the FP64 initial spectrum (pinned), {JOB_STEPS} steps, D2H of the state and "
@@ -337,6 +395,8 @@ def run_gb300(args):
             line["cpu_baseline"] = cpu
         if ws == 1 and not args.no_ensemble:
             line["ensemble"] = ensemble_bench()
+        if ws == 1 and not args.no_paper_shapes:
+            line["paper_shapes"] = paper_shapes()
         print(json.dumps(line), flush=True)
     s.close()
     if ws > 1:
@@ -353,6 +413,7 @@ def main():
     ap.add_argument("--e2e-reps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-ensemble", action="store_true", help="skip the batched 2D ensemble measurement")
+    ap.add_argument("--no-paper-shapes", action="store_true", help="skip the paper-grid measurements")
     ap.add_argument("--n", type=int, default=512, help="grid size override (profiling of smaller cases only)")
     args = ap.parse_args()
     global N_GRID

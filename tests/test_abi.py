@@ -94,3 +94,32 @@ def test_ensemble_sizes_draw():
     s = inputs.ensemble_sizes(64)
     assert len(s) == 64 and set(s) <= {128, 256, 512}
     assert s == inputs.ensemble_sizes(64)
+
+
+def test_new_entry_points_check_arguments_before_any_device_call(ns):
+    L, E = ns.lib, ns.NS_EINVAL
+    d = ns.ctypes.c_double()
+    assert L.ns_set_scheme(None, 2) == E
+    assert L.ns_set_cfl(None, 0.5) == E
+    assert L.ns_get_time(None, ns.ctypes.byref(d), ns.ctypes.byref(d)) == E
+    assert L.ns_budget(None, None) == E
+    assert L.ns_state_to_phys_device(None, None) == E
+    assert L.ns_set_forcing_phys_device(None, None) == E
+    assert L.ns_f64_to_f32(None, None, 10, 1.0, None) == E
+    assert L.ns_f32_axpy_f64(None, None, None, 10, 1.0, None) == E
+    assert L.ns_cnn_num_params(None) == -1
+    assert L.ns_cnn_get_params(None, None) == E
+    assert L.ns_cnn_set_params(None, None) == E
+    assert L.ns_cnn_forward(None, None, None, 1, None) == E
+    f = ns.ctypes.c_float()
+    assert L.ns_cnn_gradients(None, None, None, 1, None, ns.ctypes.byref(f)) == E
+    assert L.ns_cnn_train_step(None, None, None, 1, 1e-3, None, None) == E
+    L.ns_cnn_destroy(None)
+
+
+@pytest.mark.parametrize("h,w,b", [(48, 64, 1), (64, 100, 1), (32, 32, 1), (64, 64, 0)])
+def test_cnn_rejects_bad_shapes_without_a_device(ns, h, w, b):
+    out = ns.ctypes.c_void_p()
+    assert ns.lib.ns_cnn_init(ns.ctypes.byref(out), h, w, b, 0) == ns.NS_EINVAL
+    assert not out.value
+    assert b"multiples of 64" in ns.lib.ns_cnn_last_error(None)

@@ -146,3 +146,55 @@ def test_budget_matches_oracle(ns, orc, dim, n, prec):
         e, om = s.diagnostics()
     assert pe == 0.0 and pz == 0.0
     assert abs(de - 2 * nu * om) < 1e-12 * de
+
+
+def test_rk2_with_forcing_matches_oracle(ns, orc):
+    n, nu, dt, steps = 128, 1e-3, 2e-3, 10
+    u0 = ic(2, n, seed=7)
+    f_phys = inputs.kolmogorov_forcing_2d(n)
+    ref = orc.step(2, n, nu, dt, steps, u0, forcing=orc.phys_to_state(2, n, f_phys), order=2)
+    for prec in (FP64, FP32):
+        with ns.Solver(2, n, prec, nu=nu, dt=dt, forcing_phys=f_phys) as s:
+            s.set_scheme(2)
+            s.set_state_spectral(u0)
+            s.step(steps)
+            assert rel_l2(s.get_state_spectral(), ref) < TOL[prec]
+
+
+@pytest.mark.parametrize("dim,n", [(2, 64), (3, 32)])
+def test_cfl_on_a_zero_field_takes_the_initial_dt(ns, dim, n):
+    dt0 = 3e-3
+    with ns.Solver(dim, n, FP64, nu=1e-3, dt=dt0) as s:
+        s.set_state_spectral(np.zeros_like(ic(dim, n)))
+        s.set_cfl(0.5)
+        s.step(4)
+        t, dt = s.time()
+        assert dt == dt0 and abs(t - 4 * dt0) < 1e-15
+        assert not np.any(s.get_state_spectral())
+
+
+def test_cfl_with_3d_forcing_matches_oracle(ns, orc):
+    n, nu, dt_max, cfl, steps = 32, 2e-3, 0.05, 0.5, 6
+    u0 = 4.0 * ic(3, n, seed=8)
+    f_phys = orc.state_to_phys(3, n, ic(3, n, seed=9))
+    ref, dts = orc.step_cfl(3, n, nu, dt_max, cfl, steps, u0, forcing=orc.phys_to_state(3, n, f_phys))
+    with ns.Solver(3, n, FP64, nu=nu, dt=dt_max, forcing_phys=f_phys) as s:
+        s.set_state_spectral(u0)
+        s.set_cfl(cfl)
+        s.step(steps)
+        t, dt = s.time()
+        got = s.get_state_spectral()
+    assert abs(t - dts.sum()) < 1e-12 * dts.sum() and abs(dt - dts[-1]) < 1e-12 * dts[-1]
+    assert rel_l2(got, ref) < TOL[FP64]
+
+
+def test_budget_without_viscosity_has_no_dissipation(ns, orc):
+    n = 64
+    u = ic(2, n, seed=10)
+    f_phys = inputs.kolmogorov_forcing_2d(n)
+    with ns.Solver(2, n, FP64, nu=0.0, dt=1e-3, forcing_phys=f_phys) as s:
+        s.set_state_spectral(u)
+        pe, de, pz, dz = s.budget()
+    ref = orc.budget(2, n, 0.0, u, orc.phys_to_state(2, n, f_phys))
+    assert de == 0.0 and dz == 0.0
+    assert abs(pe - ref[0]) < 1e-12 * abs(ref[0]) and abs(pz - ref[2]) < 1e-12 * abs(ref[2])
