@@ -338,7 +338,6 @@ __global__ void __launch_bounds__((N / 8) * W) k3_inv2(Geo g, int nf, int z0, co
   using C = typename CplxOf<R>::T;
   constexpr int T = N / 8;
   constexpr int P = pitch_of(W, sizeof(C));
-  constexpr size_t EXTRA_SMEM = 0;
   C *sm = dyn_smem<C>();
   const int w = threadIdx.x % W, t = threadIdx.x / W;
   const int kx = blockIdx.x * W + w;
@@ -563,7 +562,6 @@ __global__ void __launch_bounds__((N / 8) * W) k3_fwd2(Geo g, int nf, int z0, co
   using C = typename CplxOf<R>::T;
   constexpr int T = N / 8;
   constexpr int P = pitch_of(W, sizeof(C));
-  constexpr size_t EXTRA_SMEM = 0;
   C *sm = dyn_smem<C>();
   const int w = threadIdx.x % W, t = threadIdx.x / W;
   const int kx = blockIdx.x * W + w;
@@ -697,7 +695,7 @@ __device__ __forceinline__ C rk_stage(C nv, C uu, C a, R e, R e2, const StepBufs
 // e = E, e2 = E2 of the mode; returns the next stage input.
 template <int MODE, typename C, typename R>
 __device__ __forceinline__ C rk_update(C nv, long long idx, R e, R e2, const StepBufs<R> &b) {
-  const R dt = (MODE == MODE_RHS || MODE == MODE_PROJ) ? (R)0 : stage_dt(b);
+  const R dt = (MODE >= MODE_RK1 && MODE <= MODE_RK4) ? stage_dt(b) : (R)0;  // M1/M2: loaded in rk_stage
   if (MODE == MODE_RK1) {
     const C uu = b.u[idx];
     const R c1 = dt * e / (R)6;
