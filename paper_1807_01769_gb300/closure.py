@@ -3,7 +3,7 @@ has no learned model; its 2D solver and Kolmogorov-type forcing are in the
 2D benchmark and forcing sections).
 
 The coarse solve advances the truncated vorticity of an N_c^2 grid; the
-fine solve (N_f^2, same nu, same forcing) is the judge.  With the spectral
+fine solve (N_f^2, same nu, same forcing) is the reference.  With the spectral
 cut-off filter P (keep the modes the coarse grid retains) and the nonlinear
 tendency N(omega) = -u . grad omega + F of the library (``ns_eval_rhs``),
 the closure target is
@@ -325,7 +325,7 @@ def a_posteriori(cfg: KolmogorovConfig, tr: Trained, seed: int, t_eval: float, e
     kc = inputs.truncation(nc)[0]
     sh = slice(1, kc + 1)
     rows = []
-    with fine_solver(cfg) as fine, coarse_solver(cfg) as plain, coarse_solver(cfg) as judge:
+    with fine_solver(cfg) as fine, coarse_solver(cfg) as plain, coarse_solver(cfg) as filtered:
         closed = ClosureSolver(cfg, tr)
         try:
             fine.set_state_spectral(inputs.random_vorticity_2d(cfg.n_fine, seed, k0=cfg.ic_k0, energy=cfg.ic_energy))
@@ -340,15 +340,15 @@ def a_posteriori(cfg: KolmogorovConfig, tr: Trained, seed: int, t_eval: float, e
                 closed.step(cfg.steps(every, False))
                 t += every
                 ref = restrict_2d(fine.get_state_spectral(), cfg.n_fine, nc)
-                judge.set_state_spectral(ref)
+                filtered.set_state_spectral(ref)
                 wp, wq = plain.get_state_spectral(), closed.get_state_spectral()
-                er, ep, eq = judge.energy_spectrum(), plain.energy_spectrum(), closed.solver.energy_spectrum()
+                er, ep, eq = filtered.energy_spectrum(), plain.energy_spectrum(), closed.solver.energy_spectrum()
 
                 def spec_err(e):
                     return float(np.mean(np.abs(np.log(np.maximum(e[sh], 1e-300) / np.maximum(er[sh], 1e-300)))))
 
                 row = {"t": round(t, 6), "err_plain": rel_l2(wp, ref), "err_closure": rel_l2(wq, ref),
-                       "enstrophy_fine": judge.diagnostics()[1], "enstrophy_plain": plain.diagnostics()[1],
+                       "enstrophy_fine": filtered.diagnostics()[1], "enstrophy_plain": plain.diagnostics()[1],
                        "enstrophy_closure": closed.solver.diagnostics()[1],
                        "spec_err_plain": spec_err(ep), "spec_err_closure": spec_err(eq),
                        "fell_back": closed.fell_back}
