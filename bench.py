@@ -122,19 +122,26 @@ class ClockSampler:
                 "samples": len(sm), "power_w_max": max(power) if power else None}
 
 
+# the sources that define the 3D FP32 pass kernels (their launch shapes included)
+PASS_KERNEL_SOURCES = ("ns_fft.cuh", "ns_internal.h", "ns_k3_f32.cu", "ns_kernels.cuh")
+
+
+def pass_kernel_digest() -> str:
+    h = hashlib.sha1()
+    csrc = os.path.join(ROOT, "paper_1807_01769_gb300", "csrc")
+    for f in PASS_KERNEL_SOURCES:
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:12]
+
+
 def traffic_from_profiles(kernel: str):
     """DRAM bytes per launch of a kernel from the committed ncu summary, if the
-    kernel source is unchanged since the counters were taken."""
+    pass-kernel sources are unchanged since the counters were taken."""
     path = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
     if not os.path.exists(path):
         return None
-    h = hashlib.sha1()
-    csrc = os.path.join(ROOT, "paper_1807_01769_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
-        if f.endswith((".cu", ".cuh", ".h")):
-            with open(os.path.join(csrc, f), "rb") as fh:
-                h.update(fh.read())
-    digest = h.hexdigest()[:12]
+    digest = pass_kernel_digest()
     for line in open(path):
         kv = dict(tok.split("=", 1) for tok in line.split() if "=" in tok)
         if kv.get("kernel") == kernel and kv.get("n") == str(N_GRID) and kv.get("source_sha") == digest:

@@ -567,30 +567,24 @@ int ns_get_state(ns_state *s, double *phys_host) {
 int ns_set_state_spectral(ns_state *s, const double *spec_host) {
   if (!s || !spec_host) return s ? fail(s, NS_EINVAL, "ns_set_state_spectral: null buffer") : NS_EINVAL;
   DevGuard dg(s->dev);
-  const long long rows = state_rows(s);
+  // the components follow each other in both layouts (st_comp = rows * hs),
+  // so one copy and one conversion cover them all
+  const long long rows = state_rows(s) * s->ncomp;
   const size_t bytes = sizeof(double) * 2 * (size_t)rows * s->g.h;
-  for (int c = 0; c < s->ncomp; ++c) {
-    NS_CK(s, cudaMemcpyAsync(s->staging, spec_host + c * 2 * rows * s->g.h, bytes, cudaMemcpyHostToDevice,
-                             s->stream));
-    int e = nsk::spec_in(s->prec, (char *)s->u + c * s->cs * s->g.st_comp, (const double *)s->staging, rows,
-                         s->g.h, s->g.hs, s->stream);
-    if (e) return fail(s, NS_ECUDA, "spec_in launch failed: %s", cudaGetErrorString((cudaError_t)e));
-  }
+  NS_CK(s, cudaMemcpyAsync(s->staging, spec_host, bytes, cudaMemcpyHostToDevice, s->stream));
+  int e = nsk::spec_in(s->prec, s->u, (const double *)s->staging, rows, s->g.h, s->g.hs, s->stream);
+  if (e) return fail(s, NS_ECUDA, "spec_in launch failed: %s", cudaGetErrorString((cudaError_t)e));
   s->zvalid = false;
   NS_CK(s, cudaStreamSynchronize(s->stream));
   return NS_OK;
 }
 
 static int get_spectral(ns_state *s, const void *src, double *spec_host) {
-  const long long rows = state_rows(s);
+  const long long rows = state_rows(s) * s->ncomp;  // all components at once, as in ns_set_state_spectral
   const size_t bytes = sizeof(double) * 2 * (size_t)rows * s->g.h;
-  for (int c = 0; c < s->ncomp; ++c) {
-    int e = nsk::spec_out(s->prec, (double *)s->staging, (const char *)src + c * s->cs * s->g.st_comp, rows, s->g.h,
-                          s->g.hs, s->stream);
-    if (e) return fail(s, NS_ECUDA, "spec_out launch failed: %s", cudaGetErrorString((cudaError_t)e));
-    NS_CK(s, cudaMemcpyAsync(spec_host + c * 2 * rows * s->g.h, s->staging, bytes, cudaMemcpyDeviceToHost,
-                             s->stream));
-  }
+  int e = nsk::spec_out(s->prec, (double *)s->staging, src, rows, s->g.h, s->g.hs, s->stream);
+  if (e) return fail(s, NS_ECUDA, "spec_out launch failed: %s", cudaGetErrorString((cudaError_t)e));
+  NS_CK(s, cudaMemcpyAsync(spec_host, s->staging, bytes, cudaMemcpyDeviceToHost, s->stream));
   NS_CK(s, cudaStreamSynchronize(s->stream));
   return NS_OK;
 }

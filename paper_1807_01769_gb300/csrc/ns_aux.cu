@@ -8,7 +8,8 @@
 // the shell index of 32 consecutive kx is non-decreasing and a warp-wide
 // segmented scan adds each run of equal shells in a fixed order before one
 // lane per run updates the warp's private bins.  Blocks write partial sums to
-// scratch; a single block adds them in block order.
+// scratch; one warp per output then adds them in a fixed order (lanes over
+// the blocks, then a butterfly).
 #include <climits>
 
 #include "ns_fft.cuh"
@@ -171,12 +172,20 @@ __global__ void __launch_bounds__(32 * kDiagWarps) k_diag(Geo g, const C *__rest
   }
 }
 
+// out[j] = sum over blocks of scratch[b][j]: one warp per column j, lanes
+// striding over the blocks, then a fixed butterfly (the same order every call).
 __global__ void k_diag_final(const double *__restrict__ scratch, long long nblocks, int width, double *__restrict__ out) {
-  for (int j = threadIdx.x; j < width; j += blockDim.x) {
-    double sacc = 0.0;
-    for (long long b = 0; b < nblocks; ++b) sacc += scratch[b * width + j];
-    out[j] = sacc;
-  }
+  const int j = (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) / 32), lane = threadIdx.x % 32;
+  if (j >= width) return;  // uniform over the warp
+  double sacc = 0.0;
+  for (long long b = lane; b < nblocks; b += 32) sacc += scratch[b * width + j];
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) sacc += __shfl_xor_sync(0xffffffffu, sacc, off);
+  if (lane == 0) out[j] = sacc;
+}
+
+static void diag_final(const double *scratch, long long nblocks, int width, double *out, cudaStream_t s) {
+  k_diag_final<<<(unsigned)((width + 7) / 8), 256, 0, s>>>(scratch, nblocks, width, out);
 }
 
 int diagnostics(int prec, const Geo &g, const void *u, int nbins, double *scratch, double *out, cudaStream_t s) {
@@ -191,7 +200,7 @@ int diagnostics(int prec, const Geo &g, const void *u, int nbins, double *scratc
     cudaFuncSetAttribute(k_diag<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     k_diag<double2><<<(unsigned)nb, 32 * kDiagWarps, smem, s>>>(g, (const double2 *)u, nbins, rpb, scratch);
   }
-  k_diag_final<<<1, 256, 0, s>>>(scratch, nb, nbins + 2, out);
+  diag_final(scratch, nb, nbins + 2, out, s);
   return (int)cudaGetLastError();
 }
 
@@ -312,7 +321,7 @@ int budget(int prec, const Geo &g, const void *u, const void *F, double nu, doub
   else
     k_budget<double2><<<(unsigned)nb, 32 * kDiagWarps, 0, s>>>(g, (const double2 *)u, (const double2 *)F, nu, rpb,
                                                                scratch);
-  k_diag_final<<<1, 32, 0, s>>>(scratch, nb, 4, out);
+  diag_final(scratch, nb, 4, out, s);
   return (int)cudaGetLastError();
 }
 
