@@ -56,6 +56,8 @@ extern "C" {
 #define NS_ECUDA (-3)        /* a CUDA runtime call or kernel launch failed */
 #define NS_EUNSUPPORTED (-4) /* grid size or precision this build does not handle */
 #define NS_ENONFINITE (-5)   /* diagnostics found a NaN or Inf in the state */
+#define NS_ETIMEOUT (-6)     /* a bounded device wait (TMA tile load) gave up; reported by
+                                ns_sync and the diagnostics, the affected steps are invalid */
 
 #define NS_FP64 0 /* state, FFTs and products in double precision */
 #define NS_FP32 1 /* state, FFTs and products in single precision; integrating

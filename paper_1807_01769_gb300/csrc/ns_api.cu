@@ -80,6 +80,11 @@ struct ns_state {
   double cfl = 0, t = 0;
   unsigned long long *umax = nullptr;
   double *ctl = nullptr;
+  // TMA: tensor map over yb (3D, 128-byte forward y-pass tile rows), device error word
+  alignas(128) unsigned char tmap_yb[128];
+  alignas(128) unsigned char tmap_zb[128];
+  bool has_tmap = false, has_tmap_zb = false;
+  int *derr = nullptr;
   // 3D step schedule: the y inverse, x pass and y forward of a stage run as a
   // pipeline over zchunks plane chunks on three forked streams, the y inverse
   // at most zlook chunks ahead of the x pass
@@ -150,6 +155,9 @@ Args base_args(ns_state *s) {
   a.yb = s->yb;
   a.dt = s->dt;
   a.dtp = s->cfl > 0 ? s->ctl : nullptr;
+  a.tmap_yb = s->has_tmap ? s->tmap_yb : nullptr;
+  a.tmap_zb = s->has_tmap_zb ? s->tmap_zb : nullptr;
+  a.err = s->derr;
   a.nsm = s->nsm;
   return a;
 }
@@ -325,7 +333,7 @@ int phys_to_spec(ns_state *s, const double *host, void *dst) {
 
 void free_all(ns_state *s) {
   if (s->graph) cudaGraphExecDestroy(s->graph);
-  void *ptrs[] = {s->tw, s->ef, s->ef2, s->u, s->acc, s->F, s->zb, s->yb, s->staging, s->diag, s->umax, s->ctl};
+  void *ptrs[] = {s->tw, s->ef, s->ef2, s->u, s->acc, s->F, s->zb, s->yb, s->staging, s->diag, s->umax, s->ctl, s->derr};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   if (s->own) cudaStreamDestroy(s->own);
@@ -501,6 +509,27 @@ int ns_init(ns_state **out, const ns_grid *grid, double nu, double dt, const dou
       (rc = dmalloc(s, &s->diag, sizeof(double) * (size_t)(s->diag_scratch + s->nbins + 2))))
     return bail(rc);
   if (forcing_phys && (rc = dmalloc(s, &s->F, field))) return bail(rc);
+  if ((rc = dmalloc(s, (void **)&s->derr, sizeof(int)))) return bail(rc);
+  INIT_CK(cudaMemsetAsync(s->derr, 0, sizeof(int), s->stream));
+  if (g.dim == 3) {
+    // TMA tensor maps over the y-pass inputs, in 8-byte elements.  yb as 2D:
+    // 6 N^2 rows of hs complex, boxes of one forward tile (128-byte rows) by
+    // up to 256 rows.  zb as 3D: (hs complex, c rows, 6 N planes), boxes of
+    // one inverse tile by up to 256 rows by one plane.
+    const unsigned long long e8 = s->cs / 8, row = (unsigned long long)g.hs * s->cs;
+    const int wf = nsk::y_fwd_columns((int)s->cs, g.N), wi = nsk::y_inv_columns((int)s->cs, g.N);
+    if (wf * s->cs == 128) {
+      const unsigned long long dims[2] = {g.hs * e8, 6ull * g.N * g.N}, strides[1] = {row};
+      const unsigned box[2] = {(unsigned)(wf * e8), (unsigned)std::min(g.N, 256)};
+      s->has_tmap = nsk::make_tensor_map(s->tmap_yb, s->yb, 2, dims, strides, box) == 0;
+    }
+    if ((wi * s->cs) % 16 == 0) {
+      const unsigned long long dims[3] = {g.hs * e8, (unsigned long long)g.c, 6ull * g.N},
+                               strides[2] = {row, row * g.c};
+      const unsigned box[3] = {(unsigned)(wi * e8), (unsigned)std::min(g.c, 256), 1};
+      s->has_tmap_zb = nsk::make_tensor_map(s->tmap_zb, s->zb, 3, dims, strides, box) == 0;
+    }
+  }
   INIT_CK(cudaMemcpyAsync(s->tw, tw.data(), tw.size(), cudaMemcpyHostToDevice, s->stream));
   INIT_CK(cudaMemcpyAsync(s->ef, ef.data(), ef.size(), cudaMemcpyHostToDevice, s->stream));
   INIT_CK(cudaMemcpyAsync(s->ef2, ef2.data(), ef2.size(), cudaMemcpyHostToDevice, s->stream));
@@ -526,12 +555,21 @@ int ns_set_stream(ns_state *s, void *cuda_stream) {
   return NS_OK;
 }
 
+// Reads (and clears) the device error word after a synchronisation.
+static int check_err(ns_state *s) {
+  int e = 0;
+  NS_CK(s, cudaMemcpy(&e, s->derr, sizeof(int), cudaMemcpyDeviceToHost));
+  if (e == 0) return NS_OK;
+  NS_CK(s, cudaMemset(s->derr, 0, sizeof(int)));
+  return fail(s, NS_ETIMEOUT, "a bounded device wait gave up (code %d): results of the affected steps are invalid", e);
+}
+
 int ns_sync(ns_state *s) {
   if (!s) return NS_EINVAL;
   DevGuard dg(s->dev);
   NS_CK(s, cudaStreamSynchronize(s->stream));
   NS_CK(s, cudaGetLastError());
-  return NS_OK;
+  return check_err(s);
 }
 
 int ns_set_state(ns_state *s, const double *phys_host) {
@@ -707,7 +745,7 @@ static int run_diag(ns_state *s, std::vector<double> &out) {
   out.resize(s->nbins + 2);
   NS_CK(s, cudaMemcpyAsync(out.data(), dout, sizeof(double) * out.size(), cudaMemcpyDeviceToHost, s->stream));
   NS_CK(s, cudaStreamSynchronize(s->stream));
-  return NS_OK;
+  return check_err(s);
 }
 
 int ns_diagnostics(ns_state *s, double *energy, double *enstrophy) {

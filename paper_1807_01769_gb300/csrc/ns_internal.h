@@ -60,6 +60,9 @@ struct Args {
   int inv;     // OP_FWD1: 1 = fuse the next stage's first inverse axis
   double dt;
   const double *dtp;         // OP_FWD1: time step in device memory (nullable: use dt)
+  const void *tmap_yb;       // OP_FWD2: 2D tensor map over yb for TMA loads (nullable: plain loads)
+  const void *tmap_zb;       // OP_INV2: 3D tensor map over zb for TMA loads (nullable: plain loads)
+  int *err;                  // device error word: a bounded wait that gave up writes a nonzero code
   unsigned long long *umax;  // OP_XPASS: [dim][kUmaxSlots] maxima of |u_i| as double bits (nullable)
   int nsm;     // streaming multiprocessors of the device (persistent grids)
   int z0, nz;  // 3D OP_INV2 / OP_XPASS / OP_FWD2: planes z0 .. z0+nz-1 (nz = 0: all)
@@ -87,6 +90,27 @@ int diagnostics(int prec, const Geo &g, const void *u, int nbins, double *scratc
 // ef[k] = exp(-nu k^2 dt), ef2[k] = exp(-nu k^2 dt / 2), k = 0 .. kc.
 int cfl_update(int prec, const Geo &g, double nu, unsigned long long *umax, double *ctl, void *ef, void *ef2,
                cudaStream_t s);
+// Tensor map (CUtensorMap, 128 bytes at out) of a `rank`-dimensional array of
+// 8-byte elements (rank 2 or 3): dims[0] innermost, strides_bytes[i] the byte
+// stride of dimension i + 1, boxes of box[] elements (ns_tma.cu).  0 = ok,
+// else a cudaError_t / CUresult value.
+int make_tensor_map(void *out, const void *base, int rank, const unsigned long long *dims,
+                    const unsigned long long *strides_bytes, const unsigned *box);
+
+// Columns per tile of the y passes for complex elements of csize bytes on
+// N-point columns (tile rows of at most 128 bytes).  Inverse: 512-thread
+// blocks so that two independent blocks share an SM, except that FP32
+// columns of 512 or more points take 1024 threads (TMA loads: 512^3 inv2
+// 0.797 -> 0.779 ms with 16 columns; 1024^3 9.83 -> 9.59 ms with 8).  Forward:
+// up to 1024-thread blocks for 128-byte rows (512^3 FP32: fwd2 0.533 -> 0.451
+// ms per launch with 16 columns before TMA, 0.366 with it).
+__host__ __device__ constexpr int y_tile_cap(int threads, int csize, int n) {
+  return (128 / csize) < (threads / (n / 8)) ? (128 / csize) : (threads / (n / 8) > 0 ? threads / (n / 8) : 1);
+}
+__host__ __device__ constexpr int y_inv_columns(int csize, int n) {
+  return y_tile_cap(csize == 8 && n >= 512 ? 1024 : 512, csize, n);
+}
+__host__ __device__ constexpr int y_fwd_columns(int csize, int n) { return y_tile_cap(1024, csize, n); }
 // Budget terms {P_E, D_E, P_Z, D_Z} (forcing power and dissipation of energy
 // and enstrophy) into out[0..3]; scratch holds diag_blocks(g) * 4 doubles.
 int budget(int prec, const Geo &g, const void *u, const void *F, double nu, double *scratch, double *out,

@@ -21,6 +21,8 @@
 // simulation object": FFT, IFFT, dealiasing, divergence, curl; "Tri-dimensional
 // simulations": FFT, RK4, curl, vector product, projection).
 #pragma once
+#include <cuda.h>  // CUtensorMap (a kernel parameter type; no driver calls here)
+
 #include "ns_fft.cuh"
 #include "ns_internal.h"
 
@@ -42,19 +44,14 @@ template <typename R, int N>
 __host__ __device__ constexpr int w_heavy() {
   return cmin(wmax<R>(), cmax(1, (sizeof(R) == 4 ? 512 : 256) / (N / 8)));
 }
-// columns per tile of the y passes.  Inverse: 512-thread blocks so that two
-// independent blocks share an SM, except that FP32 1024-point columns take
-// 1024 threads for 8 columns (64-byte rows; 1024^3: 9.83 -> 9.59 ms).  Forward:
-// up to 1024-thread blocks for 128-byte row segments (measured at 512^3 FP32:
-// fwd2 0.533 -> 0.451 ms per launch with 16 columns, while inv2 slows from
-// 0.832 to 0.904 ms).
+// columns per tile of the y passes (rules in ns_internal.h)
 template <typename R, int N>
 __host__ __device__ constexpr int w_yinv() {
-  return cmin(wmax<R>(), cmax(1, (sizeof(R) == 4 && N >= 1024 ? 1024 : 512) / (N / 8)));
+  return y_inv_columns((int)sizeof(R) * 2, N);
 }
 template <typename R, int N>
 __host__ __device__ constexpr int w_yfwd() {
-  return cmin(wmax<R>(), cmax(1, 1024 / (N / 8)));
+  return y_fwd_columns((int)sizeof(R) * 2, N);
 }
 // lines per block of the x kernels (N/16 threads per line); lines longer
 // than a warp in FP32: one line per block, whose barriers then span only that
@@ -79,11 +76,13 @@ __host__ __device__ constexpr size_t col_smem(int N, int W, int csize, size_t ex
   return (col_db(N, W, csize, extra) ? 2 : 1) * col_tile_bytes(N, W, csize) + extra;
 }
 
+// dynamic shared memory, 128-byte aligned (TMA destinations need it)
 template <typename C>
 __device__ __forceinline__ C *dyn_smem() {
-  extern __shared__ __align__(16) unsigned char ns_dyn_smem[];
+  extern __shared__ __align__(128) unsigned char ns_dyn_smem[];
   return reinterpret_cast<C *>(ns_dyn_smem);
 }
+__device__ __forceinline__ unsigned smem_addr(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
 
 // Loads of data read exactly once (pass inputs): kept out of L1 so that the
 // reused twiddle and factor tables stay there.
@@ -594,6 +593,206 @@ __global__ void __launch_bounds__((N / 8) * W) k3_fwd2(Geo g, int nf, int z0, co
   }
 }
 
+// ------------------------------------------------ TMA column-tile loads ---
+// One mbarrier per block tracks the bytes of the tile in flight.  Waits are
+// bounded: after kWaitSpins failed polls the waiting thread gives up and the
+// block leaves the kernel together, with a nonzero code in the error word.
+constexpr long long kWaitSpins = 1LL << 22;
+enum ErrCode { ERR_TMA_TIMEOUT = 1 };
+
+__device__ __forceinline__ void mbar_init(unsigned long long *bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long *bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_addr(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long *bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// bounded wait for the phase with the given parity to complete
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long *bar, unsigned parity) {
+  for (long long i = 0; i < kWaitSpins; ++i)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+// order this thread's earlier generic-proxy shared accesses before later
+// async-proxy (TMA) accesses of the same shared memory
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+}
+// box at (x, y) of a 2D tensor map into shared memory, completing on bar
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *tm, int x, int y, unsigned long long *bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];\n" ::"r"(
+          smem_addr(dst)),
+      "l"(reinterpret_cast<unsigned long long>(tm)), "r"(x), "r"(y), "r"(smem_addr(bar))
+      : "memory");
+}
+
+// box at (x, y, z) of a 3D tensor map into shared memory, completing on bar
+__device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *tm, int x, int y, int z,
+                                            unsigned long long *bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];\n" ::
+          "r"(smem_addr(dst)),
+      "l"(reinterpret_cast<unsigned long long>(tm)), "r"(x), "r"(y), "r"(z), "r"(smem_addr(bar))
+      : "memory");
+}
+
+// Retained rows of a truncated axis (c = 2 kc + 1) and the TMA boxes that
+// cover them: rows per box (at most 256) and boxes per column tile.
+__host__ __device__ constexpr int trunc_rows(int n) { return 2 * ((n - 1) / 3) + 1; }
+__host__ __device__ constexpr int tma_box_rows(int rows) { return rows < 256 ? rows : 256; }
+__host__ __device__ constexpr int tma_boxes(int rows) { return (rows + tma_box_rows(rows) - 1) / tma_box_rows(rows); }
+
+// inv2 with TMA loads: the same arithmetic as k3_inv2.  Field f's input
+// column tile (the c retained ky rows of plane (f, z), W columns) lands in a
+// dense [rows][W] shared tile from a 3D tensor map over zb (kx, ky, f N + z);
+// the last box reaches past row c, where the tensor ends, so those rows are
+// zero-filled without any memory traffic.  Same hand-off as k3_fwd2_tma.
+template <typename R, int N, int W>
+__global__ void __launch_bounds__((N / 8) * W) k3_inv2_tma(Geo g, int nf, int z0, const __grid_constant__ CUtensorMap tm,
+                                                            typename CplxOf<R>::T *__restrict__ yb,
+                                                            const typename CplxOf<R>::T *__restrict__ tw, int *err) {
+  using C = typename CplxOf<R>::T;
+  constexpr int T = N / 8;
+  constexpr int P = pitch_of(W, sizeof(C));
+  constexpr int CR = trunc_rows(N), BOXR = tma_box_rows(CR), NBOX = tma_boxes(CR);
+  constexpr size_t LAND = (size_t)NBOX * BOXR * W * sizeof(C);
+  constexpr bool DB = col_db(N, W, sizeof(C), LAND + 16);
+  C *sm = dyn_smem<C>();
+  C *land = sm + (DB ? 2 : 1) * N * P;  // [NBOX * BOXR][W]
+  unsigned long long *bar = reinterpret_cast<unsigned long long *>(land + NBOX * BOXR * W);
+  int &s_ok = *reinterpret_cast<int *>(bar + 1);
+  const int w = threadIdx.x % W, t = threadIdx.x / W;
+  const int kx = blockIdx.x * W + w;
+  const bool valid = kx < g.h;
+  const int z = z0 + blockIdx.y;
+  const int x8 = blockIdx.x * W * (int)(sizeof(C) / 8);
+  auto issue = [&](int f) {
+    mbar_expect_tx(bar, (unsigned)LAND);
+#pragma unroll
+    for (int b = 0; b < NBOX; ++b) tma_load_3d(land + b * BOXR * W, &tm, x8, b * BOXR, f * N + z, bar);
+  };
+  if (threadIdx.x == 0) {
+    mbar_init(bar, 1);
+    issue(0);
+  }
+  int row[8];
+  bool live[8];
+#pragma unroll
+  for (int m = 0; m < 8; ++m) {
+    const int n = t + T * m;
+    live[m] = valid && retained(n, N, g.kc);
+    row[m] = compact_of(n, N, g.kc, g.c);
+  }
+  C *out = yb + (long long)z * N * g.hs + kx;
+  for (int f = 0; f < nf; ++f) {
+    if (threadIdx.x == 0) {
+      bool ok = mbar_wait_bounded(bar, f & 1);
+      if (!ok) {
+        atomicExch(err, ERR_TMA_TIMEOUT);
+        mbar_wait_bounded(bar, f & 1);  // give the copy in flight a last chance to land
+      }
+      s_ok = ok;
+    }
+    __syncthreads();
+    if (!s_ok) return;  // the whole block leaves together
+    mbar_try_wait(bar, f & 1);  // completed: acquires the tile for this thread
+    C v[8];
+#pragma unroll
+    for (int m = 0; m < 8; ++m) v[m] = live[m] ? land[row[m] * W + w] : czero<C>();
+    __syncthreads();  // every thread has its values: the tile may be refilled
+    if (threadIdx.x == 0 && f + 1 < nf) {
+      fence_proxy_async_smem();
+      issue(f + 1);
+    }
+    fft_line<N, +1>(v, t, tw + N, SmCol<C, DB>{sm + w, P, N * P});
+    if (valid) {
+      C *o = out + f * g.yb_f;
+#pragma unroll
+      for (int m = 0; m < 8; ++m) o[(long long)(t + T * m) * g.hs] = v[m];
+    }
+  }
+}
+
+// fwd2 with TMA loads: the same arithmetic as k3_fwd2.  Field f's column tile
+// (N rows of W columns, rows (f N + z) N .. + N - 1 of yb viewed as a 2D array
+// of 8-byte elements) lands in a dense [N][W] shared tile, issued by thread 0
+// one field ahead (boxes of at most 256 rows); thread 0 waits for it (bounded),
+// the block barrier hands it to every thread, and each thread reads its eight
+// values t + T m of column w from the tile.
+template <typename R, int N, int W>
+__global__ void __launch_bounds__((N / 8) * W) k3_fwd2_tma(Geo g, int nf, int z0, const __grid_constant__ CUtensorMap tm,
+                                                            typename CplxOf<R>::T *__restrict__ zb,
+                                                            const typename CplxOf<R>::T *__restrict__ tw, int *err) {
+  using C = typename CplxOf<R>::T;
+  constexpr int T = N / 8;
+  constexpr int P = pitch_of(W, sizeof(C));
+  constexpr bool DB = col_db(N, W, sizeof(C), (size_t)N * W * sizeof(C) + 16);
+  constexpr int BOXR = N < 256 ? N : 256;
+  constexpr unsigned TILE_BYTES = (unsigned)(N * W * sizeof(C));
+  static_assert(W * sizeof(C) == 128, "128-byte tile rows");
+  C *sm = dyn_smem<C>();
+  C *land = sm + (DB ? 2 : 1) * N * P;  // [N][W]
+  unsigned long long *bar = reinterpret_cast<unsigned long long *>(land + N * W);
+  int &s_ok = *reinterpret_cast<int *>(bar + 1);
+  const int w = threadIdx.x % W, t = threadIdx.x / W;
+  const int kx = blockIdx.x * W + w;
+  const bool valid = kx < g.h;
+  const int z = z0 + blockIdx.y;
+  const int x8 = blockIdx.x * W * (int)(sizeof(C) / 8);
+  auto issue = [&](int f) {
+    mbar_expect_tx(bar, TILE_BYTES);
+    const int row0 = (f * N + z) * N;
+#pragma unroll
+    for (int r = 0; r < N; r += BOXR) tma_load_2d(land + r * W, &tm, x8, row0 + r, bar);
+  };
+  if (threadIdx.x == 0) {
+    mbar_init(bar, 1);
+    issue(0);
+  }
+  C *out = zb + (long long)z * g.c * g.hs + kx;
+  for (int f = 0; f < nf; ++f) {
+    if (threadIdx.x == 0) {
+      bool ok = mbar_wait_bounded(bar, f & 1);
+      if (!ok) {
+        atomicExch(err, ERR_TMA_TIMEOUT);
+        mbar_wait_bounded(bar, f & 1);  // give the copy in flight a last chance to land
+      }
+      s_ok = ok;
+    }
+    __syncthreads();
+    if (!s_ok) return;  // the whole block leaves together
+    mbar_try_wait(bar, f & 1);  // completed: acquires the tile for this thread
+    C v[8];
+#pragma unroll
+    for (int m = 0; m < 8; ++m) v[m] = land[(t + T * m) * W + w];
+    __syncthreads();  // every thread has its values: the tile may be refilled
+    if (threadIdx.x == 0 && f + 1 < nf) {
+      fence_proxy_async_smem();
+      issue(f + 1);
+    }
+    fft_line<N, -1>(v, t, tw + N, SmCol<C, DB>{sm + w, P, N * P});
+    if (valid) {
+      C *o = out + f * g.zb_f;
+#pragma unroll
+      for (int m = 0; m < 8; ++m) {
+        const int n = t + T * m;
+        if (retained(n, N, g.kc)) o[(long long)compact_of(n, N, g.kc, g.c) * g.hs] = v[m];
+      }
+    }
+  }
+}
+
 template <typename R>
 struct StepBufs {
   using C = typename CplxOf<R>::T;
@@ -622,7 +821,6 @@ __device__ __forceinline__ R stage_dt(const StepBufs<R> &b) {
 
 // Asynchronous global -> shared copies of BYTES (4, 8 or 16); a false
 // predicate zero-fills the destination without reading the source.
-__device__ __forceinline__ unsigned smem_addr(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
 template <int BYTES>
 __device__ __forceinline__ void cp_async(void *dst_smem, const void *src, bool pred) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;\n" ::"r"(smem_addr(dst_smem)), "l"(src), "n"(BYTES),
@@ -1171,6 +1369,13 @@ struct Launch3 {
   static constexpr int WYI = w_yinv<R, N>(), WYF = w_yfwd<R, N>();
   static constexpr size_t SM_L = col_smem(N, WL, sizeof(C), 0);
   static constexpr size_t SM_YI = col_smem(N, WYI, sizeof(C), 0), SM_YF = col_smem(N, WYF, sizeof(C), 0);
+  // y passes with TMA tile loads where the landing tile fits beside the
+  // exchange tile (forward: 128-byte tile rows)
+  static constexpr size_t SM_YFT = col_smem(N, WYF, sizeof(C), (size_t)N * WYF * sizeof(C) + 16);
+  static constexpr bool YF_TMA = WYF * sizeof(C) == 128 && SM_YFT <= kSmemMax;
+  static constexpr size_t SM_YIT = col_smem(
+      N, WYI, sizeof(C), (size_t)tma_boxes(trunc_rows(N)) * tma_box_rows(trunc_rows(N)) * WYI * sizeof(C) + 16);
+  static constexpr bool YI_TMA = (WYI * sizeof(C)) % 16 == 0 && SM_YIT <= kSmemMax;
   // persistent fwd1: exchange tile + RK operand slots (3 comps x 6 per thread
   // for each operand: two for RK2/RK3, one for the other stages; the smaller
   // allocation leaves more of the SM's L1, which fwd1 is sensitive to)
@@ -1195,7 +1400,9 @@ struct Launch3 {
         set_smem(k3_inv1<R, N, WL, true>, SM_L);
         set_smem(k3_inv1<R, N, WL, false>, SM_L);
         set_smem(k3_inv2<R, N, WYI>, SM_YI);
+        if constexpr (YI_TMA) set_smem(k3_inv2_tma<R, N, WYI>, SM_YIT);
         set_smem(k3_fwd2<R, N, WYF>, SM_YF);
+        if constexpr (YF_TMA) set_smem(k3_fwd2_tma<R, N, WYF>, SM_YFT);
         if constexpr (!XW) set_smem(k3_xpass<R, N, L>, SM_XP);
         set_smem(k_xfwd_real<R, N, L>, SM_X);
         set_smem(k_xinv_real<R, N, L>, SM_X);
@@ -1218,6 +1425,13 @@ struct Launch3 {
       }
       case OP_INV2: {
         const int nz = a.nz > 0 ? a.nz : N;
+        if constexpr (YI_TMA) {
+          if (a.tmap_zb != nullptr) {
+            k3_inv2_tma<R, N, WYI><<<dim3(g.hs / WYI, nz), T * WYI, SM_YIT, s>>>(
+                g, a.nf, a.z0, *reinterpret_cast<const CUtensorMap *>(a.tmap_zb), (C *)a.yb, tw, a.err);
+            break;
+          }
+        }
         k3_inv2<R, N, WYI><<<dim3(g.hs / WYI, nz), T * WYI, SM_YI, s>>>(g, a.nf, a.z0, (const C *)a.zb, (C *)a.yb, tw);
         break;
       }
@@ -1234,6 +1448,13 @@ struct Launch3 {
         break;
       case OP_FWD2: {
         const int nz = a.nz > 0 ? a.nz : N;
+        if constexpr (YF_TMA) {
+          if (a.tmap_yb != nullptr) {
+            k3_fwd2_tma<R, N, WYF><<<dim3(g.hs / WYF, nz), T * WYF, SM_YFT, s>>>(
+                g, a.nf, a.z0, *reinterpret_cast<const CUtensorMap *>(a.tmap_yb), (C *)a.zb, tw, a.err);
+            break;
+          }
+        }
         k3_fwd2<R, N, WYF><<<dim3(g.hs / WYF, nz), T * WYF, SM_YF, s>>>(g, a.nf, a.z0, (const C *)a.yb, (C *)a.zb, tw);
         break;
       }
