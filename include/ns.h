@@ -132,6 +132,14 @@ int ns_set_scheme(ns_state *s, int order);
  * Synchronises. */
 int ns_set_cfl(ns_state *s, double cfl);
 
+/* Hyper-viscosity beside nu ("nu_4", "nu_8" of FluidSim's viscosity
+ * parameters): the linear operator becomes -(nu |k|^2 + nu4 |k|^4 + nu8 |k|^8),
+ * integrated exactly by the integrating factor (which no longer factors over
+ * the axes, so E and E2 come from |k|^2-indexed tables).  nu4 = nu8 = 0
+ * returns to plain viscosity.  NS_EINVAL for negative or non-finite values,
+ * NS_EUNSUPPORTED together with CFL stepping.  Synchronises. */
+int ns_set_hyperviscosity(ns_state *s, double nu4, double nu8);
+
 /* Simulated time (sum of the steps taken since ns_init) and the dt of the
  * last step (the constant dt without CFL).  Synchronises when CFL is on. */
 int ns_get_time(ns_state *s, double *t, double *dt);
@@ -149,13 +157,15 @@ int ns_eval_rhs(ns_state *s, double *rhs_host);
 int ns_diagnostics(ns_state *s, double *energy, double *enstrophy);
 
 /* Energy and enstrophy budget terms of the state ("sim.output.spatial_means":
- * forcing power and dissipation), FP64, w as above:
+ * forcing power and dissipation), FP64, w as above, with the damping rate of
+ * a mode d(k) = nu |k|^2 + nu4 |k|^4 + nu8 |k|^8 (nu4 = nu8 = 0 unless set by
+ * ns_set_hyperviscosity):
  *   3D: out[0] P_E = sum w Re(u_hat* . F_hat)         (energy injection),
- *       out[1] D_E = nu sum w |k|^2 |u_hat|^2         (energy dissipation),
+ *       out[1] D_E = sum w d(k) |u_hat|^2             (energy dissipation),
  *       out[2] P_Z = sum w |k|^2 Re(u_hat* . F_hat)   (enstrophy injection),
- *       out[3] D_Z = nu sum w |k|^4 |u_hat|^2         (enstrophy dissipation);
- *   2D: out[0] P_E = sum w Re(w_hat* F_hat) / |k|^2,  out[1] D_E = nu sum w |w_hat|^2,
- *       out[2] P_Z = sum w Re(w_hat* F_hat),          out[3] D_Z = nu sum w |k|^2 |w_hat|^2.
+ *       out[3] D_Z = sum w |k|^2 d(k) |u_hat|^2       (enstrophy dissipation);
+ *   2D: out[0] P_E = sum w Re(w_hat* F_hat) / |k|^2,  out[1] D_E = sum w d(k) |w_hat|^2 / |k|^2,
+ *       out[2] P_Z = sum w Re(w_hat* F_hat),          out[3] D_Z = sum w d(k) |w_hat|^2.
  * F_hat is the stored (dealiased, projected) forcing; zero without one.  The
  * Galerkin system gives dE/dt = P_E - D_E, and in 2D dOmega/dt = P_Z - D_Z.
  * Synchronises; NS_ENONFINITE (values still written) on NaN or Inf. */

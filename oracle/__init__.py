@@ -57,6 +57,7 @@ def _load():
             "orc_rhs": ([I, I, P, P, P], I),
             "orc_step": ([I, I, D, D, I, P, P], I),
             "orc_step_rk2": ([I, I, D, D, I, P, P], I),
+            "orc_step_visc": ([I, I, D, D, D, D, I, I, P, P], I),
             "orc_velocity": ([I, I, P, P], I),
             "orc_step_cfl": ([I, I, D, D, D, I, I, P, P, P], I),
             "orc_diagnostics": ([I, I, P, ctypes.POINTER(D), ctypes.POINTER(D)], I),
@@ -148,13 +149,14 @@ def rhs(dim: int, n: int, state: np.ndarray, forcing: np.ndarray | None = None) 
 
 
 def step(dim: int, n: int, nu: float, dt: float, nsteps: int, state: np.ndarray,
-         forcing: np.ndarray | None = None, order: int = 4) -> np.ndarray:
+         forcing: np.ndarray | None = None, order: int = 4, nu4: float = 0.0, nu8: float = 0.0) -> np.ndarray:
     """Return the state after ``nsteps`` Lawson IF-RK steps of the given order
-    (4, or 2 = the midpoint form) (input untouched)."""
+    (4, or 2 = the midpoint form) with the damping rate
+    nu |k|^2 + nu4 |k|^4 + nu8 |k|^8 (input untouched)."""
     s = np.ascontiguousarray(state, dtype=np.complex128).reshape(state_shape(dim, n)).copy()
     f = None if forcing is None else np.ascontiguousarray(forcing, dtype=np.complex128).reshape(s.shape)
-    fn = {4: _load().orc_step, 2: _load().orc_step_rk2}[order]
-    _check(fn(dim, n, float(nu), float(dt), int(nsteps), None if f is None else _ptr(f), _ptr(s)), "step")
+    _check(_load().orc_step_visc(dim, n, float(nu), float(nu4), float(nu8), float(dt), int(order), int(nsteps),
+                                 None if f is None else _ptr(f), _ptr(s)), "step")
     return s
 
 
@@ -209,29 +211,32 @@ def _wavevectors(dim: int, n: int):
     return np.arange(h)[None, None, :], kfull[None, :, None], kfull[:, None, None]
 
 
-def budget(dim: int, n: int, nu: float, state: np.ndarray, forcing: np.ndarray | None = None):
+def budget(dim: int, n: int, nu: float, state: np.ndarray, forcing: np.ndarray | None = None,
+           nu4: float = 0.0, nu8: float = 0.0):
     """Energy and enstrophy budget terms (P_E, D_E, P_Z, D_Z) of a truncated
     spectral state: forcing power and dissipation, the "spatial means" of the
     paper's output list besides energy and enstrophy.  With the mode weights
-    w = 1 on kx = 0 and 2 elsewhere (the half spectrum stands for the full one):
-    3D velocity:  P_E = sum w Re(u* . F), D_E = nu sum w k^2 |u|^2,
-                  P_Z = sum w k^2 Re(u* . F), D_Z = nu sum w k^4 |u|^2;
-    2D vorticity: P_E = sum w Re(w* F) / k^2, D_E = nu sum w |w|^2,
-                  P_Z = sum w Re(w* F), D_Z = nu sum w k^2 |w|^2  (k = 0 excluded).
+    w = 1 on kx = 0 and 2 elsewhere (the half spectrum stands for the full one)
+    and the damping rate d = nu k^2 + nu4 k^4 + nu8 k^8 of a mode:
+    3D velocity:  P_E = sum w Re(u* . F), D_E = sum w d |u|^2,
+                  P_Z = sum w k^2 Re(u* . F), D_Z = sum w k^2 d |u|^2;
+    2D vorticity: P_E = sum w Re(w* F) / k^2, D_E = sum w d |w|^2 / k^2,
+                  P_Z = sum w Re(w* F), D_Z = sum w d |w|^2  (k = 0 excluded).
     Plain numpy in float64 (no FFT involved)."""
     s = np.ascontiguousarray(state, dtype=np.complex128).reshape(state_shape(dim, n))
     f = np.zeros_like(s) if forcing is None else np.ascontiguousarray(forcing, dtype=np.complex128).reshape(s.shape)
     kx, ky, kz = _wavevectors(dim, n)
     k2 = (kx * kx + ky * ky + kz * kz).astype(np.float64)
     w = np.where(kx == 0, 1.0, 2.0) * np.ones_like(k2)
+    d = nu * k2 + nu4 * k2 ** 2 + nu8 * k2 ** 4
     if dim == 3:
         m2 = np.sum(np.abs(s) ** 2, axis=0)
         pf = np.sum((np.conj(s) * f).real, axis=0)
-        return (float(np.sum(w * pf)), float(nu * np.sum(w * k2 * m2)),
-                float(np.sum(w * k2 * pf)), float(nu * np.sum(w * k2 * k2 * m2)))
+        return (float(np.sum(w * pf)), float(np.sum(w * d * m2)),
+                float(np.sum(w * k2 * pf)), float(np.sum(w * k2 * d * m2)))
     m2 = np.abs(s) ** 2
     pf = (np.conj(s) * f).real
     nz = k2 > 0
     inv = np.where(nz, 1.0 / np.where(nz, k2, 1.0), 0.0)
-    return (float(np.sum(w * pf * inv)), float(nu * np.sum(w * m2 * nz)),
-            float(np.sum(w * pf * nz)), float(nu * np.sum(w * k2 * m2)))
+    return (float(np.sum(w * pf * inv)), float(np.sum(w * d * inv * m2)),
+            float(np.sum(w * pf * nz)), float(np.sum(w * d * m2)))

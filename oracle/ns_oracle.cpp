@@ -398,16 +398,23 @@ int orc_rhs(int dim, int n, const double *state, const double *forcing, double *
 //   k2 = N(a);           b = E2 u + dt/2 k2
 //   k3 = N(b);           c = E u + dt E2 k3
 //   k4 = N(c);           u <- E u + dt/6 (E k1 + 2 E2 k2 + 2 E2 k3 + k4)
-int orc_step(int dim, int n, double nu, double dt, int nsteps, const double *forcing, double *state) {
-  if ((dim != 2 && dim != 3) || !is_pow2(n) || n < 4 || nsteps < 0 || nu < 0 || !(dt > 0)) return -1;
+// nsteps Lawson IF-RK steps of the given order (4 or 2) in place with the
+// damping rate nu |k|^2 + nu4 |k|^4 + nu8 |k|^8 of each mode (hyper-viscosity
+// "nu_4", "nu_8" beside "nu_2"): E = exp(-rate dt), E2 = exp(-rate dt / 2).
+int orc_step_visc(int dim, int n, double nu, double nu4, double nu8, double dt, int order, int nsteps,
+                  const double *forcing, double *state) {
+  if ((dim != 2 && dim != 3) || !is_pow2(n) || n < 4 || nsteps < 0 || nu < 0 || nu4 < 0 || nu8 < 0 || !(dt > 0) ||
+      (order != 2 && order != 4))
+    return -1;
   Grid g(dim, n);
   const long nt = (long)g.ntrunc();
   const long tot = nt * g.ncomp();
   std::vector<double> E(nt), E2(nt);
   for (long i = 0; i < nt; ++i) {
-    const double k2 = k2_trunc(g, i);
-    E[i] = std::exp(-nu * k2 * dt);
-    E2[i] = std::exp(-nu * k2 * dt * 0.5);
+    const double k2 = k2_trunc(g, i), k4 = k2 * k2;
+    const double rate = nu * k2 + nu4 * k4 + nu8 * k4 * k4;
+    E[i] = std::exp(-rate * dt);
+    E2[i] = std::exp(-rate * dt * 0.5);
   }
   cd *u = reinterpret_cast<cd *>(state);
   const cd *F = reinterpret_cast<const cd *>(forcing);
@@ -416,6 +423,10 @@ int orc_step(int dim, int n, double nu, double dt, int nsteps, const double *for
     rhs(g, u, F, k1.data());
     for (long j = 0; j < tot; ++j) s[j] = E2[j % nt] * (u[j] + 0.5 * dt * k1[j]);
     rhs(g, s.data(), F, k2.data());
+    if (order == 2) {
+      for (long j = 0; j < tot; ++j) u[j] = E[j % nt] * u[j] + dt * E2[j % nt] * k2[j];
+      continue;
+    }
     for (long j = 0; j < tot; ++j) s[j] = E2[j % nt] * u[j] + 0.5 * dt * k2[j];
     rhs(g, s.data(), F, k3.data());
     for (long j = 0; j < tot; ++j) s[j] = E[j % nt] * u[j] + dt * E2[j % nt] * k3[j];
@@ -428,31 +439,16 @@ int orc_step(int dim, int n, double nu, double dt, int nsteps, const double *for
   return 0;
 }
 
+int orc_step(int dim, int n, double nu, double dt, int nsteps, const double *forcing, double *state) {
+  return orc_step_visc(dim, n, nu, 0.0, 0.0, dt, 4, nsteps, forcing, state);
+}
+
 // nsteps Lawson IF-RK2 (midpoint) steps in place, the order-2 member of the
 // paper's Runge-Kutta time stepping with the same integrating factor:
 //   k1 = N(u);           a = E2 (u + dt/2 k1)
 //   k2 = N(a);           u <- E u + dt E2 k2
 int orc_step_rk2(int dim, int n, double nu, double dt, int nsteps, const double *forcing, double *state) {
-  if ((dim != 2 && dim != 3) || !is_pow2(n) || n < 4 || nsteps < 0 || nu < 0 || !(dt > 0)) return -1;
-  Grid g(dim, n);
-  const long nt = (long)g.ntrunc();
-  const long tot = nt * g.ncomp();
-  std::vector<double> E(nt), E2(nt);
-  for (long i = 0; i < nt; ++i) {
-    const double k2 = k2_trunc(g, i);
-    E[i] = std::exp(-nu * k2 * dt);
-    E2[i] = std::exp(-nu * k2 * dt * 0.5);
-  }
-  cd *u = reinterpret_cast<cd *>(state);
-  const cd *F = reinterpret_cast<const cd *>(forcing);
-  std::vector<cd> k1(tot), k2(tot), s(tot);
-  for (int step = 0; step < nsteps; ++step) {
-    rhs(g, u, F, k1.data());
-    for (long j = 0; j < tot; ++j) s[j] = E2[j % nt] * (u[j] + 0.5 * dt * k1[j]);
-    rhs(g, s.data(), F, k2.data());
-    for (long j = 0; j < tot; ++j) u[j] = E[j % nt] * u[j] + dt * E2[j % nt] * k2[j];
-  }
-  return 0;
+  return orc_step_visc(dim, n, nu, 0.0, 0.0, dt, 2, nsteps, forcing, state);
 }
 
 // Physical velocity of a state: 3D the three components (the state itself),

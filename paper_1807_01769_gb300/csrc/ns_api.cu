@@ -80,6 +80,9 @@ struct ns_state {
   double cfl = 0, t = 0;
   unsigned long long *umax = nullptr;
   double *ctl = nullptr;
+  // hyper-viscosity nu4 k^4 + nu8 k^8 beside nu k^2: E, E2 indexed by |k|^2
+  double nu4 = 0, nu8 = 0;
+  void *ek2 = nullptr, *ek22 = nullptr;
   // TMA: tensor map over yb (3D, 128-byte forward y-pass tile rows), device error word
   alignas(128) unsigned char tmap_yb[128];
   alignas(128) unsigned char tmap_zb[128];
@@ -156,6 +159,9 @@ Args base_args(ns_state *s) {
   a.dt = s->dt;
   a.dtp = s->cfl > 0 ? s->ctl : nullptr;
   a.tmap_yb = s->has_tmap ? s->tmap_yb : nullptr;
+  const bool hyper = s->nu4 > 0 || s->nu8 > 0;
+  a.ek2 = hyper ? s->ek2 : nullptr;
+  a.ek22 = hyper ? s->ek22 : nullptr;
   a.tmap_zb = s->has_tmap_zb ? s->tmap_zb : nullptr;
   a.err = s->derr;
   a.nsm = s->nsm;
@@ -333,7 +339,7 @@ int phys_to_spec(ns_state *s, const double *host, void *dst) {
 
 void free_all(ns_state *s) {
   if (s->graph) cudaGraphExecDestroy(s->graph);
-  void *ptrs[] = {s->tw, s->ef, s->ef2, s->u, s->acc, s->F, s->zb, s->yb, s->staging, s->diag, s->umax, s->ctl, s->derr};
+  void *ptrs[] = {s->tw, s->ef, s->ef2, s->u, s->acc, s->F, s->zb, s->yb, s->staging, s->diag, s->umax, s->ctl, s->derr, s->ek2, s->ek22};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   if (s->own) cudaStreamDestroy(s->own);
@@ -386,6 +392,24 @@ void fill_tables(const ns_state *s, std::vector<unsigned char> &tw, std::vector<
     e[k] = (R)std::exp(-s->nu * (double)k * k * s->dt);
     e2[k] = (R)std::exp(-s->nu * (double)k * k * s->dt * 0.5);
   }
+}
+
+// |k|^2-indexed factor tables of a hyper-viscous state: exp(-(nu k^2 + nu4 k^4 + nu8 k^8) dt), dt/2.
+template <typename R>
+int upload_k2_tables(ns_state *s) {
+  const long long q_max = (long long)s->grid.dim * s->g.kc * s->g.kc;
+  std::vector<R> e(q_max + 1), e2(q_max + 1);
+  for (long long q = 0; q <= q_max; ++q) {
+    const double k2 = (double)q, k4 = k2 * k2, rate = s->nu * k2 + s->nu4 * k4 + s->nu8 * k4 * k4;
+    e[q] = (R)std::exp(-rate * s->dt);
+    e2[q] = (R)std::exp(-rate * s->dt * 0.5);
+  }
+  const size_t bytes = sizeof(R) * (size_t)(q_max + 1);
+  int rc;
+  if (!s->ek2 && ((rc = dmalloc(s, &s->ek2, bytes)) || (rc = dmalloc(s, &s->ek22, bytes)))) return rc;
+  NS_CK(s, cudaMemcpy(s->ek2, e.data(), bytes, cudaMemcpyHostToDevice));
+  NS_CK(s, cudaMemcpy(s->ek22, e2.data(), bytes, cudaMemcpyHostToDevice));
+  return NS_OK;
 }
 
 // Constant-dt factor tables refilled from the host (leaving CFL stepping).
@@ -683,6 +707,8 @@ int ns_set_scheme(ns_state *s, int order) {
 int ns_set_cfl(ns_state *s, double cfl) {
   if (!s) return NS_EINVAL;
   if (!(cfl >= 0) || !std::isfinite(cfl)) return fail(s, NS_EINVAL, "ns_set_cfl: cfl must be finite and >= 0");
+  if (cfl > 0 && (s->nu4 > 0 || s->nu8 > 0))
+    return fail(s, NS_EUNSUPPORTED, "ns_set_cfl: CFL stepping with hyper-viscosity is not supported");
   DevGuard dg(s->dev);
   NS_CK(s, cudaStreamSynchronize(s->stream));
   int rc;
@@ -702,6 +728,30 @@ int ns_set_cfl(ns_state *s, double cfl) {
     if (rc) return rc;
   }
   s->cfl = cfl;
+  if (s->graph) {
+    cudaGraphExecDestroy(s->graph);
+    s->graph = nullptr;
+  }
+  return NS_OK;
+}
+
+int ns_set_hyperviscosity(ns_state *s, double nu4, double nu8) {
+  if (!s) return NS_EINVAL;
+  if (!(nu4 >= 0) || !(nu8 >= 0) || !std::isfinite(nu4) || !std::isfinite(nu8))
+    return fail(s, NS_EINVAL, "ns_set_hyperviscosity: coefficients must be finite and >= 0");
+  if ((nu4 > 0 || nu8 > 0) && s->cfl > 0)
+    return fail(s, NS_EUNSUPPORTED, "ns_set_hyperviscosity: not supported with CFL stepping");
+  DevGuard dg(s->dev);
+  NS_CK(s, cudaStreamSynchronize(s->stream));
+  s->nu4 = nu4;
+  s->nu8 = nu8;
+  if (nu4 > 0 || nu8 > 0) {
+    const int rc = s->prec == NS_FP32 ? upload_k2_tables<float>(s) : upload_k2_tables<double>(s);
+    if (rc) {
+      s->nu4 = s->nu8 = 0;
+      return rc;
+    }
+  }
   if (s->graph) {
     cudaGraphExecDestroy(s->graph);
     s->graph = nullptr;
@@ -766,7 +816,7 @@ int ns_budget(ns_state *s, double *out) {
   DevGuard dg(s->dev);
   double *scratch = (double *)s->diag;
   double *dout = scratch + s->diag_scratch;
-  int e = nsk::budget(s->prec, s->g, s->u, s->F, s->nu, scratch, dout, s->stream);
+  int e = nsk::budget(s->prec, s->g, s->u, s->F, s->nu, s->nu4, s->nu8, scratch, dout, s->stream);
   if (e) return fail(s, NS_ECUDA, "budget launch failed: %s", cudaGetErrorString((cudaError_t)e));
   NS_CK(s, cudaMemcpyAsync(out, dout, sizeof(double) * 4, cudaMemcpyDeviceToHost, s->stream));
   NS_CK(s, cudaStreamSynchronize(s->stream));

@@ -250,15 +250,17 @@ int cfl_update(int prec, const Geo &g, double nu, unsigned long long *umax, doub
   return (int)cudaGetLastError();
 }
 
-// Energy and enstrophy budget terms, per block into scratch[b][0..3]:
-//   3D (velocity u, forcing F): P_E = sum w Re(u* . F),      D_E = nu sum w k^2 |u|^2,
-//                               P_Z = sum w k^2 Re(u* . F),  D_Z = nu sum w k^4 |u|^2;
-//   2D (vorticity w, forcing F): P_E = sum w Re(w* F) / k^2,  D_E = nu sum w |w|^2,
-//                               P_Z = sum w Re(w* F),         D_Z = nu sum w k^2 |w|^2.
+// Energy and enstrophy budget terms, per block into scratch[b][0..3], with
+// the damping rate of a mode d(k) = nu k^2 + nu4 k^4 + nu8 k^8:
+//   3D (velocity u, forcing F): P_E = sum w Re(u* . F),      D_E = sum w d |u|^2,
+//                               P_Z = sum w k^2 Re(u* . F),  D_Z = sum w k^2 d |u|^2;
+//   2D (vorticity w, forcing F): P_E = sum w Re(w* F) / k^2,  D_E = sum w d |w|^2 / k^2,
+//                               P_Z = sum w Re(w* F),         D_Z = sum w d |w|^2.
 // Same row ownership and fixed reduction order as k_diag.
 template <typename C>
 __global__ void __launch_bounds__(32 * kDiagWarps) k_budget(Geo g, const C *__restrict__ u, const C *__restrict__ F,
-                                                            double nu, int rows_per_block, double *__restrict__ scratch) {
+                                                            double nu, double nu4, double nu8, int rows_per_block,
+                                                            double *__restrict__ scratch) {
   __shared__ double wsum[kDiagWarps][4];
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   const long long nrows = diag_rows(g);
@@ -284,16 +286,17 @@ __global__ void __launch_bounds__(32 * kDiagWarps) k_budget(Geo g, const C *__re
           pf += (double)a.x * f.x + (double)a.y * f.y;
         }
       }
+      const double k4 = k2 * k2, d = nu * k2 + nu4 * k4 + nu8 * k4 * k4;
       if (g.dim == 3) {
         acc[0] += w * pf;
-        acc[1] += w * nu * k2 * m2;
+        acc[1] += w * d * m2;
         acc[2] += w * k2 * pf;
-        acc[3] += w * nu * k2 * k2 * m2;
+        acc[3] += w * k2 * d * m2;
       } else if (k2 > 0) {
         acc[0] += w * pf / k2;
-        acc[1] += w * nu * m2;
+        acc[1] += w * (d / k2) * m2;
         acc[2] += w * pf;
-        acc[3] += w * nu * k2 * m2;
+        acc[3] += w * d * m2;
       }
     }
   }
@@ -311,16 +314,17 @@ __global__ void __launch_bounds__(32 * kDiagWarps) k_budget(Geo g, const C *__re
   }
 }
 
-int budget(int prec, const Geo &g, const void *u, const void *F, double nu, double *scratch, double *out,
-           cudaStream_t s) {
+int budget(int prec, const Geo &g, const void *u, const void *F, double nu, double nu4, double nu8, double *scratch,
+           double *out, cudaStream_t s) {
   const long long nb = diag_blocks(g);
   const long long rows = diag_rows(g);
   const int rpb = (int)((rows + nb - 1) / nb);
   if (prec == 1)
-    k_budget<float2><<<(unsigned)nb, 32 * kDiagWarps, 0, s>>>(g, (const float2 *)u, (const float2 *)F, nu, rpb, scratch);
+    k_budget<float2><<<(unsigned)nb, 32 * kDiagWarps, 0, s>>>(g, (const float2 *)u, (const float2 *)F, nu, nu4, nu8, rpb,
+                                                              scratch);
   else
-    k_budget<double2><<<(unsigned)nb, 32 * kDiagWarps, 0, s>>>(g, (const double2 *)u, (const double2 *)F, nu, rpb,
-                                                               scratch);
+    k_budget<double2><<<(unsigned)nb, 32 * kDiagWarps, 0, s>>>(g, (const double2 *)u, (const double2 *)F, nu, nu4,
+                                                               nu8, rpb, scratch);
   diag_final(scratch, nb, 4, out, s);
   return (int)cudaGetLastError();
 }

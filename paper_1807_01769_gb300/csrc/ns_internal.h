@@ -63,6 +63,7 @@ struct Args {
   const void *tmap_yb;       // OP_FWD2: 2D tensor map over yb for TMA loads (nullable: plain loads)
   const void *tmap_zb;       // OP_INV2: 3D tensor map over zb for TMA loads (nullable: plain loads)
   int *err;                  // device error word: a bounded wait that gave up writes a nonzero code
+  const void *ek2, *ek22;    // OP_FWD1: E, E2 indexed by |k|^2 (hyper-viscosity), nullable
   unsigned long long *umax;  // OP_XPASS: [dim][kUmaxSlots] maxima of |u_i| as double bits (nullable)
   int nsm;     // streaming multiprocessors of the device (persistent grids)
   int z0, nz;  // 3D OP_INV2 / OP_XPASS / OP_FWD2: planes z0 .. z0+nz-1 (nz = 0: all)
@@ -112,8 +113,9 @@ __host__ __device__ constexpr int y_inv_columns(int csize, int n) {
 }
 __host__ __device__ constexpr int y_fwd_columns(int csize, int n) { return y_tile_cap(1024, csize, n); }
 // Budget terms {P_E, D_E, P_Z, D_Z} (forcing power and dissipation of energy
-// and enstrophy) into out[0..3]; scratch holds diag_blocks(g) * 4 doubles.
-int budget(int prec, const Geo &g, const void *u, const void *F, double nu, double *scratch, double *out,
-           cudaStream_t s);
+// and enstrophy, the latter with the damping rate nu k^2 + nu4 k^4 + nu8 k^8)
+// into out[0..3]; scratch holds diag_blocks(g) * 4 doubles.
+int budget(int prec, const Geo &g, const void *u, const void *F, double nu, double nu4, double nu8, double *scratch,
+           double *out, cudaStream_t s);
 
 }  // namespace nsk

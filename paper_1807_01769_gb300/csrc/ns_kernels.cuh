@@ -805,6 +805,9 @@ struct StepBufs {
   C *dst;
   R dt;
   const double *dtp;  // time step in device memory (CFL stepping), nullable
+  // hyper-viscous states: E, E2 indexed by |k|^2 (the operator does not
+  // factor over the axes); null = the per-axis tables ef, ef2
+  const R *ek2, *ek22;
 };
 
 // The time step of a stage update: read from device memory at each use when
@@ -1036,7 +1039,14 @@ __global__ void __launch_bounds__((N / 8) * W) k3_fwd1(Geo g, StepBufs<R> b) {
       }
       C nv[3] = {ax, ay, az};
       C out[3];
-      const R e = exy * axis_factor(b.ef, kz), e2 = exy2 * axis_factor(b.ef2, kz);
+      R e, e2;
+      if (b.ek2 != nullptr) {
+        e = __ldg(b.ek2 + k2);
+        e2 = __ldg(b.ek22 + k2);
+      } else {
+        e = exy * axis_factor(b.ef, kz);
+        e2 = exy2 * axis_factor(b.ef2, kz);
+      }
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
         const int slot = (c * 6 + rk_slot(m)) * NT + threadIdx.x;
@@ -1259,7 +1269,14 @@ __device__ __forceinline__ void fwd1_2d_unit(const Geo &g, const StepBufs<R> &b,
     C nv = k2 == 0 ? czero<C>() : cscale(s[m], scale);
     const long long idx = (long long)compact_of(n, N, g.kc, g.c) * g.hs + kx;
     if (MODE != MODE_PROJ && b.F != nullptr) nv = cadd(nv, b.F[idx]);
-    const R e = axis_factor(b.ef, kx) * axis_factor(b.ef, ky), e2 = axis_factor(b.ef2, kx) * axis_factor(b.ef2, ky);
+    R e, e2;
+    if (b.ek2 != nullptr) {
+      e = __ldg(b.ek2 + k2);
+      e2 = __ldg(b.ek22 + k2);
+    } else {
+      e = axis_factor(b.ef, kx) * axis_factor(b.ef, ky);
+      e2 = axis_factor(b.ef2, kx) * axis_factor(b.ef2, ky);
+    }
     s[m] = rk_update<MODE>(nv, idx, e, e2, b);
   }
   if (INV) {
@@ -1356,6 +1373,8 @@ inline StepBufs<R> step_bufs(const Args &a) {
   b.dst = (C *)a.dst;
   b.dt = (R)a.dt;
   b.dtp = a.dtp;
+  b.ek2 = (const R *)a.ek2;
+  b.ek22 = (const R *)a.ek22;
   return b;
 }
 

@@ -76,6 +76,7 @@ SIGNATURES = {
     "ns_budget": ([_P, _P], _I),
     "ns_set_scheme": ([_P, _I], _I),
     "ns_set_cfl": ([_P, _D], _I),
+    "ns_set_hyperviscosity": ([_P, _D, _D], _I),
     "ns_get_time": ([_P, _PD, _PD], _I),
     "ns_state_to_phys_device": ([_P, _P], _I),
     "ns_set_forcing_phys_device": ([_P, _P], _I),
@@ -243,6 +244,10 @@ class Solver:
     def set_cfl(self, cfl: float) -> None:
         """CFL-adaptive dt (capped by the initial dt); 0 = constant dt."""
         _check(lib.ns_set_cfl(self.state, float(cfl)), self.state)
+
+    def set_hyperviscosity(self, nu4: float, nu8: float = 0.0) -> None:
+        """Add -(nu4 |k|^4 + nu8 |k|^8) to the linear operator (0, 0 removes it)."""
+        _check(lib.ns_set_hyperviscosity(self.state, float(nu4), float(nu8)), self.state)
 
     def time(self):
         """(simulated time, dt of the last step)."""

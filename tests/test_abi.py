@@ -101,6 +101,7 @@ def test_new_entry_points_check_arguments_before_any_device_call(ns):
     d = ns.ctypes.c_double()
     assert L.ns_set_scheme(None, 2) == E
     assert L.ns_set_cfl(None, 0.5) == E
+    assert L.ns_set_hyperviscosity(None, 1e-5, 0.0) == E
     assert L.ns_get_time(None, ns.ctypes.byref(d), ns.ctypes.byref(d)) == E
     assert L.ns_budget(None, None) == E
     assert L.ns_state_to_phys_device(None, None) == E

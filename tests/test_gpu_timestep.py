@@ -198,3 +198,51 @@ def test_budget_without_viscosity_has_no_dissipation(ns, orc):
     ref = orc.budget(2, n, 0.0, u, orc.phys_to_state(2, n, f_phys))
     assert de == 0.0 and dz == 0.0
     assert abs(pe - ref[0]) < 1e-12 * abs(ref[0]) and abs(pz - ref[2]) < 1e-12 * abs(ref[2])
+
+
+@pytest.mark.parametrize("dim,n,prec,order", [(2, 64, FP64, 4), (2, 128, FP32, 4), (2, 64, FP64, 2),
+                                              (3, 32, FP64, 4), (3, 64, FP32, 4), (3, 32, FP32, 2)])
+def test_hyperviscosity_matches_oracle(ns, orc, dim, n, prec, order):
+    nu, dt, steps = 2e-3, 2e-3, 10
+    nu4, nu8 = (2e-5, 1e-11) if dim == 2 else (1e-3, 1e-9)  # visible on each initial field
+    u0 = ic(dim, n, seed=11)
+    ref = orc.step(dim, n, nu, dt, steps, u0, order=order, nu4=nu4, nu8=nu8)
+    plain = orc.step(dim, n, nu, dt, steps, u0, order=order)
+    assert rel_l2(ref, plain) > 1e3 * TOL[FP32]  # the hyper terms are visible
+    with ns.Solver(dim, n, prec, nu=nu, dt=dt) as s:
+        s.set_scheme(order)
+        s.set_hyperviscosity(nu4, nu8)
+        s.set_state_spectral(u0)
+        s.step(steps)
+        got = s.get_state_spectral()
+        s.set_hyperviscosity(0.0, 0.0)  # back to plain viscosity
+        s.set_state_spectral(u0)
+        s.step(steps)
+        got_plain = s.get_state_spectral()
+    assert rel_l2(got, ref) < TOL[prec]
+    assert rel_l2(got_plain, plain) < TOL[prec]
+
+
+def test_hyperviscosity_budget_and_exclusions(ns, orc):
+    n, nu, nu4, nu8 = 64, 1e-3, 1e-5, 1e-12
+    u = ic(2, n, seed=12)
+    f_phys = inputs.kolmogorov_forcing_2d(n)
+    ref = orc.budget(2, n, nu, u, orc.phys_to_state(2, n, f_phys), nu4=nu4, nu8=nu8)
+    with ns.Solver(2, n, FP64, nu=nu, dt=1e-3, forcing_phys=f_phys) as s:
+        s.set_state_spectral(u)
+        s.set_hyperviscosity(nu4, nu8)
+        got = s.budget()
+        for a, b in zip(got, ref):
+            assert abs(a - b) <= 1e-11 * max(abs(b), 1e-3 * max(abs(r) for r in ref))
+        with pytest.raises(ns.NSError) as ei:
+            s.set_cfl(0.5)
+        assert ei.value.code == ns.NS_EUNSUPPORTED
+        s.set_hyperviscosity(0.0, 0.0)
+        s.set_cfl(0.5)
+        with pytest.raises(ns.NSError) as ei:
+            s.set_hyperviscosity(1e-5, 0.0)
+        assert ei.value.code == ns.NS_EUNSUPPORTED
+        for bad in ((-1e-5, 0.0), (0.0, float("nan"))):
+            with pytest.raises(ns.NSError) as ei:
+                s.set_hyperviscosity(*bad)
+            assert ei.value.code == ns.NS_EINVAL

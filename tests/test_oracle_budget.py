@@ -66,3 +66,17 @@ def test_dissipation_is_twice_nu_enstrophy_and_no_forcing_no_power(orc, dim, n):
     assert pe == 0.0 and pz == 0.0
     assert abs(de - 2 * nu * om) < 1e-12 * de
     assert dz > 0
+
+
+@pytest.mark.parametrize("dim,n", [(2, 32), (3, 16)])
+def test_energy_rate_with_hyperviscosity(orc, dim, n):
+    nu, nu4, nu8, h = 0.01, 1e-3, 1e-7, 1e-4
+    u = inputs.random_vorticity_2d(n, seed=3, k0=3.0) if dim == 2 else inputs.random_velocity_3d(n, seed=3, k0=2.0)
+    f = forcing(orc, dim, n, 11)
+    pe, de, _, _ = orc.budget(dim, n, nu, u, f, nu4=nu4, nu8=nu8)
+    _, de0, _, _ = orc.budget(dim, n, nu, u, f)
+    assert de > 1.2 * de0  # the hyper terms matter at these coefficients
+    v = [orc.diagnostics(dim, n, orc.step(dim, n, nu, h, k, u, forcing=f, nu4=nu4, nu8=nu8) if k else u)[0]
+         for k in range(3)]
+    rate = (-3 * v[0] + 4 * v[1] - v[2]) / (2 * h)
+    assert abs(rate - (pe - de)) < 1e-5 * (abs(pe) + de)

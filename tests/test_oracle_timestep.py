@@ -85,3 +85,30 @@ def test_cfl_rule(orc, order):
         assert abs(dt - min(1.0, 0.4 * (2 * np.pi / 32) / vmax.max())) < 1e-15
         ref = orc.step(2, 32, nu, dt, 1, ref, order=order)
     np.testing.assert_array_equal(got, ref)
+
+
+@pytest.mark.parametrize("order", [2, 4])
+def test_hyperviscosity_exact_decay_of_a_single_2d_mode(orc, order):
+    # one Fourier mode has no nonlinear term in 2D: w(t) = w0 exp(-(nu k^2 + nu4 k^4 + nu8 k^8) t)
+    n, nu, nu4, nu8, dt, steps = 32, 0.01, 2e-4, 1e-8, 0.05, 8
+    kc, c, h = inputs.truncation(n)
+    w0 = np.zeros((c, h), np.complex128)
+    w0[3, 4] = 0.8 + 0.3j  # (ky, kx) = (3, 4), |k|^2 = 25
+    got = orc.step(2, n, nu, dt, steps, w0, order=order, nu4=nu4, nu8=nu8)
+    rate = nu * 25 + nu4 * 25 ** 2 + nu8 * 25 ** 4
+    np.testing.assert_allclose(got, w0 * np.exp(-rate * dt * steps), atol=1e-15)
+
+
+def test_hyperviscosity_exact_decay_of_a_beltrami_field(orc):
+    # ABC flow at |k| = 1: u x w = 0, each mode decays by exp(-(nu + nu4 + nu8) t)
+    n, nu, nu4, nu8, dt, steps = 16, 0.02, 0.03, 0.01, 0.1, 5
+    u0 = orc.phys_to_state(3, n, inputs.abc_flow(n))
+    got = orc.step(3, n, nu, dt, steps, u0, nu4=nu4, nu8=nu8)
+    np.testing.assert_allclose(got, u0 * np.exp(-(nu + nu4 + nu8) * dt * steps), atol=1e-14)
+
+
+def test_zero_hyperviscosity_is_the_plain_step(orc):
+    u0 = inputs.random_vorticity_2d(32, seed=4, k0=3.0)
+    a = orc.step(2, 32, 0.01, 0.02, 5, u0)
+    b = orc.step(2, 32, 0.01, 0.02, 5, u0, nu4=0.0, nu8=0.0)
+    np.testing.assert_array_equal(a, b)
