@@ -684,7 +684,7 @@ __global__ void __launch_bounds__((N / 8) * W) k3_inv2_tma(Geo g, int nf, int z0
   };
   if (threadIdx.x == 0) {
     mbar_init(bar, 1);
-    issue(0);
+    if (nf > 0) issue(0);  // no copy may outlive the block
   }
   int row[8];
   bool live[8];
@@ -758,7 +758,7 @@ __global__ void __launch_bounds__((N / 8) * W) k3_fwd2_tma(Geo g, int nf, int z0
   };
   if (threadIdx.x == 0) {
     mbar_init(bar, 1);
-    issue(0);
+    if (nf > 0) issue(0);  // no copy may outlive the block
   }
   C *out = zb + (long long)z * g.c * g.hs + kx;
   for (int f = 0; f < nf; ++f) {
