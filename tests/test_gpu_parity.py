@@ -323,16 +323,19 @@ def embed(u_small, n_small, n_big):
     return out
 
 
-def test_max_size_3d_1024_two_steps(ns, orc):
+@pytest.mark.parametrize("prec,steps,tol", [(FP32, 2, 1e-6), (FP64, 1, 1e-12)])
+def test_max_size_3d_1024(ns, orc, prec, steps, tol):
+    # the largest 3D grid, both precisions (FP64: about 80 GB and 2 s per step
+    # on the FP64 units; its y passes take 4-column TMA tiles)
     n, nu, dt, m = 1024, 1.0 / 1600, 2e-3, 32
     u_small = orc.phys_to_state(3, m, inputs.taylor_green_3d(m))
-    with ns.Solver(3, n, FP32, nu=nu, dt=dt) as s:
+    with ns.Solver(3, n, prec, nu=nu, dt=dt) as s:
         s.set_state_spectral(embed(u_small, m, n))
-        s.step(2)
+        s.step(steps)
         e, om = s.diagnostics()
-    ref = orc.step(3, m, nu, dt, 2, u_small)
+    ref = orc.step(3, m, nu, dt, steps, u_small)
     re, rom = orc.diagnostics(3, m, ref)
-    assert abs(e - re) < 1e-6 * re and abs(om - rom) < 1e-6 * rom
+    assert abs(e - re) < tol * re and abs(om - rom) < tol * rom
 
 
 def test_plane_chunk_pipeline_is_bitwise_identical(ns, monkeypatch):
