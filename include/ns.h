@@ -61,7 +61,8 @@ extern "C" {
 
 #define NS_FP64 0 /* state, FFTs and products in double precision */
 #define NS_FP32 1 /* state, FFTs and products in single precision; integrating
-                     factors computed in FP64 on the host, reductions in FP64 */
+                     factors computed in FP64 (on the host, or on the device
+                     under CFL stepping) and rounded, reductions in FP64 */
 
 typedef struct ns_state ns_state;
 
@@ -105,7 +106,8 @@ int ns_get_state(ns_state *s, double *phys_host);
 int ns_set_state_spectral(ns_state *s, const double *spec_host);
 int ns_get_state_spectral(ns_state *s, double *spec_host);
 
-/* Advance nsteps >= 0 Lawson IF-RK4 steps.  Asynchronous: returns after the
+/* Advance nsteps >= 0 Lawson IF-RK steps (RK4 unless ns_set_scheme chose
+ * RK2; dt constant unless ns_set_cfl).  Asynchronous: returns after the
  * work is enqueued on the state's stream (a captured CUDA graph per step).
  * While the caller captures that stream into a graph of its own, the step's
  * kernels are enqueued one by one instead, so the caller's graph holds them;
