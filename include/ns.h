@@ -130,12 +130,13 @@ int ns_set_scheme(ns_state *s, int order);
  * ns_init), the maxima taken on the grid points by the first x pass of the
  * step, and integrates with it; dt and the integrating factors are updated on
  * the device inside the step graph, so stepping stays asynchronous.  cfl = 0
- * returns to the constant dt_init.  NS_EINVAL for cfl < 0 or not finite.
- * Synchronises. */
+ * returns to the constant dt_init.  NS_EINVAL for cfl < 0 or not finite,
+ * NS_EUNSUPPORTED for cfl > 0 on a state with hyper-viscosity.  Synchronises. */
 int ns_set_cfl(ns_state *s, double cfl);
 
-/* Hyper-viscosity beside nu ("nu_4", "nu_8" of FluidSim's viscosity
- * parameters): the linear operator becomes -(nu |k|^2 + nu4 |k|^4 + nu8 |k|^8),
+/* Hyper-viscosity beside nu (the paper's viscosity parameter nu_2 is named for
+ * the power of the Laplacian; its higher orders are read as nu4 and nu8): the
+ * linear operator becomes -(nu |k|^2 + nu4 |k|^4 + nu8 |k|^8),
  * integrated exactly by the integrating factor (which no longer factors over
  * the axes, so E and E2 come from |k|^2-indexed tables).  nu4 = nu8 = 0
  * returns to plain viscosity.  NS_EINVAL for negative or non-finite values,
