@@ -139,8 +139,10 @@ class Trained:
 
 def train(X: np.ndarray, T: np.ndarray, steps: int = 3000, batch: int = 16, lr: float = 1e-3, seed: int = 0,
           log=None) -> Trained:
-    """Adam on the mean squared error of normalised targets; minibatches are
-    contiguous slices of a per-epoch host shuffle; cosine learning-rate decay."""
+    """Adam on the mean squared error of normalised targets; the normalised
+    snapshots are uploaded once and each minibatch is gathered on the device,
+    on the stream the CNN runs on, from a per-epoch host permutation; cosine
+    learning-rate decay."""
     import torch
 
     n, h, w = X.shape
@@ -149,17 +151,22 @@ def train(X: np.ndarray, T: np.ndarray, steps: int = 3000, batch: int = 16, lr: 
     net = ns.CNN(h, w, batch, seed=seed)
     losses = []
     per_epoch = n // batch
-    xd = td = None
+    xs = torch.from_numpy(np.ascontiguousarray(X / x_scale, dtype=np.float32)).cuda()
+    ts = torch.from_numpy(np.ascontiguousarray(T / t_scale, dtype=np.float32)).cuda()
+    xb = torch.empty((batch, h, w), dtype=torch.float32, device="cuda")
+    tb = torch.empty_like(xb)
+    perm = None
     for k in range(steps):
         e = k % per_epoch
         if e == 0:
             perm = rng.permutation(n)
-            xd = torch.from_numpy(np.ascontiguousarray(X[perm] / x_scale, dtype=np.float32)).cuda()
-            td = torch.from_numpy(np.ascontiguousarray(T[perm] / t_scale, dtype=np.float32)).cuda()
+        idx = torch.from_numpy(perm[e * batch:(e + 1) * batch]).cuda()
+        torch.index_select(xs, 0, idx, out=xb)
+        torch.index_select(ts, 0, idx, out=tb)
         lr_k = lr * 0.5 * (1.0 + math.cos(math.pi * k / steps))
-        off = e * batch * h * w * 4
         want = (k % 50 == 0) or k == steps - 1
-        loss = net.train_step(xd.data_ptr() + off, td.data_ptr() + off, batch, lr_k, want_loss=want)
+        loss = net.train_step(xb.data_ptr(), tb.data_ptr(), batch, lr_k, want_loss=want,
+                              stream=torch.cuda.current_stream().cuda_stream)
         if want:
             losses.append((k, loss))
             if log and k % 500 == 0:
