@@ -263,6 +263,37 @@ def paper_shapes(target_s=0.25):
             "(sequential for 2D 512^2, Beskow MPI runs otherwise), for context", "runs": out}
 
 
+def tensor_core_bench(u0, e_fp32, om_fp32, steps=20):
+    """The same workload with the x-line transforms on the tensor cores
+    (NS_FP32_TC: split-BF16 GEMMs, FP32 accumulation), beside the FP32 path:
+    step time, x pass per launch (CUDA events), and the energy and enstrophy
+    after the warm-up and timed steps relative to the FP32 run's."""
+    import torch
+    from paper_1807_01769_gb300 import ns
+
+    stream = torch.cuda.Stream()
+    with ns.Solver(3, N_GRID, ns.NS_FP32_TC, nu=NU, dt=DT) as s:
+        s.set_stream(stream.cuda_stream)
+        s.set_state_spectral(u0)
+        s.step(3)
+        s.sync()
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        s.step(steps)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        ms = ev0.elapsed_time(ev1) / steps
+        e, om = s.diagnostics()
+        prof = s.profile_step(3)
+    x = prof.get("xpass", (0.0, 0, 0))
+    return {"precision": "NS_FP32_TC", "steps": steps, "ms_per_step": ms, "value": N_GRID ** 3 / (ms / 1e3) / 1e6,
+            "xpass_ms_per_launch": x[0] / x[1] if x[1] else None,
+            "energy_rel_diff_vs_fp32": abs(e - e_fp32) / e_fp32,
+            "enstrophy_rel_diff_vs_fp32": abs(om - om_fp32) / om_fp32,
+            "note": "not the headline: products carry ~1e-5 relative error (BF16 hi+lo operands)"}
+
+
 def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
@@ -312,7 +343,8 @@ def run_gb300(args):
     cpu = cpu_baseline() if (rank == 0 and ws == 1 and not args.no_cpu_baseline) else None
 
     u0 = inputs.random_velocity_3d(N_GRID, seed=0, k0=4.0, a=2.0, energy=0.5)
-    s = ns.Solver(3, N_GRID, ns.NS_FP32, nu=NU, dt=DT)
+    prec = ns.NS_FP32_TC if args.precision == "tc" else ns.NS_FP32
+    s = ns.Solver(3, N_GRID, prec, nu=NU, dt=DT)
     # a dedicated (non-default) torch stream: the library launches on it and
     # the CUDA events below are recorded on it
     stream = torch.cuda.Stream()
@@ -350,7 +382,7 @@ def run_gb300(args):
     dom_avg_s = dom_ms / dom_n / 1e3
     hbm, peak_kind = peaks()
     achieved = dom_bytes / dom_avg_s / 1e9
-    traffic = traffic_from_profiles(dom)
+    traffic = traffic_from_profiles(dom) if prec == ns.NS_FP32 else None
 
     # end to end through the C ABI with pinned host buffers: upload the initial
     # state, advance one job (JOB_STEPS steps), read back state and spectrum
@@ -377,8 +409,10 @@ def run_gb300(args):
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": max(args.warmup, 3), "ms_per_step": ms_max / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "n": N_GRID, "precision": "fp32", "parallelism": f"replicas x{ws}",
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32" if prec == ns.NS_FP32 else "f32+bf16x3",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n": N_GRID, "precision": args.precision,
+                       "parallelism": f"replicas x{ws}",
                        "l2": L2_NOTE, "job_steps": JOB_STEPS},
             "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm, "peak_kind": peak_kind,
                          "unit": "GB/s", "frac": achieved / hbm, "traffic": traffic,
@@ -404,6 +438,8 @@ def run_gb300(args):
             line["ensemble"] = ensemble_bench()
         if ws == 1 and not args.no_paper_shapes:
             line["paper_shapes"] = paper_shapes()
+        if ws == 1 and prec == ns.NS_FP32 and not args.no_tc:
+            line["tensor_core"] = tensor_core_bench(u0, e, om)
         print(json.dumps(line), flush=True)
     s.close()
     if ws > 1:
@@ -422,6 +458,9 @@ def main():
     ap.add_argument("--no-ensemble", action="store_true", help="skip the batched 2D ensemble measurement")
     ap.add_argument("--no-paper-shapes", action="store_true", help="skip the paper-grid measurements")
     ap.add_argument("--n", type=int, default=512, help="grid size override (profiling of smaller cases only)")
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "tc"],
+                    help="tc: the x-line transforms on the tensor cores (profiling; the headline is fp32)")
+    ap.add_argument("--no-tc", action="store_true", help="skip the tensor-core comparison")
     args = ap.parse_args()
     global N_GRID
     N_GRID = args.n

@@ -63,11 +63,18 @@ extern "C" {
 #define NS_FP32 1 /* state, FFTs and products in single precision; integrating
                      factors computed in FP64 (on the host, or on the device
                      under CFL stepping) and rounded, reductions in FP64 */
+#define NS_FP32_TC 2 /* as NS_FP32, except that the x-line transforms and the
+                        product (3D, n = 64 .. 512) run on the tensor cores:
+                        each transform is a pair of BF16 GEMMs on hi + lo
+                        splits of the FP32 values (three products, FP32
+                        accumulation), about 1e-5 relative error per
+                        transform instead of 1e-7 */
 
 typedef struct ns_state ns_state;
 
 /* Grid description.  dim = 2 or 3; n = points per axis, a power of two with
- * 16 <= n <= 2048 (2D) or 16 <= n <= 1024 (3D); precision = NS_FP64|NS_FP32. */
+ * 16 <= n <= 2048 (2D) or 16 <= n <= 1024 (3D); precision = NS_FP64|NS_FP32, or
+ * NS_FP32_TC for 3D grids with n in {64, 128, 256, 512} (NS_EUNSUPPORTED otherwise). */
 typedef struct {
   int dim;
   int n;

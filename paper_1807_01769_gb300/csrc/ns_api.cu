@@ -24,6 +24,7 @@
 #include "ns.h"
 #include "ns_fft.cuh"
 #include "ns_internal.h"
+#include "ns_tc.h"
 
 using nsk::Args;
 using nsk::Geo;
@@ -50,10 +51,11 @@ struct DevGuard {
 int grid_check(const ns_grid *g) {
   if (!g) return NS_EINVAL;
   if (g->dim != 2 && g->dim != 3) return NS_EINVAL;
-  if (g->precision != NS_FP64 && g->precision != NS_FP32) return NS_EINVAL;
+  if (g->precision != NS_FP64 && g->precision != NS_FP32 && g->precision != NS_FP32_TC) return NS_EINVAL;
   if (!is_pow2(g->n)) return NS_EINVAL;
   const int nmax = g->dim == 3 ? 1024 : 2048;
   if (g->n < 16 || g->n > nmax) return NS_EUNSUPPORTED;
+  if (g->precision == NS_FP32_TC && (g->dim != 3 || !nsk::tc_supported(g->n))) return NS_EUNSUPPORTED;
   return NS_OK;
 }
 
@@ -63,7 +65,10 @@ struct ns_state {
   int dev = 0;
   ns_grid grid{};
   Geo g{};
-  int prec = 0, ncomp = 1, nbins = 0, nsm = 1;
+  int prec = 0, ncomp = 1, nbins = 0, nsm = 1;  // prec: NS_FP64 or NS_FP32 (storage and all other passes)
+  bool tc = false;      // NS_FP32_TC: the x pass on the tensor cores
+  void *tcm = nullptr;  // its DFT matrices
+  alignas(128) unsigned char tmap_xtc[128];  // its TMA boxes over yb (one tile of x lines)
   size_t cs = 8;  // bytes per complex element
   double nu = 0, dt = 0;
   cudaStream_t own = nullptr, stream = nullptr, cap = nullptr;
@@ -135,7 +140,8 @@ int dispatch(ns_state *s, int op, const Args &a, cudaStream_t st) {
   if (op == nsk::OP_CFL)
     rc = nsk::cfl_update(s->prec, s->g, s->nu, s->umax, s->ctl, s->ef, s->ef2, st);
   else if (s->grid.dim == 3)
-    rc = s->prec == NS_FP32 ? nsk::dispatch3_f32(op, a, st) : nsk::dispatch3_f64(op, a, st);
+    rc = s->tc ? nsk::dispatch3_tc(op, a, s->tcm, s->tmap_xtc, st)
+               : (s->prec == NS_FP32 ? nsk::dispatch3_f32(op, a, st) : nsk::dispatch3_f64(op, a, st));
   else
     rc = s->prec == NS_FP32 ? nsk::dispatch2_f32(op, a, st) : nsk::dispatch2_f64(op, a, st);
   if (rc == -1) return fail(s, NS_EUNSUPPORTED, "no kernels instantiated for N=%d", s->grid.n);
@@ -339,7 +345,7 @@ int phys_to_spec(ns_state *s, const double *host, void *dst) {
 
 void free_all(ns_state *s) {
   if (s->graph) cudaGraphExecDestroy(s->graph);
-  void *ptrs[] = {s->tw, s->ef, s->ef2, s->u, s->acc, s->F, s->zb, s->yb, s->staging, s->diag, s->umax, s->ctl, s->derr, s->ek2, s->ek22};
+  void *ptrs[] = {s->tw, s->ef, s->ef2, s->u, s->acc, s->F, s->zb, s->yb, s->staging, s->diag, s->umax, s->ctl, s->derr, s->ek2, s->ek22, s->tcm};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   if (s->own) cudaStreamDestroy(s->own);
@@ -462,7 +468,8 @@ int ns_init(ns_state **out, const ns_grid *grid, double nu, double dt, const dou
   cudaDeviceGetAttribute(&s->nsm, cudaDevAttrMultiProcessorCount, s->dev);
   if (s->nsm < 1) s->nsm = 1;
   s->grid = *grid;
-  s->prec = grid->precision;
+  s->tc = grid->precision == NS_FP32_TC;
+  s->prec = s->tc ? NS_FP32 : grid->precision;
   s->ncomp = grid->dim == 3 ? 3 : 1;
   s->nu = nu;
   s->dt = dt;
@@ -534,6 +541,20 @@ int ns_init(ns_state **out, const ns_grid *grid, double nu, double dt, const dou
     return bail(rc);
   if (forcing_phys && (rc = dmalloc(s, &s->F, field))) return bail(rc);
   if ((rc = dmalloc(s, (void **)&s->derr, sizeof(int)))) return bail(rc);
+  if (s->tc) {
+    const std::vector<unsigned char> m = nsk::tc_matrices(g.N);
+    if ((rc = dmalloc(s, &s->tcm, m.size()))) return bail(rc);
+    INIT_CK(cudaMemcpy(s->tcm, m.data(), m.size(), cudaMemcpyHostToDevice));
+    // yb as 2D in 8-byte elements: hs columns by 6 N^2 rows, boxes of whole
+    // rows by one tile of lines
+    const unsigned long long dims[2] = {(unsigned long long)g.hs, 6ull * g.N * g.N},
+                             strides[1] = {(unsigned long long)g.hs * s->cs};
+    const unsigned box[2] = {(unsigned)g.hs, (unsigned)nsk::tc_lines_per_tile(g.N)};
+    if (nsk::make_tensor_map(s->tmap_xtc, s->yb, 2, dims, strides, box) != 0) {
+      fail(s, NS_EUNSUPPORTED, "ns_init: tensor map for the tensor-core x pass could not be made");
+      return bail(NS_EUNSUPPORTED);
+    }
+  }
   INIT_CK(cudaMemsetAsync(s->derr, 0, sizeof(int), s->stream));
   if (g.dim == 3) {
     // TMA tensor maps over the y-pass inputs, in 8-byte elements.  yb as 2D:

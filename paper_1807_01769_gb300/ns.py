@@ -24,6 +24,7 @@ NS_ENONFINITE = -5
 NS_ETIMEOUT = -6
 NS_FP64 = 0
 NS_FP32 = 1
+NS_FP32_TC = 2
 
 ERROR_NAMES = {0: "NS_OK", -1: "NS_EINVAL", -2: "NS_ENOMEM", -3: "NS_ECUDA", -4: "NS_EUNSUPPORTED",
                -5: "NS_ENONFINITE", -6: "NS_ETIMEOUT"}
