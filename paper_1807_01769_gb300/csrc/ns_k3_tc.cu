@@ -54,30 +54,52 @@ std::vector<unsigned char> matrices() {
   return m;
 }
 
+// blocks per SM of the kernel for N, found once at OP_PREPARE (outside any
+// stream capture, where the occupancy query may not run)
+template <int N>
+int &blocks_per_sm() {
+  static int v = 0;
+  return v;
+}
+
 template <int N>
 int launch(int op, const Args &a, const void *mats, const void *tmap, cudaStream_t s) {
   using G = tc::Geom<N>;
   if (op == OP_PREPARE) {
     set_smem(tc::k3_xpass_tc<N>, G::SMEM);
-    // the largest shared-memory carveout, so that the occupancy query below
-    // (and the hardware) fit the blocks the tensor memory holds
+    // the largest shared-memory carveout, so that the SM holds the blocks the
+    // tensor memory allows
     cudaFuncSetAttribute(tc::k3_xpass_tc<N>, cudaFuncAttributePreferredSharedMemoryCarveout,
                          (int)cudaSharedmemCarveoutMaxShared);
+    // resident blocks from the kernel's registers and shared memory and the
+    // tensor memory it allocates (counted here: the occupancy query does not
+    // see the tensor memory and answered one block per SM for this kernel)
+    int per_sm = 1;
+    cudaFuncAttributes fa{};
+    int dev = 0, regs_sm = 0, smem_sm = 0, reserved = 0;
+    if (cudaFuncGetAttributes(&fa, tc::k3_xpass_tc<N>) == cudaSuccess && cudaGetDevice(&dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev) == cudaSuccess) {
+      const int regs_block = (fa.numRegs + 7) / 8 * 8 * tc::kThreads;
+      const int by_regs = regs_block > 0 ? regs_sm / regs_block : 1;
+      const int by_smem = smem_sm / (int)(G::SMEM + fa.sharedSizeBytes + reserved);
+      per_sm = by_regs < by_smem ? by_regs : by_smem;
+    }
+    blocks_per_sm<N>() = per_sm < 1 ? 1 : (per_sm > G::CTAS ? G::CTAS : per_sm);
+    cudaGetLastError();
     return dispatch3_f32(op, a, s);
   }
   if (op != OP_XPASS) return dispatch3_f32(op, a, s);
   if (tmap == nullptr || a.g.hs != G::HS) return (int)cudaErrorInvalidValue;
-  static int per_sm = 0;
-  if (per_sm == 0) {
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tc::k3_xpass_tc<N>, 128, G::SMEM);
-    if (per_sm < 1) per_sm = 1;
-    if (per_sm > G::CTAS) per_sm = G::CTAS;
-  }
+  const int per_sm = blocks_per_sm<N>() > 0 ? blocks_per_sm<N>() : 1;
   const long long lines = (long long)(a.nz > 0 ? a.nz : N) * N, tiles = lines / G::L;
-  const long long grid = tiles < (long long)per_sm * (a.nsm > 0 ? a.nsm : 1) ? tiles : (long long)per_sm * a.nsm;
-  tc::k3_xpass_tc<N><<<(unsigned)grid, 128, G::SMEM, s>>>(a.g, (long long)a.z0 * N, tiles, (float2 *)a.yb,
-                                                           (const float2 *)a.tw, (const uint4 *)mats,
-                                                           *reinterpret_cast<const CUtensorMap *>(tmap), a.umax, a.err);
+  const long long slots = (long long)per_sm * (a.nsm > 0 ? a.nsm : 1);
+  const long long grid = tiles < slots ? tiles : slots;
+  tc::k3_xpass_tc<N><<<(unsigned)grid, tc::kThreads, G::SMEM, s>>>(a.g, (long long)a.z0 * N, tiles, (float2 *)a.yb,
+                                                                   (const float2 *)a.tw, (const uint4 *)mats,
+                                                                   *reinterpret_cast<const CUtensorMap *>(tmap),
+                                                                   a.umax, a.err);
   return (int)cudaGetLastError();
 }
 

@@ -20,8 +20,8 @@
 // transform reuses the inverse matrices on conjugated input:
 // DFT_-(z) = conj(DFT_+(conj z)).
 //
-// A block (128 threads, one per tensor-memory lane) owns L = 128 / R1 lines
-// per tile.  Stage-A operands are K-major (thread = row, each writes its own
+// A block (256 threads, two per tensor-memory lane, each taking half of its
+// row's values) owns L = 128 / R1 lines per tile.  Stage-A operands are K-major (thread = row, each writes its own
 // 16-byte row segments), stage-B operands MN-major (the thread holding row
 // (line, b) of stage A writes column b of the rows (line, c)), so no register
 // transposes are needed.  The spectral rows of each inverse pair arrive by
@@ -90,15 +90,29 @@ __device__ __forceinline__ void tmem_ld8(unsigned taddr, float (&v)[8]) {
 #pragma unroll
   for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
 }
+__device__ __forceinline__ void tmem_ld4(unsigned taddr, float (&v)[4]) {
+  unsigned r[4];
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];\n"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(taddr));
+#pragma unroll
+  for (int i = 0; i < 4; ++i) v[i] = __uint_as_float(r[i]);
+}
 template <int X>
 __device__ __forceinline__ void tmem_ld(unsigned taddr, float (&v)[X]) {
-  static_assert(X % 8 == 0, "multiples of 8 columns");
+  static_assert(X % 4 == 0, "multiples of 4 columns");
 #pragma unroll
   for (int i = 0; i < X / 8; ++i) {
     float t[8];
     tmem_ld8(taddr + 8 * i, t);
 #pragma unroll
     for (int j = 0; j < 8; ++j) v[8 * i + j] = t[j];
+  }
+  if constexpr (X % 8 != 0) {
+    float t[4];
+    tmem_ld4(taddr + X - 4, t);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) v[X - 4 + j] = t[j];
   }
 }
 // bounded wait for the completion of the mbarrier phase with parity ph
@@ -164,6 +178,7 @@ struct Plan<512> {
 //        K-major [n][k] like OPA
 //  LAND : TMA landing tile of one inverse pair: [2 fields][L lines][HS]
 //        complex64 (HS = the padded row length of the spectral buffers)
+//  TW   : the twiddles w^(b c) = exp(+2 pi i b c / N), b c < N, complex64
 // Tensor memory: GA = stage-A results (MT tiles x KA columns), T1..T3 = the
 // three inverse pair results (KB columns each; T1, T2 then take the forward
 // stage-B results and T3 the forward n_z stage-A result).
@@ -180,7 +195,8 @@ struct Geom {
   static constexpr unsigned FB = FA + 2 * FA_HALF, FB_HALF = (unsigned)KB * KB * 2;
   static constexpr unsigned MATS_BYTES = 2 * FA_HALF + 2 * FB_HALF;
   static constexpr unsigned LAND = FB + 2 * FB_HALF, LAND_FIELD = (unsigned)L * HS * 8;
-  static constexpr unsigned USED = LAND + 2 * LAND_FIELD;
+  static constexpr unsigned TW = LAND + 2 * LAND_FIELD, TW_BYTES = (unsigned)((R1 - 1) * (R2 - 1) + 1) * 8;
+  static constexpr unsigned USED = TW + (TW_BYTES + 127u) / 128u * 128u;
   static constexpr unsigned TCOLS = 4 * KB;  // a power of two: 64, 128 or 256
   static constexpr unsigned GA = 0, T1 = KB, T2 = 2 * KB, T3 = 3 * KB;
   static constexpr int CTAS = 512 / TCOLS;  // blocks per SM the tensor memory holds
@@ -195,33 +211,59 @@ struct Geom {
 };
 
 // -------------------------------------------------------------- kernel --
-// Stage B operand of one stage-A row (group grp = line or line pair, index b):
-// v = the row's stage-A outputs (re c, then im c), twiddled by w^(b c) and
-// written as column (p R2 + b) of the MN-major rows (grp R1 + c).
+// -------------------------------------------------------------- kernel --
+// Two threads per tensor-memory lane: thread tid serves row (tid mod 128) and
+// takes half h = tid / 128 of the row's values in every phase.
+constexpr int kThreads = 256;
+
+// NV (4 or 8) consecutive BF16 elements: hi at p, lo at p + lo_off
+template <int NV>
+__device__ __forceinline__ void put_run(unsigned char *p, unsigned lo_off, const float *x) {
+  static_assert(NV == 4 || NV == 8, "runs of 8 or 16 bytes");
+  if constexpr (NV == 8)
+    put8(p, p + lo_off, x);
+  else
+    put4(p, p + lo_off, x[0], x[1], x[2], x[3]);
+}
+// element k of K-major row r of an operand tile at p (row stride in core matrices: kbytes16 = K * 16)
+__device__ __forceinline__ unsigned char *kmajor(unsigned char *p, int r, int k, int kbytes16) {
+  return p + (r >> 3) * kbytes16 + (r & 7) * 16 + (k >> 3) * 128 + (k & 7) * 2;
+}
+
+// Stage-B operand from one stage-A row (group grp = line or line pair, index
+// b) whose outputs sit in this warp's lanes from tensor-memory address taddr
+// (re c at column c, im at R1 + c): the half h of them, c in [h R1/2,
+// (h+1) R1/2), twiddled by w^(b c) and written as column (p R2 + b) of the
+// MN-major rows (grp R1 + c).  Warp-collective (the load); `store` = the row
+// is real.
 template <int N>
-__device__ __forceinline__ void stage_b_operand(unsigned char *sm, const float (&v)[Geom<N>::KA], int grp, int b,
-                                                const float2 *__restrict__ tw) {
+__device__ __forceinline__ void stage_b_half(unsigned char *sm, unsigned taddr, int grp, int b, int h, bool store) {
   using G = Geom<N>;
-  constexpr int R1 = G::R1, R2 = G::R2;
-  float yr[R1], yi[R1];
+  constexpr int R1 = G::R1, R2 = G::R2, CH = R1 / 2;
+  float vr[CH], vi[CH];
+  tmem_ld<CH>(taddr + h * CH, vr);
+  tmem_ld<CH>(taddr + R1 + h * CH, vi);
+  tmem_wait_ld();
+  if (!store) return;
+  const float2 *tws = reinterpret_cast<const float2 *>(sm + G::TW);
+  float yr[CH], yi[CH];
 #pragma unroll
-  for (int c = 0; c < R1; ++c) {
-    const float2 w = __ldg(tw + b * c);  // exp(-2 pi i b c / N): use its conjugate
-    const float xr = v[c], xi = v[R1 + c];
-    yr[c] = fmaf(xr, w.x, xi * w.y);
-    yi[c] = fmaf(xi, w.x, -(xr * w.y));
+  for (int i = 0; i < CH; ++i) {
+    const float2 w = tws[b * (h * CH + i)];  // exp(+2 pi i b c / N)
+    yr[i] = fmaf(vr[i], w.x, -(vi[i] * w.y));
+    yi[i] = fmaf(vi[i], w.x, vr[i] * w.y);
   }
+  const int m0 = grp * R1 + h * CH;
 #pragma unroll
   for (int p = 0; p < 2; ++p) {
     const int kp = p * R2 + b;
-    unsigned char *row = sm + G::OPB + (kp >> 3) * 2048 + (kp & 7) * 16 + (grp * R1 / 8) * 128;
-#pragma unroll
-    for (int c8 = 0; c8 < R1 / 8; ++c8) put8(row + c8 * 128, row + c8 * 128 + G::OPB_HALF, (p ? yi : yr) + 8 * c8);
+    unsigned char *dst = sm + G::OPB + (kp >> 3) * 2048 + (kp & 7) * 16 + (m0 >> 3) * 128 + (m0 & 7) * 2;
+    put_run<CH>(dst, G::OPB_HALF, p ? yi : yr);
   }
 }
 
-// Stage-A MMAs of the operand tile at byte offset tile_off into tensor-memory column col;
-// stage-B MMAs into col.  Issued by one thread.
+// Stage-A MMAs of the operand tile at byte offset tile_off into tensor-memory
+// column col; stage-B MMAs into col.  Issued by one thread.
 template <int N>
 __device__ __forceinline__ void issue_a(unsigned sbase, unsigned tmem, unsigned tile_off, unsigned col) {
   using G = Geom<N>;
@@ -247,13 +289,13 @@ __device__ __forceinline__ void issue_b(unsigned sbase, unsigned tmem, unsigned 
     }
 }
 
-// Forward stage-B result of row (grp, c) at tensor-memory column col: G[k] =
-// conj of the forward DFT of the pair z = y_a + i y_b, k = c + R1 d.  Returns
-// Y_a[k], Y_b[k] for d <= KC / R1 (the partner G[N - k] comes from lane
-// (grp, (R1 - c) mod R1)); the caller stores those with k <= KC.
+// Forward stage-B result of row (grp, c) in this warp's lanes from taddr:
+// G[k] = conj of the forward DFT of the pair z = y_a + i y_b, k = c + R1 d.
+// Writes Y_b (second = true) or Y_a for k = c + R1 d <= KC to out[k]; the
+// partner G[N - k] comes from lane (grp, (R1 - c) mod R1).  Warp-collective.
 template <int N>
-__device__ __forceinline__ void split_pair(unsigned taddr, int c, int lane, float2 (&ya)[Geom<N>::KC / Geom<N>::R1 + 1],
-                                           float2 (&ybv)[Geom<N>::KC / Geom<N>::R1 + 1]) {
+__device__ __forceinline__ void split_store(unsigned taddr, int c, int lane, bool second, bool store,
+                                            float2 *__restrict__ out) {
   using G = Geom<N>;
   constexpr int R1 = G::R1, R2 = G::R2, DM = G::KC / R1 + 1;
   float v[G::KB];
@@ -268,28 +310,37 @@ __device__ __forceinline__ void split_pair(unsigned taddr, int c, int lane, floa
     const float hr = __shfl_sync(0xffffffffu, sr, src), hi = __shfl_sync(0xffffffffu, si, src);
     const float gr = v[d], gi = v[R2 + d];
     // Z = conj G: Y_a = (Z[k] + conj Z[N-k]) / 2, Y_b = (Z[k] - conj Z[N-k]) / (2 i)
-    ya[d] = make_float2(0.5f * (gr + hr), 0.5f * (hi - gi));
-    ybv[d] = make_float2(-0.5f * (gi + hi), 0.5f * (hr - gr));
+    const float2 y = second ? make_float2(-0.5f * (gi + hi), 0.5f * (hr - gr))
+                            : make_float2(0.5f * (gr + hr), 0.5f * (hi - gi));
+    if (store && c + R1 * d <= G::KC) out[c + R1 * d] = y;
   }
 }
 
 template <int N>
-__global__ void __launch_bounds__(128, 1)
+__global__ void __launch_bounds__(kThreads, 2)
     k3_xpass_tc(Geo g, long long line_base, long long tiles, float2 *__restrict__ yb, const float2 *__restrict__ tw,
                 const uint4 *__restrict__ mats, const __grid_constant__ CUtensorMap tm,
                 unsigned long long *__restrict__ umax, int *__restrict__ err) {
   using G = Geom<N>;
-  constexpr int R1 = G::R1, R2 = G::R2, L = G::L, MT = G::MT, KA = G::KA, KB = G::KB, KC = G::KC;
-  constexpr int DM = KC / R1 + 1;
+  constexpr int R1 = G::R1, R2 = G::R2, L = G::L, MT = G::MT, KA = G::KA, KC = G::KC;
+  constexpr int CH = R1 / 2;                        // a (or c) values per half row
+  constexpr int CHK = R2 / 8 >= 2 ? 8 : 4;          // points per product chunk
+  constexpr int NCH = R2 / CHK;                     // chunks per row (even: split by half)
+  static_assert(NCH % 2 == 0, "product chunks split between the halves");
   unsigned char *sm = dyn_smem<unsigned char>();
   __shared__ __align__(8) unsigned long long bars[3];  // stage A done, stage B done, tile landed
   __shared__ unsigned tslot;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int row = tid & 127, h = tid >> 7;
   const unsigned sbase = smem_addr(sm);
   const long long fs = g.yb_f, hs = g.hs;
 
-  for (unsigned i = tid; i < G::MATS_BYTES / 16; i += 128)
+  for (unsigned i = tid; i < G::MATS_BYTES / 16; i += kThreads)
     reinterpret_cast<uint4 *>(sm + G::FA)[i] = __ldg(mats + i);
+  for (unsigned i = tid; i < G::TW_BYTES / 8; i += kThreads) {
+    const float2 w = __ldg(tw + i);  // exp(-2 pi i j / N): store the conjugate
+    reinterpret_cast<float2 *>(sm + G::TW)[i] = make_float2(w.x, -w.y);
+  }
   if (warp == 0) tmem_alloc(&tslot, G::TCOLS);
   if (tid == 0) {
     mbar_init(&bars[0], 1);
@@ -300,9 +351,9 @@ __global__ void __launch_bounds__(128, 1)
   __syncthreads();
   fence_after();
   const unsigned tmem = tslot;
-  const unsigned tlane = tmem + ((unsigned)(warp * 32) << 16);  // this warp's lanes
+  const unsigned tlane = tmem + ((unsigned)((warp & 3) * 32) << 16);  // this warp's lanes
   unsigned pha = 0, phb = 0, pht = 0;
-  bool bad = false, tma_pending = false;
+  bool bad = false, tma_pending = false, failed = false;
   const float2 *land = reinterpret_cast<const float2 *>(sm + G::LAND);
   const long long nn = (long long)N * N;  // lines per field
   // one thread: the spectral rows of fields f, f + 1 of the tile's lines into LAND
@@ -335,15 +386,14 @@ __global__ void __launch_bounds__(128, 1)
     fence_before();
     return !__syncthreads_or(bad);
   };
-
-  const int line = tid / R1, c = tid % R1;  // this thread's stage-B row
-  float umx = 0.f, umy = 0.f, umz = 0.f;
-  bool failed = false;
 #define NS_TC_PUBLISH_OR_LEAVE \
   if (!publish()) {            \
     failed = true;             \
     goto out;                  \
   }
+
+  const int line = row / R1, c = row % R1;  // this thread's stage-B row
+  float umx = 0.f, umy = 0.f, umz = 0.f;
 
   for (long long tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
     const long long line0 = line_base + tile * L;
@@ -352,12 +402,12 @@ __global__ void __launch_bounds__(128, 1)
       wait_t();  // fields 2 pp, 2 pp + 1 of this tile's lines are in LAND
 #pragma unroll
       for (int j = 0; j < MT; ++j) {
-        const int ra = tid + 128 * j, ln = ra / R2, b = ra % R2;
+        const int ra = row + 128 * j, ln = ra / R2, b = ra % R2;
         const float2 *pa = land + ln * G::HS, *pb = pa + L * G::HS;
-        float z[KA];
+        float zr[CH], zi[CH];
 #pragma unroll
-        for (int a = 0; a < R1; ++a) {
-          const int k = R2 * a + b;
+        for (int i = 0; i < CH; ++i) {
+          const int k = R2 * (h * CH + i) + b;
           const bool lo = k <= KC, hi = k >= N - KC;
           float2 xa = make_float2(0.f, 0.f), xb = xa;
           if (lo || hi) {
@@ -367,12 +417,12 @@ __global__ void __launch_bounds__(128, 1)
           }
           if (k == 0) xa.y = xb.y = 0.f;  // the self-conjugate mode is real
           // k <= kc: z = xa + i xb;  k >= N - kc: z = conj(xa) + i conj(xb)
-          z[a] = lo ? xa.x - xb.y : xa.x + xb.y;
-          z[R1 + a] = lo ? xa.y + xb.x : xb.x - xa.y;
+          zr[i] = lo ? xa.x - xb.y : xa.x + xb.y;
+          zi[i] = lo ? xa.y + xb.x : xb.x - xa.y;
         }
-        unsigned char *row = sm + G::OPA + j * 2 * G::TILE_A + (tid >> 3) * (KA * 16) + (tid & 7) * 16;
-#pragma unroll
-        for (int g8 = 0; g8 < KA / 8; ++g8) put8(row + g8 * 128, row + g8 * 128 + G::TILE_A, z + 8 * g8);
+        unsigned char *tile_p = sm + G::OPA + j * 2 * G::TILE_A;
+        put_run<CH>(kmajor(tile_p, row, h * CH, KA * 16), G::TILE_A, zr);
+        put_run<CH>(kmajor(tile_p, row, R1 + h * CH, KA * 16), G::TILE_A, zi);
       }
       NS_TC_PUBLISH_OR_LEAVE
       // LAND is free: the next pair of this tile, or the first pair of the next tile
@@ -396,109 +446,93 @@ __global__ void __launch_bounds__(128, 1)
       if (pp > 0) wait_b();  // the previous pair's stage B has read the operand
 #pragma unroll
       for (int j = 0; j < MT; ++j) {
-        const int ra = tid + 128 * j;
-        float v[KA];
-        tmem_ld<KA>(tlane + G::GA + j * KA, v);
-        tmem_wait_ld();
-        stage_b_operand<N>(sm, v, ra / R2, ra % R2, tw);
+        const int ra = row + 128 * j;
+        stage_b_half<N>(sm, tlane + G::GA + j * KA, ra / R2, ra % R2, h, true);
       }
       NS_TC_PUBLISH_OR_LEAVE
       if (tid == 0) {
         fence_after();
-        issue_b<N>(sbase, tmem, G::T1 + pp * KB);
+        issue_b<N>(sbase, tmem, G::T1 + pp * G::KB);
         commit(&bars[1]);
       }
     }
     wait_b();
     // ------------------------------------- product, forward stage-A rows --
-    // this thread: points n = c + R1 d of line `line`; u = (T1.re, T1.im,
-    // T2.re), w = (T2.im, T3.re, T3.im); forward operands z = conj(n_x + i n_y)
-    // into tiles 0..MT-1 and z = conj(n_z[even line] + i n_z[odd line]) into
-    // the OPB region (free: the last inverse stage B has completed)
+    // this thread: points n = c + R1 d of line `line`, d in its chunks; u =
+    // (T1.re, T1.im, T2.re), w = (T2.im, T3.re, T3.im); forward operands z =
+    // conj(n_x + i n_y) into the OPA tiles and z = conj(n_z[even line] + i
+    // n_z[odd line]) into the OPB region (free: the last inverse stage B has
+    // completed), laid out as a stage-A tile
     {
-      const int par = line & 1;
+      const int par = line & 1, q = line >> 1;
 #pragma unroll
-      for (int d0 = 0; d0 < R2; d0 += 8) {
-        float ux[8], uy[8], uz[8], wx[8], wy[8], wz[8];
-        tmem_ld8(tlane + G::T1 + d0, ux);
-        tmem_ld8(tlane + G::T1 + R2 + d0, uy);
-        tmem_ld8(tlane + G::T2 + d0, uz);
-        tmem_ld8(tlane + G::T2 + R2 + d0, wx);
-        tmem_ld8(tlane + G::T3 + d0, wy);
-        tmem_ld8(tlane + G::T3 + R2 + d0, wz);
+      for (int cc = 0; cc < NCH / 2; ++cc) {
+        const int d0 = (2 * cc + h) * CHK;
+        float ux[CHK], uy[CHK], uz[CHK], wx[CHK], wy[CHK], wz[CHK];
+        tmem_ld<CHK>(tlane + G::T1 + d0, ux);
+        tmem_ld<CHK>(tlane + G::T1 + R2 + d0, uy);
+        tmem_ld<CHK>(tlane + G::T2 + d0, uz);
+        tmem_ld<CHK>(tlane + G::T2 + R2 + d0, wx);
+        tmem_ld<CHK>(tlane + G::T3 + d0, wy);
+        tmem_ld<CHK>(tlane + G::T3 + R2 + d0, wz);
         tmem_wait_ld();
-        float nx[8], ny[8], nz[8], nzp[8];
+        float nx[CHK], ny[CHK], nz[CHK], nzp[CHK];
 #pragma unroll
-        for (int i = 0; i < 8; ++i) {
+        for (int i = 0; i < CHK; ++i) {
           nx[i] = fmaf(uy[i], wz[i], -(uz[i] * wy[i]));
-          ny[i] = fmaf(uz[i], wx[i], -(ux[i] * wz[i]));
+          ny[i] = -fmaf(uz[i], wx[i], -(ux[i] * wz[i]));  // stored negated: z = conj(n_x + i n_y)
           nz[i] = fmaf(ux[i], wy[i], -(uy[i] * wx[i]));
           umx = fmaxf(umx, fabsf(ux[i]));
           umy = fmaxf(umy, fabsf(uy[i]));
           umz = fmaxf(umz, fabsf(uz[i]));
         }
 #pragma unroll
-        for (int i = 0; i < 8; ++i) nzp[i] = __shfl_xor_sync(0xffffffffu, nz[i], R1);
+        for (int i = 0; i < CHK; ++i) nzp[i] = __shfl_xor_sync(0xffffffffu, nz[i], R1);
         // (n_x, -n_y) rows (line, c + R1 jj), K = a = d / MT
+        constexpr int RUN = CHK / MT;
 #pragma unroll
         for (int jj = 0; jj < MT; ++jj) {
-          const int ra = line * R2 + c + R1 * jj, t = ra / 128, r = ra % 128;
-          unsigned char *row = sm + G::OPA + t * 2 * G::TILE_A + (r >> 3) * (KA * 16) + (r & 7) * 16;
+          const int ra = line * R2 + c + R1 * jj;
+          unsigned char *tile_p = sm + G::OPA + (ra >> 7) * 2 * G::TILE_A;
+          float xr[RUN], xi[RUN];
 #pragma unroll
-          for (int run = 0; run < 8 / (4 * MT); ++run) {
-            const int a0 = d0 / MT + 4 * run;
-            float xr[4], xi[4];
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-              const int i = jj + MT * (4 * run + e);
-              xr[e] = nx[i];
-              xi[e] = -ny[i];
-            }
-            const int kr = a0, ki = R1 + a0;
-            put4(row + (kr >> 3) * 128 + (kr & 7) * 2, row + (kr >> 3) * 128 + (kr & 7) * 2 + G::TILE_A, xr[0],
-                 xr[1], xr[2], xr[3]);
-            put4(row + (ki >> 3) * 128 + (ki & 7) * 2, row + (ki >> 3) * 128 + (ki & 7) * 2 + G::TILE_A, xi[0],
-                 xi[1], xi[2], xi[3]);
+          for (int e = 0; e < RUN; ++e) {
+            xr[e] = nx[jj + MT * e];
+            xi[e] = ny[jj + MT * e];
           }
+          const int a0 = d0 / MT;
+          put_run<RUN>(kmajor(tile_p, ra & 127, a0, KA * 16), G::TILE_A, xr);
+          put_run<RUN>(kmajor(tile_p, ra & 127, R1 + a0, KA * 16), G::TILE_A, xi);
         }
-        // n_z pair rows (line / 2, b), b = c + R1 par (MT = 2: points of parity
-        // par) or b = c with the K range split between the two lines (MT = 1)
+        // n_z pair rows (q, b): MT = 2: b = c + R1 par, the points of parity
+        // par; MT = 1: b = c, the K range split between the two lines
         {
-          const int q = line >> 1;
+          float xr[RUN], xi[RUN];
+          bool mine;
+          int r, a0;
+          if constexpr (MT == 2) {
 #pragma unroll
-          for (int run = 0; run < 2; ++run) {
-            int a0;
-            bool mine;
-            float xr[4], xi[4];
-            if (MT == 2) {
-              a0 = d0 / 2 + 4 * run;
-              mine = run == 0;  // the four points of parity par fill one run
-#pragma unroll
-              for (int e = 0; e < 4; ++e) {  // point 2 e + par of the chunk
-                const float own = par ? nz[2 * e + 1] : nz[2 * e], oth = par ? nzp[2 * e + 1] : nzp[2 * e];
-                xr[e] = par ? oth : own;
-                xi[e] = -(par ? own : oth);
-              }
-            } else {
-              a0 = d0 + 4 * run;
-              mine = (a0 >= R1 / 2 ? 1 : 0) == par;
-#pragma unroll
-              for (int e = 0; e < 4; ++e) {
-                const int i = 4 * run + e;
-                const float own = nz[i], oth = nzp[i];
-                xr[e] = par ? oth : own;
-                xi[e] = -(par ? own : oth);
-              }
+            for (int e = 0; e < RUN; ++e) {
+              const float own = par ? nz[2 * e + 1] : nz[2 * e], oth = par ? nzp[2 * e + 1] : nzp[2 * e];
+              xr[e] = par ? oth : own;
+              xi[e] = -(par ? own : oth);
             }
-            if (mine) {
-              const int r = q * R2 + c + (MT == 2 ? R1 * par : 0);
-              unsigned char *row = sm + G::OPB + (r >> 3) * (KA * 16) + (r & 7) * 16;
-              const int kr = a0, ki = R1 + a0;
-              put4(row + (kr >> 3) * 128 + (kr & 7) * 2, row + (kr >> 3) * 128 + (kr & 7) * 2 + G::TILE_A, xr[0],
-                   xr[1], xr[2], xr[3]);
-              put4(row + (ki >> 3) * 128 + (ki & 7) * 2, row + (ki >> 3) * 128 + (ki & 7) * 2 + G::TILE_A, xi[0],
-                   xi[1], xi[2], xi[3]);
+            mine = true;
+            r = q * R2 + c + R1 * par;
+            a0 = d0 / 2;
+          } else {
+#pragma unroll
+            for (int e = 0; e < RUN; ++e) {
+              xr[e] = par ? nzp[e] : nz[e];
+              xi[e] = -(par ? nz[e] : nzp[e]);
             }
+            mine = (d0 >= R1 / 2 ? 1 : 0) == par;
+            r = q * R2 + c;
+            a0 = d0;
+          }
+          if (mine) {
+            put_run<RUN>(kmajor(sm + G::OPB, r, a0, KA * 16), G::TILE_A, xr);
+            put_run<RUN>(kmajor(sm + G::OPB, r, R1 + a0, KA * 16), G::TILE_A, xi);
           }
         }
       }
@@ -514,11 +548,8 @@ __global__ void __launch_bounds__(128, 1)
     // ------------------------------------------------ forward stage B ------
 #pragma unroll
     for (int j = 0; j < MT; ++j) {
-      const int ra = tid + 128 * j;
-      float v[KA];
-      tmem_ld<KA>(tlane + G::GA + j * KA, v);
-      tmem_wait_ld();
-      stage_b_operand<N>(sm, v, ra / R2, ra % R2, tw);
+      const int ra = row + 128 * j;
+      stage_b_half<N>(sm, tlane + G::GA + j * KA, ra / R2, ra % R2, h, true);
     }
     NS_TC_PUBLISH_OR_LEAVE
     if (tid == 0) {
@@ -526,13 +557,8 @@ __global__ void __launch_bounds__(128, 1)
       issue_b<N>(sbase, tmem, G::T1);
       commit(&bars[1]);
     }
-    {
-      float v[KA];
-      tmem_ld<KA>(tlane + G::T3, v);
-      tmem_wait_ld();
-      wait_b();  // the n_x, n_y stage B has read the operand
-      if (tid < 64 * MT) stage_b_operand<N>(sm, v, tid / R2, tid % R2, tw);
-    }
+    wait_b();  // the n_x, n_y stage B has read the operand
+    stage_b_half<N>(sm, tlane + G::T3, row / R2, row % R2, h, row < 64 * MT);
     NS_TC_PUBLISH_OR_LEAVE
     if (tid == 0) {
       fence_after();
@@ -540,29 +566,11 @@ __global__ void __launch_bounds__(128, 1)
       commit(&bars[1]);
     }
     // ----------------------------------------------------------- outputs ---
-    {
-      float2 ya[DM], ybv[DM];
-      split_pair<N>(tlane + G::T1, c, lane, ya, ybv);
-      float2 *ox = yb + (line0 + line) * hs, *oy = ox + fs;
-#pragma unroll
-      for (int d = 0; d < DM; ++d)
-        if (c + R1 * d <= KC) {
-          ox[c + R1 * d] = ya[d];
-          oy[c + R1 * d] = ybv[d];
-        }
-    }
+    // F1 rows (line, c): half 0 stores n_x, half 1 n_y
+    split_store<N>(tlane + G::T1, c, lane, h == 1, true, yb + h * fs + (line0 + line) * hs);
     wait_b();
-    if (warp < 2) {  // rows (q, c), q < L / 2: n_z of lines 2q, 2q + 1
-      float2 ya[DM], ybv[DM];
-      split_pair<N>(tlane + G::T2, c, lane, ya, ybv);
-      float2 *o0 = yb + 2 * fs + (line0 + 2 * line) * hs, *o1 = o0 + hs;
-#pragma unroll
-      for (int d = 0; d < DM; ++d)
-        if (c + R1 * d <= KC) {
-          o0[c + R1 * d] = ya[d];
-          o1[c + R1 * d] = ybv[d];
-        }
-    }
+    // F2 rows (q, c), q < L / 2 (lanes 0..63): half 0 stores n_z of line 2q, half 1 of line 2q + 1
+    if ((warp & 3) < 2) split_store<N>(tlane + G::T2, c, lane, h == 1, true, yb + 2 * fs + (line0 + 2 * line + h) * hs);
     if (__syncthreads_or(bad)) {
       failed = true;
       goto out;
