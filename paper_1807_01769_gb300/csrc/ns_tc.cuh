@@ -173,12 +173,15 @@ struct Plan<512> {
 //  OPB : stage-B operand, hi and lo MN-major [K = KB][M = 128]; core
 //        (m/8, k/8) at (k/8) 2048 + (m/8) 128, row k % 8 at 16 (k % 8); it
 //        also holds the stage-A tile of the forward n_z pairs (laid out as an
-//        OPA tile), which is consumed before the next stage-B operand is built
+//        OPA tile), which is consumed before the next stage-B operand is built;
+//        OPA, free by then, takes the n_z pairs' stage-B operand (same size,
+//        same layout) so that both forward stage-B GEMMs run together
 //  FA, FB : real-block DFT-R1 / DFT-R2 matrices (+ sign), hi and lo,
 //        K-major [n][k] like OPA
 //  LAND : TMA landing tile of one inverse pair: [2 fields][L lines][HS]
 //        complex64 (HS = the padded row length of the spectral buffers)
-//  TW   : the twiddles w^(b c) = exp(+2 pi i b c / N), b c < N, complex64
+//  TW   : the twiddles w^(b c) = exp(+2 pi i b c / N) as [c][b] complex64
+//        (the lanes of a warp hold consecutive b)
 // Tensor memory: GA = stage-A results (MT tiles x KA columns), T1..T3 = the
 // three inverse pair results (KB columns each; T1, T2 then take the forward
 // stage-B results and T3 the forward n_z stage-A result).
@@ -195,7 +198,7 @@ struct Geom {
   static constexpr unsigned FB = FA + 2 * FA_HALF, FB_HALF = (unsigned)KB * KB * 2;
   static constexpr unsigned MATS_BYTES = 2 * FA_HALF + 2 * FB_HALF;
   static constexpr unsigned LAND = FB + 2 * FB_HALF, LAND_FIELD = (unsigned)L * HS * 8;
-  static constexpr unsigned TW = LAND + 2 * LAND_FIELD, TW_BYTES = (unsigned)((R1 - 1) * (R2 - 1) + 1) * 8;
+  static constexpr unsigned TW = LAND + 2 * LAND_FIELD, TW_BYTES = (unsigned)R1 * R2 * 8;
   static constexpr unsigned USED = TW + (TW_BYTES + 127u) / 128u * 128u;
   static constexpr unsigned TCOLS = 4 * KB;  // a power of two: 64, 128 or 256
   static constexpr unsigned GA = 0, T1 = KB, T2 = 2 * KB, T3 = 3 * KB;
@@ -206,7 +209,8 @@ struct Geom {
   static constexpr unsigned SMEM = ((USED > FLOOR ? USED : FLOOR) + 127u) / 128u * 128u;
   static constexpr unsigned IDA = idesc_bf16(128, KA, false), IDB = idesc_bf16(128, KB, true);
   static_assert(KB <= 64 && MT * KA == KB, "tensor-memory map");
-  static_assert(2 * TILE_A <= 2 * OPB_HALF && LAND % 128 == 0 && HS <= 256 && L <= 256, "shared-memory map");
+  static_assert(2 * TILE_A <= 2 * OPB_HALF && OPA_BYTES == 2 * OPB_HALF && LAND % 128 == 0 && HS <= 256 && L <= 256,
+                "shared-memory map");
   static_assert(SMEM <= 232448, "shared memory");
 };
 
@@ -234,10 +238,11 @@ __device__ __forceinline__ unsigned char *kmajor(unsigned char *p, int r, int k,
 // b) whose outputs sit in this warp's lanes from tensor-memory address taddr
 // (re c at column c, im at R1 + c): the half h of them, c in [h R1/2,
 // (h+1) R1/2), twiddled by w^(b c) and written as column (p R2 + b) of the
-// MN-major rows (grp R1 + c).  Warp-collective (the load); `store` = the row
-// is real.
+// MN-major rows (grp R1 + c) of the stage-B operand at byte offset opb.
+// Warp-collective (the load); `store` = the row is real.
 template <int N>
-__device__ __forceinline__ void stage_b_half(unsigned char *sm, unsigned taddr, int grp, int b, int h, bool store) {
+__device__ __forceinline__ void stage_b_half(unsigned char *sm, unsigned opb, unsigned taddr, int grp, int b, int h,
+                                             bool store) {
   using G = Geom<N>;
   constexpr int R1 = G::R1, R2 = G::R2, CH = R1 / 2;
   float vr[CH], vi[CH];
@@ -249,7 +254,7 @@ __device__ __forceinline__ void stage_b_half(unsigned char *sm, unsigned taddr, 
   float yr[CH], yi[CH];
 #pragma unroll
   for (int i = 0; i < CH; ++i) {
-    const float2 w = tws[b * (h * CH + i)];  // exp(+2 pi i b c / N)
+    const float2 w = tws[(h * CH + i) * R2 + b];  // exp(+2 pi i b c / N)
     yr[i] = fmaf(vr[i], w.x, -(vi[i] * w.y));
     yi[i] = fmaf(vi[i], w.x, vr[i] * w.y);
   }
@@ -257,13 +262,14 @@ __device__ __forceinline__ void stage_b_half(unsigned char *sm, unsigned taddr, 
 #pragma unroll
   for (int p = 0; p < 2; ++p) {
     const int kp = p * R2 + b;
-    unsigned char *dst = sm + G::OPB + (kp >> 3) * 2048 + (kp & 7) * 16 + (m0 >> 3) * 128 + (m0 & 7) * 2;
+    unsigned char *dst = sm + opb + (kp >> 3) * 2048 + (kp & 7) * 16 + (m0 >> 3) * 128 + (m0 & 7) * 2;
     put_run<CH>(dst, G::OPB_HALF, p ? yi : yr);
   }
 }
 
 // Stage-A MMAs of the operand tile at byte offset tile_off into tensor-memory
-// column col; stage-B MMAs into col.  Issued by one thread.
+// column col; stage-B MMAs of the operand at byte offset opb into col.
+// Issued by one thread.
 template <int N>
 __device__ __forceinline__ void issue_a(unsigned sbase, unsigned tmem, unsigned tile_off, unsigned col) {
   using G = Geom<N>;
@@ -277,13 +283,13 @@ __device__ __forceinline__ void issue_a(unsigned sbase, unsigned tmem, unsigned 
     }
 }
 template <int N>
-__device__ __forceinline__ void issue_b(unsigned sbase, unsigned tmem, unsigned col) {
+__device__ __forceinline__ void issue_b(unsigned sbase, unsigned tmem, unsigned opb, unsigned col) {
   using G = Geom<N>;
 #pragma unroll
   for (int pr = 0; pr < 3; ++pr)
 #pragma unroll
     for (int q = 0; q < G::KB / 16; ++q) {
-      const unsigned a = sbase + G::OPB + (pr == 2 ? G::OPB_HALF : 0) + q * 4096;
+      const unsigned a = sbase + opb + (pr == 2 ? G::OPB_HALF : 0) + q * 4096;
       const unsigned b = sbase + G::FB + (pr == 1 ? G::FB_HALF : 0) + q * 256;
       mma(tmem + col, sdesc(a, 2048, 128), sdesc(b, 128, G::KB * 16), G::IDB, (pr | q) != 0);
     }
@@ -338,7 +344,7 @@ __global__ void __launch_bounds__(kThreads, 2)
   for (unsigned i = tid; i < G::MATS_BYTES / 16; i += kThreads)
     reinterpret_cast<uint4 *>(sm + G::FA)[i] = __ldg(mats + i);
   for (unsigned i = tid; i < G::TW_BYTES / 8; i += kThreads) {
-    const float2 w = __ldg(tw + i);  // exp(-2 pi i j / N): store the conjugate
+    const float2 w = __ldg(tw + (i / R2) * (i % R2));  // exp(-2 pi i b c / N), b c < N: store the conjugate
     reinterpret_cast<float2 *>(sm + G::TW)[i] = make_float2(w.x, -w.y);
   }
   if (warp == 0) tmem_alloc(&tslot, G::TCOLS);
@@ -447,12 +453,12 @@ __global__ void __launch_bounds__(kThreads, 2)
 #pragma unroll
       for (int j = 0; j < MT; ++j) {
         const int ra = row + 128 * j;
-        stage_b_half<N>(sm, tlane + G::GA + j * KA, ra / R2, ra % R2, h, true);
+        stage_b_half<N>(sm, G::OPB, tlane + G::GA + j * KA, ra / R2, ra % R2, h, true);
       }
       NS_TC_PUBLISH_OR_LEAVE
       if (tid == 0) {
         fence_after();
-        issue_b<N>(sbase, tmem, G::T1 + pp * G::KB);
+        issue_b<N>(sbase, tmem, G::OPB, G::T1 + pp * G::KB);
         commit(&bars[1]);
       }
     }
@@ -546,36 +552,31 @@ __global__ void __launch_bounds__(kThreads, 2)
     }
     wait_a();
     // ------------------------------------------------ forward stage B ------
+    // (n_x, n_y) pairs into OPB, n_z pairs into OPA (both stage-A operands
+    // have been read: stage A has completed)
 #pragma unroll
     for (int j = 0; j < MT; ++j) {
       const int ra = row + 128 * j;
-      stage_b_half<N>(sm, tlane + G::GA + j * KA, ra / R2, ra % R2, h, true);
+      stage_b_half<N>(sm, G::OPB, tlane + G::GA + j * KA, ra / R2, ra % R2, h, true);
     }
+    stage_b_half<N>(sm, G::OPA, tlane + G::T3, row / R2, row % R2, h, row < 64 * MT);
     NS_TC_PUBLISH_OR_LEAVE
     if (tid == 0) {
       fence_after();
-      issue_b<N>(sbase, tmem, G::T1);
-      commit(&bars[1]);
-    }
-    wait_b();  // the n_x, n_y stage B has read the operand
-    stage_b_half<N>(sm, tlane + G::T3, row / R2, row % R2, h, row < 64 * MT);
-    NS_TC_PUBLISH_OR_LEAVE
-    if (tid == 0) {
-      fence_after();
-      issue_b<N>(sbase, tmem, G::T2);
+      issue_b<N>(sbase, tmem, G::OPB, G::T1);
+      issue_b<N>(sbase, tmem, G::OPA, G::T2);
       commit(&bars[1]);
     }
     // ----------------------------------------------------------- outputs ---
+    wait_b();
     // F1 rows (line, c): half 0 stores n_x, half 1 n_y
     split_store<N>(tlane + G::T1, c, lane, h == 1, true, yb + h * fs + (line0 + line) * hs);
-    wait_b();
     // F2 rows (q, c), q < L / 2 (lanes 0..63): half 0 stores n_z of line 2q, half 1 of line 2q + 1
     if ((warp & 3) < 2) split_store<N>(tlane + G::T2, c, lane, h == 1, true, yb + 2 * fs + (line0 + 2 * line + h) * hs);
-    if (__syncthreads_or(bad)) {
-      failed = true;
-      goto out;
-    }
+    // the next tile's first publish orders these tensor-memory reads before
+    // its MMAs and catches a wait that gave up
   }
+  if (__syncthreads_or(bad)) failed = true;
 #undef NS_TC_PUBLISH_OR_LEAVE
 out:
   if (umax != nullptr) {

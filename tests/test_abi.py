@@ -47,8 +47,15 @@ def test_sizes(ns):
     assert (s["kc"], s["c"], s["h"], s["nbins"]) == (42, 85, 43, 60)
 
 
+def test_tensor_core_precision_grids(ns):
+    # NS_FP32_TC: 3D grids with a tensor-core x pass (64 .. 512) share the FP32 sizes
+    for n in (64, 128, 256, 512):
+        assert ns.ns_sizes(3, n, ns.NS_FP32_TC) == ns.ns_sizes(3, n, ns.NS_FP32)
+
+
 @pytest.mark.parametrize("dim,n,prec,code", [(4, 64, 1, -1), (3, 100, 1, -1), (3, 8, 1, -4), (3, 2048, 1, -4),
-                                              (2, 4096, 1, -4), (2, 64, 7, -1)])
+                                              (2, 4096, 1, -4), (2, 64, 7, -1), (2, 256, 2, -4), (3, 32, 2, -4),
+                                              (3, 1024, 2, -4)])
 def test_bad_grids_rejected(ns, dim, n, prec, code):
     with pytest.raises(ns.NSError) as ei:
         ns.ns_sizes(dim, n, prec)
