@@ -215,7 +215,6 @@ struct Geom {
 };
 
 // -------------------------------------------------------------- kernel --
-// -------------------------------------------------------------- kernel --
 // Two threads per tensor-memory lane: thread tid serves row (tid mod 128) and
 // takes half h = tid / 128 of the row's values in every phase.
 constexpr int kThreads = 256;
