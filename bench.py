@@ -13,6 +13,9 @@ work is fixed and scaling is weak.
 
 --impl reference times the FP64 CPU oracle (the baseline this project is
 measured against) on the host cores, rank 0 only, one bounded sample per step.
+The line also carries `tensor_core`: the same workload with the x-line
+transforms on the tensor cores (precision NS_FP32_TC, split-BF16 GEMMs),
+beside the FP32 headline; `--precision tc` times that mode alone (profiling).
 """
 from __future__ import annotations
 
