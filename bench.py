@@ -447,7 +447,10 @@ def run_gb300(args):
         if ws == 1 and not args.no_paper_shapes:
             line["paper_shapes"] = paper_shapes()
         if ws == 1 and prec == ns.NS_FP32 and not args.no_tc:
-            line["tensor_core"] = tensor_core_bench(u0)
+            try:  # a side measurement: it must never cost the headline line
+                line["tensor_core"] = tensor_core_bench(u0)
+            except Exception as exc:  # noqa: BLE001
+                line["tensor_core"] = {"precision": "NS_FP32_TC", "error": f"{type(exc).__name__}: {exc}"}
         print(json.dumps(line), flush=True)
     s.close()
     if ws > 1:
