@@ -12,7 +12,11 @@ work is fixed and scaling is weak.
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
 
 --impl reference times the FP64 CPU oracle (the baseline this project is
-measured against) on the host cores, rank 0 only, one bounded sample per step.
+measured against) on the host cores, rank 0 only, on the same 512^3 workload
+(time-bounded: the line states how many steps ran).  The GPU line carries
+err_vs_fp64: the relative L2 error after 10 steps against the oracle of the
+FP32, tensor-core and FP64 forms (64^3 instance of the recipe) and of the
+ensemble (one member per grid size), each beside its stated bound.
 The line also carries `tensor_core`: the same workload with the x-line
 transforms on the tensor cores (precision NS_FP32_TC, split-BF16 GEMMs),
 beside the FP32 headline; `--precision tc` times that mode alone (profiling).
@@ -43,6 +47,8 @@ L2_NOTE = "inputs larger than L2: state 0.49 GB, pass buffers 3.6 GB vs 129 MB L
 # Algorithmic bytes of one 512^3 FP32 step for the fused three-phase model
 # (truncated spectrum, middle-axis passes counted once): 252.8 B/point.
 MODEL_BYTES_PER_POINT = 252.8
+# wall-clock bound of the reference arm's timed oracle steps (seconds)
+REF_BUDGET_S = 90.0
 
 
 def peaks():
@@ -152,19 +158,72 @@ def traffic_from_profiles(kernel: str):
     return None
 
 
-def cpu_baseline(n=256, steps=2):
-    """The FP64 oracle as it stands, on this host's cores: a bounded sample
-    (`steps` RK4 steps of the same recipe on an n^3 grid)."""
+def cpu_baseline(n=None, steps=1):
+    """The FP64 oracle as it stands, on this host's cores: a bounded sample,
+    `steps` RK4 steps of the bench recipe on the bench grid itself (one 512^3
+    step holds about 25 GB of host memory and takes ~40 s on 16 Grace cores)."""
     import oracle
     from paper_1807_01769_gb300 import inputs
 
+    n = N_GRID if n is None else n
     u0 = inputs.random_velocity_3d(n, seed=0, k0=4.0, a=2.0, energy=0.5)
     t0 = time.perf_counter()
     oracle.step(3, n, NU, DT, steps, u0)
     t = time.perf_counter() - t0
     return {"value": n ** 3 * steps / t / 1e6, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
-            "sample": f"{steps} Lawson IF-RK4 steps of the same recipe at {n}^3 in FP64 ({t:.1f} s); the 512^3 "
-                      f"step is ~{(512 // n) ** 3}x the work"}
+            "sample": f"{steps} Lawson IF-RK4 step(s) of the bench recipe at {n}^3 in FP64 ({t:.1f} s), "
+                      f"the same grid as the GPU line"}
+
+
+def _rel_l2(a, b):
+    import numpy as np
+
+    w = np.full(b.shape[-1], 2.0)
+    w[0] = 1.0
+    return float(np.sqrt(np.sum(w * np.abs(a - b) ** 2) / np.sum(w * np.abs(b) ** 2)))
+
+
+# error bounds each precision states after 10 steps against the FP64 oracle
+ERR_TOL = {"fp32": 1e-5, "fp32_tc": 1e-3, "fp64": 1e-11, "ensemble_fp32": 1e-5}
+
+
+def err_vs_fp64(steps=10, n=64):
+    """Relative L2 error (half-spectrum weights, i.e. the physical L2 error by
+    Parseval) after `steps` steps against the FP64 oracle, outside the timed
+    region: the 3D forms on the n^3 instance of the bench recipe (same seed,
+    nu, dt), the ensemble on one member of each of its grid sizes (2D recipe of
+    the ensemble line, seeds = member indices)."""
+    import oracle
+    from paper_1807_01769_gb300 import inputs, ns
+
+    out = {}
+    u0 = inputs.random_velocity_3d(n, seed=0, k0=4.0, a=2.0, energy=0.5)
+    ref = oracle.step(3, n, NU, DT, steps, u0)
+    for name, prec in (("fp32", ns.NS_FP32), ("fp32_tc", ns.NS_FP32_TC), ("fp64", ns.NS_FP64)):
+        with ns.Solver(3, n, prec, nu=NU, dt=DT) as s:
+            s.set_state_spectral(u0)
+            s.step(steps)
+            err = _rel_l2(s.get_state_spectral(), ref)
+        out[name] = {"rel_l2": err, "tol": ERR_TOL[name], "ok": err <= ERR_TOL[name], "grid": f"{n}^3",
+                     "steps": steps}
+    sizes = inputs.ensemble_sizes(64)
+    members = [sizes.index(m) for m in (128, 256, 512) if m in sizes]
+    ens = []
+    with ns.Ensemble([sizes[m] for m in members], ns.NS_FP32, nu=5e-4, dt=5e-4, autotune=False) as e:
+        w0 = [inputs.random_vorticity_2d(sizes[m], seed=m, k0=8.0, a=2.0, energy=0.5) for m in members]
+        for j, w in enumerate(w0):
+            e.set_state_spectral(j, w)
+        e.step(steps)
+        for j, m in enumerate(members):
+            nm = sizes[m]
+            err = _rel_l2(e.get_state_spectral(j), oracle.step(2, nm, 5e-4, 5e-4, steps, w0[j]))
+            ens.append({"member": m, "grid": f"{nm}^2", "rel_l2": err})
+    worst = max(x["rel_l2"] for x in ens)
+    out["ensemble_fp32"] = {"rel_l2": worst, "tol": ERR_TOL["ensemble_fp32"], "ok": worst <= ERR_TOL["ensemble_fp32"],
+                            "steps": steps, "members": ens}
+    out["note"] = (f"{steps} steps vs the FP64 oracle; 3D forms on the {n}^3 instance of the bench recipe, the "
+                   "ensemble on one member of each size")
+    return out
 
 
 ENSEMBLE_WORKLOAD = ("64 independent 2D NS runs (vorticity form), sizes drawn uniformly from {128^2, 256^2, 512^2} "
@@ -303,27 +362,39 @@ def tensor_core_bench(u0, steps=20, warm=3):
 
 
 def run_reference(args):
+    """The oracle on the bench workload itself (512^3, FP64, host cores): one
+    512^3 RK4 step takes ~40 s on 16 Grace cores, so the run is bounded by
+    time: warm-up steps and timed steps stop once REF_BUDGET_S seconds have
+    gone into each (at least one timed step); the line states how many ran."""
     ws, rank, _ = dist_env()
     if rank != 0:
         return 0
     import oracle
     from paper_1807_01769_gb300 import inputs
 
-    n = 64
+    n = N_GRID
     u = inputs.random_velocity_3d(n, seed=0, k0=4.0, a=2.0, energy=0.5)
-    for _ in range(args.warmup):
-        u = oracle.step(3, n, NU, DT, 1, u)
     t0 = time.perf_counter()
-    for _ in range(args.steps):
+    warm = 0
+    while warm < args.warmup and time.perf_counter() - t0 < REF_BUDGET_S / 4:
         u = oracle.step(3, n, NU, DT, 1, u)
+        warm += 1
+    timed = 0
+    t0 = time.perf_counter()
+    while timed < max(args.steps, 1) and (timed == 0 or time.perf_counter() - t0 < REF_BUDGET_S):
+        u = oracle.step(3, n, NU, DT, 1, u)
+        timed += 1
     t = time.perf_counter() - t0
-    v = n ** 3 * args.steps / t / 1e6
+    v = n ** 3 * timed / t / 1e6
+    sample = (f"{timed} of the {args.steps} requested Lawson IF-RK4 steps of the bench workload at {n}^3 in FP64 "
+              f"timed after {warm} warm-up step(s) (time-bounded at {REF_BUDGET_S:.0f} s)")
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t / args.steps * 1e3,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "n": N_GRID, "sample_n": n, "l2": L2_NOTE},
+            "steps": timed, "warmup": warm, "requested_steps": args.steps, "requested_warmup": args.warmup,
+            "ms_per_step": t / timed * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n": n, "l2": L2_NOTE},
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
-                             "sample": f"each step is one Lawson IF-RK4 step of the same recipe at {n}^3 in FP64"},
+                             "sample": sample},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -442,6 +513,8 @@ def run_gb300(args):
         }
         if cpu is not None:
             line["cpu_baseline"] = cpu
+        if ws == 1 and not args.no_err:
+            line["err_vs_fp64"] = err_vs_fp64()
         if ws == 1 and not args.no_ensemble:
             line["ensemble"] = ensemble_bench()
         if ws == 1 and not args.no_paper_shapes:
@@ -472,6 +545,7 @@ def main():
     ap.add_argument("--precision", default="fp32", choices=["fp32", "tc"],
                     help="tc: the x-line transforms on the tensor cores (profiling; the headline is fp32)")
     ap.add_argument("--no-tc", action="store_true", help="skip the tensor-core comparison")
+    ap.add_argument("--no-err", action="store_true", help="skip the 10-step error against the FP64 oracle")
     args = ap.parse_args()
     global N_GRID
     N_GRID = args.n

@@ -298,10 +298,12 @@ int ns_f32_axpy_f64(const float *src_dev, const double *base_dev, double *dst_de
                     void *stream);
 
 /* Diagnostics for callers that cannot allocate device memory.
- * The FluidSim paper has no counterpart: this entry point exists for code that
- * must not call cudaMalloc -- a host callback, an allocator hook, a process
- * whose device memory is owned and budgeted by another framework -- but holds
- * a spectrum on the device.  It computes what ns_diagnostics and
+ * The FluidSim paper has no counterpart: this entry point exists for ordinary
+ * host code that must not call cudaMalloc -- an allocator hook, code under a
+ * memory pool that must not grow, a process whose device memory is owned and
+ * budgeted by another framework -- but holds a spectrum on the device.  It
+ * makes CUDA runtime calls and launches kernels, so it must not be called from
+ * a stream callback or a host function enqueued with cudaLaunchHostFunc.  It computes what ns_diagnostics and
  * ns_energy_spectrum compute, with the same kernels and summation order, and
  * allocates nothing: its partial sums live in a static device array of
  * NS_NOALLOC_SCRATCH_DOUBLES doubles (2 MiB) that every GPU loading the
@@ -316,9 +318,12 @@ int ns_f32_axpy_f64(const float *src_dev, const double *base_dev, double *dst_de
  * Asynchronous: returns once the work is enqueued; synchronise the stream
  * before reading out_dev.  Returns NS_OK, NS_EINVAL (null pointer, bad grid),
  * NS_EUNSUPPORTED (the grid needs more scratch than the static array holds:
- * every 2D grid fits, 3D up to n = 256), or NS_ECUDA.  The first call on a
- * device looks up the array's device address (cudaGetSymbolAddress) with that
- * device current; make that first call before any stream capture.  All calls
+ * every 2D grid fits, 3D up to n = 256), or NS_ECUDA.  Every call looks up
+ * the array's device address (cudaGetSymbolAddress) on the current device.
+ * The first call on a device loads the library module that holds the array
+ * (CUDA loads modules lazily) and so commits its 2 MiB then: make one warm-up
+ * call per device outside any region where allocation is forbidden and
+ * before any stream capture; later calls allocate nothing.  All calls
  * share the array, so calls whose kernels may overlap on the GPU (unordered
  * streams) race on it; calls on one stream are ordered and safe.  Each call
  * rewrites the scratch it reads, so nothing needs clearing in between. */

@@ -55,6 +55,7 @@ def _load():
             "orc_phys_to_state": ([I, I, P, P], I),
             "orc_state_to_phys": ([I, I, P, P], I),
             "orc_rhs": ([I, I, P, P, P], I),
+            "orc_rhs_modes": ([I, I, P, P, I, P, P], I),
             "orc_step": ([I, I, D, D, I, P, P], I),
             "orc_step_rk2": ([I, I, D, D, I, P, P], I),
             "orc_step_visc": ([I, I, D, D, D, D, I, I, P, P], I),
@@ -145,6 +146,20 @@ def rhs(dim: int, n: int, state: np.ndarray, forcing: np.ndarray | None = None) 
     f = None if forcing is None else np.ascontiguousarray(forcing, dtype=np.complex128).reshape(s.shape)
     out = np.zeros_like(s)
     _check(_load().orc_rhs(dim, n, _ptr(s), None if f is None else _ptr(f), _ptr(out)), "rhs")
+    return out
+
+
+def rhs_modes(n: int, state: np.ndarray, modes, forcing: np.ndarray | None = None) -> np.ndarray:
+    """Nonlinear term of the 3D state on selected modes by the direct Galerkin
+    sum over retained triads (no FFT): ``modes`` is a sequence of (kx, ky, kz)
+    with 0 <= kx <= kc, |ky|, |kz| <= kc; returns complex128 ``(len(modes), 3)``.
+    About c^3 triads per mode (c = 2 kc + 1), spread over the oracle's threads."""
+    s = np.ascontiguousarray(state, dtype=np.complex128).reshape(state_shape(3, n))
+    f = None if forcing is None else np.ascontiguousarray(forcing, dtype=np.complex128).reshape(s.shape)
+    k = np.ascontiguousarray(np.asarray(modes, dtype=np.int32).reshape(-1, 3))
+    out = np.zeros((k.shape[0], 3), np.complex128)
+    _check(_load().orc_rhs_modes(3, n, _ptr(s), None if f is None else _ptr(f), int(k.shape[0]), _ptr(k),
+                                 _ptr(out)), "rhs_modes")
     return out
 
 

@@ -308,6 +308,83 @@ void rhs(const Grid &g, const cd *st, const cd *forcing, cd *out) {
   }
 }
 
+// Coefficient of wavevector (px, py, pz) (every |p_i| <= kc) of the real
+// field whose truncated half spectrum is tr (one component): the stored value
+// for px > 0, the conjugate of the stored -p for px < 0, and on the px = 0
+// plane the Hermitian part (X(p) + conj X(-p)) / 2, which is what the real
+// part of the complex inverse transform keeps (irfftn above).
+cd coef(const Grid &g, const cd *tr, int px, int py, int pz) {
+  auto at = [&](int x, int y, int z) {
+    const long iz = z >= 0 ? z : z + g.c, iy = y >= 0 ? y : y + g.c;
+    return tr[(iz * g.c + iy) * g.h + x];
+  };
+  if (px > 0) return at(px, py, pz);
+  if (px < 0) return std::conj(at(-px, -py, -pz));
+  return 0.5 * (at(0, py, pz) + std::conj(at(0, -py, -pz)));
+}
+
+// Nonlinear term of selected modes by the direct Galerkin sum over retained
+// triads (3D, rotational form, the plain definition of the dealiased product):
+//   n(k) = sum_{p + q = k, |p_i|, |q_i| <= kc} u(p) x (i q x u(q)),
+//   N(k) = n(k) - k (k . n(k)) / |k|^2 + F(k),  N(0) = 0.
+// The sum over p runs one pz slab at a time; slabs are added in order, so the
+// result does not depend on the thread count.
+void rhs_modes(const Grid &g, const cd *st, const cd *forcing, int nk, const int *kidx, cd *out) {
+  const long nt = (long)g.ntrunc();
+  const int kc = g.kc, c = g.c;
+  const cd I(0.0, 1.0);
+  std::vector<cd> part((size_t)nk * c * 3);
+#pragma omp parallel for collapse(2) schedule(dynamic)
+  for (int s = 0; s < nk; ++s) {
+    for (int sz = 0; sz < c; ++sz) {
+      const int kx = kidx[3 * s], ky = kidx[3 * s + 1], kz = kidx[3 * s + 2];
+      const int pz = sz - kc, qz = kz - pz;
+      cd acc[3] = {0.0, 0.0, 0.0};
+      if (std::abs(qz) <= kc) {
+        for (int py = std::max(-kc, ky - kc); py <= std::min(kc, ky + kc); ++py) {
+          const int qy = ky - py;
+          for (int px = std::max(-kc, kx - kc); px <= std::min(kc, kx + kc); ++px) {
+            const int qx = kx - px;
+            const cd ux = coef(g, st, px, py, pz), uy = coef(g, st + nt, px, py, pz),
+                     uz = coef(g, st + 2 * nt, px, py, pz);
+            const cd vx = coef(g, st, qx, qy, qz), vy = coef(g, st + nt, qx, qy, qz),
+                     vz = coef(g, st + 2 * nt, qx, qy, qz);
+            // omega(q) = i q x u(q)
+            const cd wx = I * ((double)qy * vz - (double)qz * vy);
+            const cd wy = I * ((double)qz * vx - (double)qx * vz);
+            const cd wz = I * ((double)qx * vy - (double)qy * vx);
+            acc[0] += uy * wz - uz * wy;
+            acc[1] += uz * wx - ux * wz;
+            acc[2] += ux * wy - uy * wx;
+          }
+        }
+      }
+      for (int a = 0; a < 3; ++a) part[((size_t)s * c + sz) * 3 + a] = acc[a];
+    }
+  }
+  for (int s = 0; s < nk; ++s) {
+    const int kx = kidx[3 * s], ky = kidx[3 * s + 1], kz = kidx[3 * s + 2];
+    cd nv[3] = {0.0, 0.0, 0.0};
+    for (int sz = 0; sz < c; ++sz)
+      for (int a = 0; a < 3; ++a) nv[a] += part[((size_t)s * c + sz) * 3 + a];
+    const double k2 = (double)kx * kx + (double)ky * ky + (double)kz * kz;
+    if (k2 == 0.0) {
+      out[3 * s] = out[3 * s + 1] = out[3 * s + 2] = 0.0;
+      continue;
+    }
+    const cd kn = ((double)kx * nv[0] + (double)ky * nv[1] + (double)kz * nv[2]) / k2;
+    nv[0] -= (double)kx * kn;
+    nv[1] -= (double)ky * kn;
+    nv[2] -= (double)kz * kn;
+    if (forcing) {
+      const long iz = kz >= 0 ? kz : kz + c, iy = ky >= 0 ? ky : ky + c;
+      const long i = (iz * c + iy) * g.h + kx;
+      for (int a = 0; a < 3; ++a) nv[a] += forcing[a * nt + i];
+    }
+    for (int a = 0; a < 3; ++a) out[3 * s + a] = nv[a];
+  }
+}
+
 double k2_trunc(const Grid &g, long i) {
   double k[3];
   kvec_trunc(g, i, k);
@@ -390,6 +467,23 @@ int orc_rhs(int dim, int n, const double *state, const double *forcing, double *
   if ((dim != 2 && dim != 3) || !is_pow2(n) || n < 4) return -1;
   rhs(Grid(dim, n), reinterpret_cast<const cd *>(state), reinterpret_cast<const cd *>(forcing),
       reinterpret_cast<cd *>(out));
+  return 0;
+}
+
+// Nonlinear term N(state) (+ forcing, nullable) of nk selected modes by the
+// direct Galerkin sum (3D only).  kidx holds nk triplets (kx, ky, kz) with
+// 0 <= kx <= kc and |ky|, |kz| <= kc; out receives nk x 3 complex values
+// ordered (mode, component).  Cost: about c^3 triads per mode.
+int orc_rhs_modes(int dim, int n, const double *state, const double *forcing, int nk, const int *kidx,
+                  double *out) {
+  if (dim != 3 || !is_pow2(n) || n < 4 || nk < 0) return -1;
+  Grid g(dim, n);
+  for (int s = 0; s < nk; ++s) {
+    const int kx = kidx[3 * s], ky = kidx[3 * s + 1], kz = kidx[3 * s + 2];
+    if (kx < 0 || kx > g.kc || std::abs(ky) > g.kc || std::abs(kz) > g.kc) return -1;
+  }
+  rhs_modes(g, reinterpret_cast<const cd *>(state), reinterpret_cast<const cd *>(forcing), nk, kidx,
+            reinterpret_cast<cd *>(out));
   return 0;
 }
 

@@ -2,19 +2,25 @@
 // (energy, enstrophy, shell spectrum) for callers that cannot allocate device
 // memory themselves.
 //
-// Who needs it: code that runs where cudaMalloc is off limits -- inside a
-// host callback or a custom allocator's hook, under a memory pool that must
-// not grow, or in a process whose device memory is owned and budgeted by
-// another framework.  Such a caller already holds the spectrum and an output
-// buffer; the only device memory the reduction needs beyond them is the
-// per-block partial sums, and here that scratch is a fixed array compiled into
-// the library.
+// Who needs it: ordinary host code that must not call cudaMalloc -- a custom
+// allocator's hook, code running under a memory pool that must not grow, or a
+// process whose device memory is owned and budgeted by another framework.
+// Such a caller already holds the spectrum and an output buffer; the only
+// device memory the reduction needs beyond them is the per-block partial sums,
+// and here that scratch is a fixed array compiled into the library.  The call
+// itself makes CUDA runtime calls and launches kernels, so it cannot be made
+// from a stream callback or a host function enqueued with cudaLaunchHostFunc.
 //
 // The array is file-scope device memory: every GPU that loads the library
 // holds NS_NOALLOC_SCRATCH_DOUBLES doubles (2 MiB) for the life of the
-// process.  In host code its name is only a host-side stand-in, never a device
-// address, so its address is looked up with cudaGetSymbolAddress once per
-// device, with that device current, on the first call made on that device.
+// process.  With CUDA's lazy module loading the module that holds it is
+// loaded, and those 2 MiB committed, on its first use on a device: the first
+// call on each device is a warm-up to make outside any region where
+// allocation is forbidden and before any stream capture.  In host code the
+// array's name is only a host-side stand-in, never a device address, so every
+// call looks up the device address with cudaGetSymbolAddress, with the
+// calling device current (cheap next to the two launches, and never stale
+// after a device reset reloads the module).
 // Every call shares the array.  Each block overwrites its own partial row
 // before the final pass reads it, so nothing has to be cleared between calls,
 // but two calls whose kernels overlap on the GPU (different streams, no
@@ -22,7 +28,6 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
-#include <mutex>
 
 #include "ns.h"
 #include "ns_internal.h"
@@ -30,10 +35,6 @@
 namespace {
 
 static __device__ __align__(256) double g_noalloc_scratch[NS_NOALLOC_SCRATCH_DOUBLES];
-
-constexpr int kMaxDevices = 64;
-std::mutex g_mu;
-double *g_scratch_ptr[kMaxDevices] = {nullptr};
 
 bool is_pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
 
@@ -58,21 +59,9 @@ extern "C" int ns_diagnostics_noalloc(const ns_grid *grid, const void *spec_dev,
   const int nbins = (int)std::floor(std::sqrt((double)g.dim * g.kc * g.kc) + 0.5) + 1;
   const long long need = nsk::diag_scratch_doubles(g, nbins);
   if (need > NS_NOALLOC_SCRATCH_DOUBLES) return NS_EUNSUPPORTED;  // grid too large for the static scratch
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return NS_ECUDA;
-  if (dev < 0 || dev >= kMaxDevices) return NS_EUNSUPPORTED;
-  double *scratch = nullptr;
-  {
-    std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_scratch_ptr[dev]) {
-      void *p = nullptr;
-      e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-      if (e != cudaSuccess) return NS_ECUDA;
-      g_scratch_ptr[dev] = static_cast<double *>(p);
-    }
-    scratch = g_scratch_ptr[dev];
-  }
+  void *p = nullptr;
+  if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess) return NS_ECUDA;
+  double *scratch = static_cast<double *>(p);
   const int rc = nsk::diagnostics(grid->precision, g, spec_dev, nbins, scratch, out_dev, (cudaStream_t)cuda_stream);
   if (rc != 0) return NS_ECUDA;
   return NS_OK;

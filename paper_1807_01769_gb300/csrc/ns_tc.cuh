@@ -359,6 +359,11 @@ __global__ void __launch_bounds__(kThreads, 2)
   const unsigned tlane = tmem + ((unsigned)((warp & 3) * 32) << 16);  // this warp's lanes
   unsigned pha = 0, phb = 0, pht = 0;
   bool bad = false, tma_pending = false, failed = false;
+  // a commit to bars[0] / bars[1] whose completion this thread has not seen,
+  // and the parity of the phase that completes it (drained before the
+  // tensor memory is freed on the failure path)
+  bool pend_a = false, pend_b = false;
+  unsigned par_a = 0, par_b = 0;
   const float2 *land = reinterpret_cast<const float2 *>(sm + G::LAND);
   const long long nn = (long long)N * N;  // lines per field
   // one thread: the spectral rows of fields f, f + 1 of the tile's lines into LAND
@@ -371,14 +376,27 @@ __global__ void __launch_bounds__(kThreads, 2)
   tma_pending = (long long)blockIdx.x < tiles;
   // stage A done -> its results; stage B done -> its results or a free operand
   auto wait_a = [&]() {
-    bad |= !wait_phase(&bars[0], pha);
+    const bool ok = wait_phase(&bars[0], pha);
+    bad |= !ok;
+    pend_a = pend_a && !ok;
     pha ^= 1u;
     fence_after();
   };
   auto wait_b = [&]() {
-    bad |= !wait_phase(&bars[1], phb);
+    const bool ok = wait_phase(&bars[1], phb);
+    bad |= !ok;
+    pend_b = pend_b && !ok;
     phb ^= 1u;
     fence_after();
+  };
+  // every thread notes each commit (the issuing thread is thread 0)
+  auto note_a = [&]() {
+    pend_a = true;
+    par_a = pha;
+  };
+  auto note_b = [&]() {
+    pend_b = true;
+    par_b = phb;
   };
   auto wait_t = [&]() {
     bad |= !wait_phase(&bars[2], pht);
@@ -446,6 +464,7 @@ __global__ void __launch_bounds__(kThreads, 2)
           }
         }
         tma_pending = more;
+        note_a();
       }
       wait_a();
       if (pp > 0) wait_b();  // the previous pair's stage B has read the operand
@@ -460,6 +479,7 @@ __global__ void __launch_bounds__(kThreads, 2)
         issue_b<N>(sbase, tmem, G::OPB, G::T1 + pp * G::KB);
         commit(&bars[1]);
       }
+      note_b();
     }
     wait_b();
     // ------------------------------------- product, forward stage-A rows --
@@ -549,6 +569,7 @@ __global__ void __launch_bounds__(kThreads, 2)
       issue_a<N>(sbase, tmem, G::OPB, G::T3);
       commit(&bars[0]);
     }
+    note_a();
     wait_a();
     // ------------------------------------------------ forward stage B ------
     // (n_x, n_y) pairs into OPB, n_z pairs into OPA (both stage-A operands
@@ -566,6 +587,7 @@ __global__ void __launch_bounds__(kThreads, 2)
       issue_b<N>(sbase, tmem, G::OPA, G::T2);
       commit(&bars[1]);
     }
+    note_b();
     // ----------------------------------------------------------- outputs ---
     wait_b();
     // F1 rows (line, c): half 0 stores n_x, half 1 n_y
@@ -591,6 +613,10 @@ out:
   if (failed) {
     if (tid == 0) atomicExch(err, 2);
     if (tma_pending) wait_phase(&bars[2], pht);  // let a copy in flight land before the block leaves
+    // MMAs this thread has not seen complete may still write tensor memory:
+    // give each one a last bounded wait before the memory is freed
+    if (pend_a) wait_phase(&bars[0], par_a);
+    if (pend_b) wait_phase(&bars[1], par_b);
   }
   fence_before();
   __syncthreads();

@@ -98,17 +98,16 @@ def random_vorticity_2d(n: int, seed: int, k0: float = 8.0, a: float = 1.0, ener
     return np.ascontiguousarray(w.astype(np.complex128))
 
 
-def random_velocity_3d(n: int, seed: int, k0: float = 4.0, a: float = 2.0, energy: float = 0.5) -> np.ndarray:
-    """Truncated 3D solenoidal velocity spectrum, |u_hat| ~ sqrt(E(k))/k with
-    E(k) ~ k^4 exp(-a (k/k0)^2).  Each mode is a random combination of two unit
-    vectors perpendicular to k with random phases, so k . u_hat = 0 holds by
-    construction; Hermitian on kx = 0; zero mean; mean energy = ``energy``."""
-    kx, ky, kz = wavenumbers(n, 3)
+def _solenoidal_modes(kx, ky, kz, seed: int, amp_of_k):
+    """Random solenoidal coefficients on the given modes (arrays of equal
+    shape): each mode is amp(|k|) (cos a e^{i p1} e1 + sin a e^{i p2} e2) with
+    e1, e2 an orthonormal pair perpendicular to the canonical k; modes of the
+    kx = 0 plane take the conjugate of their canonical partner, so that plane
+    is Hermitian; the k = 0 mode is zero.  Returns (3, ...) complex128."""
     kxc, kyc, kzc, flip = _canonical(kx, ky, kz)
     kv = np.stack([kxc, kyc, kzc]).astype(np.float64)
     k2 = (kv ** 2).sum(0)
     k = np.sqrt(k2)
-    # orthonormal pair perpendicular to the canonical k
     kperp = np.sqrt(kv[0] ** 2 + kv[1] ** 2)
     on_axis = kperp == 0
     safe = np.where(on_axis, 1.0, kperp)
@@ -120,18 +119,50 @@ def random_velocity_3d(n: int, seed: int, k0: float = 4.0, a: float = 2.0, energ
                    kv[2] * e1[0] - kv[0] * e1[2],
                    kv[0] * e1[1] - kv[1] * e1[0]]) / ksafe
     e2 = np.where(on_axis[None], np.stack([np.zeros_like(k), np.ones_like(k), np.zeros_like(k)]), e2)
-    amp = np.sqrt(k4_gauss_spectrum(k, k0, a)) / ksafe
+    amp = amp_of_k(k, ksafe)
     p1 = 2.0 * np.pi * uniform01(seed, kxc, kyc, kzc, 1)
     p2 = 2.0 * np.pi * uniform01(seed, kxc, kyc, kzc, 2)
     al = 2.0 * np.pi * uniform01(seed, kxc, kyc, kzc, 3)
     u = amp * (np.cos(al) * np.exp(1j * p1) * e1 + np.sin(al) * np.exp(1j * p2) * e2)
     u = np.where(flip[None], np.conj(u), u)
     u[:, k2 == 0] = 0.0
+    return u
+
+
+def random_velocity_3d(n: int, seed: int, k0: float = 4.0, a: float = 2.0, energy: float = 0.5) -> np.ndarray:
+    """Truncated 3D solenoidal velocity spectrum, |u_hat| ~ sqrt(E(k))/k with
+    E(k) ~ k^4 exp(-a (k/k0)^2).  Each mode is a random combination of two unit
+    vectors perpendicular to k with random phases, so k . u_hat = 0 holds by
+    construction; Hermitian on kx = 0; zero mean; mean energy = ``energy``."""
+    kx, ky, kz = wavenumbers(n, 3)
+    u = _solenoidal_modes(kx, ky, kz, seed, lambda k, ksafe: np.sqrt(k4_gauss_spectrum(k, k0, a)) / ksafe)
     weight = np.where(kx == 0, 1.0, 2.0)
     e = np.sum(weight * 0.5 * (np.abs(u) ** 2).sum(0))
     if e > 0:
         u *= np.sqrt(energy / e)
     return np.ascontiguousarray(u.astype(np.complex128))
+
+
+def random_velocity_3d_flat(n: int, seed: int, energy: float = 0.5, planes: int = 16) -> np.ndarray:
+    """Truncated 3D solenoidal velocity spectrum with the same modulus on every
+    retained mode but k = 0 (a flat, white spectrum up to the 2/3 cut-off), so
+    every retained row of every axis carries energy.  Random phases and
+    directions as in random_velocity_3d (same generator, same keys); built
+    ``planes`` kz rows at a time so that 1024^3 grids stay within a few GB of
+    temporaries; mean energy = ``energy``."""
+    kc, c, h = truncation(n)
+    u = np.empty((3, c, c, h), np.complex128)
+    i = np.arange(c)
+    kfull = np.where(i <= kc, i, i - c)
+    e = 0.0
+    for z0 in range(0, c, planes):
+        kz, ky, kx = np.meshgrid(kfull[z0:z0 + planes], kfull, np.arange(h), indexing="ij")
+        blk = _solenoidal_modes(kx, ky, kz, seed, lambda k, ksafe: np.ones_like(k))
+        u[:, z0:z0 + planes] = blk
+        e += float(np.sum(np.where(kx == 0, 1.0, 2.0) * 0.5 * (np.abs(blk) ** 2).sum(0)))
+    if e > 0:
+        u *= np.sqrt(energy / e)
+    return u
 
 
 def grid_coords(n: int):

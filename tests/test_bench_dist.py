@@ -61,7 +61,7 @@ def test_single_rank_needs_no_process_group():
 @pytest.mark.parametrize("rank", [0, 1])
 def test_reference_arm_prints_on_rank_zero_only(rank):
     env = dict(os.environ, RANK=str(rank), LOCAL_RANK=str(rank), WORLD_SIZE="2", MASTER_ADDR="127.0.0.1")
-    r = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--gpus", "2", "--steps", "1",
+    r = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--gpus", "2", "--n", "32", "--steps", "1",
                         "--warmup", "0"], cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
     assert r.returncode == 0, r.stderr
     lines = [x for x in r.stdout.splitlines() if x.strip()]

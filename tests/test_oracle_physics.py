@@ -114,6 +114,61 @@ def test_rhs_3d_equals_galerkin_sum(orc):
     assert np.abs(got - ref).max() <= 1e-13 * np.abs(ref).max()
 
 
+def _all_modes(n):
+    kc, c, h = inputs.truncation(n)
+    return [(kx, ky, kz) for kz in range(-kc, kc + 1) for ky in range(-kc, kc + 1) for kx in range(h)]
+
+
+def _at(trunc, n, modes):
+    kc, c, h = inputs.truncation(n)
+    return np.array([[trunc[a, kz % c, ky % c, kx] for a in range(3)] for kx, ky, kz in modes])
+
+
+def test_rhs_modes_equals_galerkin_sum(orc):
+    # the oracle's sampled direct sum against the independent numpy sum
+    n = 8
+    u = inputs.random_velocity_3d(n, seed=9, k0=1.5)
+    modes = _all_modes(n)
+    got = orc.rhs_modes(n, u, modes)
+    ref = _at(galerkin_rhs_3d(u, n), n, modes)
+    assert np.abs(ref).max() > 1e-3
+    assert np.abs(got - ref).max() <= 1e-13 * np.abs(ref).max()
+
+
+def test_rhs_modes_equals_fft_rhs_with_forcing_and_non_hermitian_plane(orc):
+    # two algorithms for one definition: the direct triad sum and the
+    # pseudo-spectral product; the kx = 0 plane is deliberately not Hermitian
+    # (both take its Hermitian part, the real part of the inverse transform)
+    n = 16
+    rng = np.random.default_rng(4)
+    shape = orc.state_shape(3, n)
+    u = rng.standard_normal(shape) + 1j * rng.standard_normal(shape)
+    f = rng.standard_normal(shape) + 1j * rng.standard_normal(shape)
+    modes = _all_modes(n)
+    got = orc.rhs_modes(n, u, modes, f)
+    ref = _at(orc.rhs(3, n, u, f), n, modes)
+    assert np.abs(got - ref).max() <= 1e-12 * np.abs(ref).max()
+
+
+def test_rhs_modes_single_triad_closed_form(orc):
+    # u holds two modes p and q (with their conjugates): at k = p + q only the
+    # triads (p, q) and (q, p) contribute, N(k) = P(k)[u_p x (i q x u_q) + u_q x (i p x u_p)]
+    n = 16
+    p, q = np.array([1, 2, 0]), np.array([2, -1, 1])
+    up, uq = np.array([0.3 + 0.1j, -0.2j, 0.5]), np.array([0.1, 0.4 - 0.3j, -0.25j])
+    kc, c, h = inputs.truncation(n)
+    u = np.zeros(orc.state_shape(3, n), np.complex128)
+    u[:, p[2] % c, p[1] % c, p[0]] = up
+    u[:, q[2] % c, q[1] % c, q[0]] = uq
+    k = p + q
+    nv = np.cross(up, np.cross(1j * q, uq)) + np.cross(uq, np.cross(1j * p, up))
+    nv = nv - k * (k @ nv) / (k @ k)
+    got = orc.rhs_modes(n, u, [tuple(int(x) for x in k)])[0]
+    assert np.abs(got - nv).max() < 1e-15
+    with pytest.raises(ValueError):
+        orc.rhs_modes(n, u, [(-1, 0, 0)])  # kx must be in 0..kc
+
+
 def test_rhs_3d_divergence_free(orc):
     n = 16
     u = inputs.random_velocity_3d(n, seed=2, k0=3.0)

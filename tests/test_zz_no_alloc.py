@@ -1,9 +1,11 @@
-"""ns_diagnostics_noalloc, the diagnostics entry point for callers that cannot
-allocate device memory (a host callback, an allocator hook, a process whose
-device memory belongs to another framework): called through the C ABI on a
-spectrum the caller holds on the device, twice in a row, it must give what
-the allocating entry points ns_diagnostics / ns_energy_spectrum give for the
-same state.  Its scratch is a static device array shared by every call."""
+"""ns_diagnostics_noalloc, the diagnostics entry point for host code that
+cannot allocate device memory (an allocator hook, a process whose device
+memory belongs to another framework): called through the C ABI on a spectrum
+the caller holds on the device, twice in a row, it must give what the
+allocating entry points ns_diagnostics / ns_energy_spectrum give for the same
+state.  Its scratch is a static device array shared by every call; the first
+call on a device loads the module that holds it, and the second call must
+leave the device's free memory unchanged."""
 import ctypes
 
 import numpy as np
@@ -39,9 +41,13 @@ def test_noalloc_matches_allocating_entry_points(dim, n, prec):
     out = torch.full((nb + 2,), float("nan"), dtype=torch.float64, device="cuda")
     grid = ns.ns_grid(dim, n, prec)
     stream = torch.cuda.current_stream().cuda_stream
-    for _ in range(2):
+    for i in range(2):
+        torch.cuda.synchronize()
+        free0 = torch.cuda.mem_get_info()[0]
         assert _call(ns, grid, dev.data_ptr(), out.data_ptr(), stream) == ns.NS_OK
         torch.cuda.synchronize()
+        if i == 1:  # after the warm-up call: nothing is allocated on the device
+            assert torch.cuda.mem_get_info()[0] == free0
         got = out.cpu().numpy()
         assert abs(got[0] - e_ref) <= REL * e_ref
         assert abs(got[1] - om_ref) <= REL * om_ref
