@@ -249,15 +249,21 @@ struct StagePlan {
   static constexpr int TWOFF = stage_tw_offset(L, S);
 };
 
-// Synchronisation scope of the exchanges: a whole block, or one warp when
-// every line exchanged lives inside that warp.
+// Synchronisation scope of the exchanges: a whole block, one warp when every
+// line exchanged lives inside that warp, or (SY >= 64, a multiple of 32) the
+// group of SY consecutive threads that owns the line, through the named
+// barrier 1 + threadIdx.x / SY (barrier 0 is the block's; at most 15 groups).
 enum SyncScope { SYNC_BLOCK = 0, SYNC_WARP = 1 };
 template <int SY>
 __device__ __forceinline__ void fft_sync() {
-  if (SY == SYNC_WARP)
+  if constexpr (SY == SYNC_WARP) {
     __syncwarp();
-  else
+  } else if constexpr (SY >= 64) {
+    static_assert(SY % 32 == 0, "named-barrier groups are whole warps");
+    asm volatile("bar.sync %0, %1;\n" ::"r"(1 + (int)threadIdx.x / SY), "n"(SY) : "memory");
+  } else {
     __syncthreads();
+  }
 }
 
 template <int L, int S, int DIR, int SY, typename C, typename SM>

@@ -91,6 +91,23 @@ __device__ __forceinline__ C ld_stream(const C *p) {
   return __ldcg(p);
 }
 
+// Asynchronous global -> shared copies of BYTES (4, 8 or 16); a false
+// predicate zero-fills the destination without reading the source.
+template <int BYTES>
+__device__ __forceinline__ void cp_async(void *dst_smem, const void *src, bool pred) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;\n" ::"r"(smem_addr(dst_smem)), "l"(src), "n"(BYTES),
+               "r"(pred ? BYTES : 0)
+               : "memory");
+}
+// 16 bytes, cached in L2 only (streamed operands that would evict L1 data).
+__device__ __forceinline__ void cp_async_cg16(void *dst_smem, const void *src, bool pred) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(smem_addr(dst_smem)), "l"(src),
+               "r"(pred ? 16 : 0)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
 __device__ __forceinline__ bool retained(int n, int N, int kc) { return n <= kc || n >= N - kc; }
 __device__ __forceinline__ int compact_of(int n, int N, int kc, int c) { return n <= kc ? n : n - (N - c); }
 __device__ __forceinline__ int kfull_of(int n, int N, int kc) { return n <= kc ? n : n - N; }
@@ -552,6 +569,186 @@ __global__ void __launch_bounds__(32 * WPB, 16 / WPB) k3_xpass_w(Geo g, long lon
   }
 }
 
+// ---------------------------------------- paired-field x pass (FP32) ---
+// Two real fields travel as one complex line z = x_a + i x_b, so each c2r or
+// r2c of length N is half of one complex FFT of length N with no half-length
+// pre- or post-processing.  A group of T = N/8 threads owns two lines (A, B)
+// and takes them in turn: the three inverse pairs (u_x, u_y), (u_z, w_x),
+// (w_y, w_z) of a line, the product n = u x w at its 8 points per thread,
+// the forward transform of n_x + i n_y, and at the end of line B the forward
+// transform of n_z[A] + i n_z[B].  The physical fields stay in registers
+// (48 values per thread).
+//
+// Slots: thread t holds index k = t + T m.  k is retained (k <= kc or
+// k >= N - kc) only for m in {0, 1, 2, 5, 6, 7} (kc < 3N/8), so slots 3 and 4
+// are zero on input and never needed on output.
+__host__ __device__ constexpr int xp_sync(int T) { return T >= 64 ? T : SYNC_WARP; }
+// per group: the double-buffered exchange line, the partner region (3T) and
+// two staging buffers of the two input rows of a pair ([2][2][xp_row(N)])
+__host__ __device__ constexpr int xp_row(int N) { return ((N - 1) / 3 + 2) / 2 * 2; }
+__host__ __device__ constexpr size_t xp_group_elems(int N) {
+  return 2 * (size_t)smline_len(N) + 3 * (N / 8) + 4 * (size_t)xp_row(N);
+}
+
+// Copy the retained part of the rows X_a, X_b of one pair (h complex each,
+// rounded up to whole 16-byte chunks; the row padding holds the extra
+// column) into a staging buffer [2][xp_row(N)], 16 bytes per cp.async.
+template <int N>
+__device__ __forceinline__ void xp_stage(float2 *st, const float2 *__restrict__ ra, const float2 *__restrict__ rb,
+                                         int t) {
+  constexpr int T = N / 8, RW = xp_row(N), CH = RW / 2;  // chunks per row
+  for (int c = t; c < 2 * CH; c += T) {
+    const int r = c / CH, q = c % CH;
+    cp_async_cg16(st + r * RW + 2 * q, (r ? rb : ra) + 2 * q, true);
+  }
+  cp_async_commit();
+}
+// z(k) = X_a(k) + i X_b(k) for k <= kc, conj X_a(N - k) + i conj X_b(N - k) for
+// k >= N - kc, zero elsewhere; at k = 0 the real parts (the real part of the
+// self-conjugate term, as the c2r of a Hermitian spectrum keeps).
+template <int N>
+__device__ __forceinline__ void xp_build(float2 (&v)[8], const float2 *st, int t, int kc) {
+  constexpr int T = N / 8, RW = xp_row(N);
+#pragma unroll
+  for (int j = 0; j < 6; ++j) {
+    const int m = j < 3 ? j : j + 2, k = t + T * m;
+    const bool ok = j < 3 ? k <= kc : k >= N - kc;
+    const int idx = j < 3 ? k : N - k;
+    float2 z = czero<float2>();
+    if (ok) {
+      const float2 a = st[idx], b = st[RW + idx];
+      z = j < 3 ? float2{a.x - b.y, a.y + b.x} : float2{a.x + b.y, b.x - a.y};
+      if (k == 0) z = float2{a.x, b.x};
+    }
+    v[m] = z;
+  }
+  v[3] = v[4] = czero<float2>();
+}
+// Split the forward transform Z of z = x_a + i x_b (v[m] = Z(t + T m)) into
+// X_a(k) = (Z(k) + conj Z(N-k))/2 and X_b(k) = (Z(k) - conj Z(N-k))/(2i) for
+// k <= kc, written to da[k], db[k].  The partners Z(N - k) (slots 5..7 of
+// other threads) go through the group's region P of 3T entries.
+template <int N, int SY>
+__device__ __forceinline__ void xp_emit(const float2 (&v)[8], int t, float2 *P, float2 *__restrict__ da,
+                                        float2 *__restrict__ db, int kc) {
+  constexpr int T = N / 8;
+#pragma unroll
+  for (int m = 5; m < 8; ++m) P[t + T * (m - 5)] = v[m];
+  fft_sync<SY>();
+#pragma unroll
+  for (int m = 0; m < 3; ++m) {
+    const int k = t + T * m;
+    if (k <= kc) {
+      const float2 zk = v[m], zm = k == 0 ? v[0] : P[3 * T - k];
+      da[k] = float2{0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y)};
+      db[k] = float2{0.5f * (zk.y + zm.y), 0.5f * (zm.x - zk.x)};
+    }
+  }
+}
+// largest |x| over the warp merged into *slot (atomic maximum on the bits of a
+// non-negative double)
+__device__ __forceinline__ void umax_merge1(float m, unsigned long long *slot) {
+  for (int off = 16; off > 0; off >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, off));
+  if ((threadIdx.x & 31) == 0) atomicMax(slot, (unsigned long long)__double_as_longlong((double)m));
+}
+
+template <int N>
+__host__ __device__ constexpr int xp_groups() {
+  return N >= 512 ? 2 : (N == 256 ? 4 : 8);
+}
+// resident blocks per SM the launch bounds ask for (512 threads per SM at
+// most 128 registers a thread)
+template <int N>
+__host__ __device__ constexpr int xp_min_blocks() {
+  return cmax(1, 512 / ((N / 8) * xp_groups<N>()));
+}
+template <int N, int GPB>
+__global__ void __launch_bounds__((N / 8) * GPB, xp_min_blocks<N>())
+    k3_xpass_p(Geo g, long long line_base, float2 *__restrict__ yb, const float2 *__restrict__ tw,
+               unsigned long long *__restrict__ umax) {
+  constexpr int T = N / 8, SY = xp_sync(T), RW = xp_row(N);
+  static_assert(GPB <= 15 || SY == SYNC_WARP, "named barriers 1..15");
+  float2 *S = dyn_smem<float2>();
+  const int grp = threadIdx.x / T, t = threadIdx.x % T;
+  float2 *gs = S + grp * xp_group_elems(N);
+  const SmLine<float2, N, true> view{gs, smline_len(N)};
+  float2 *P = gs + 2 * smline_len(N);
+  float2 *stage = P + 3 * T;  // [2 buffers][2 rows][RW]
+  const float2 *stw = tw + N;  // stage tables of the length-N transform
+  const long long lineA = line_base + ((long long)blockIdx.x * GPB + grp) * 2;
+  const long long fs = g.yb_f, hs = g.hs;
+  const int kc = g.kc;
+  // the six input pairs of the group in order: (line A, pairs 0..2), (line B, pairs 0..2)
+  auto src = [&](int i, int r) { return yb + (2 * (i % 3) + r) * fs + (lineA + i / 3) * hs; };
+  xp_stage<N>(stage, src(0, 0), src(0, 1), t);
+  float nzA[8];
+#pragma unroll 1
+  for (int ln = 0; ln < 2; ++ln) {
+    const long long line = lineA + ln;
+    float2 p0[8], p1[8], v[8];
+#pragma unroll 1
+    for (int pp = 0; pp < 3; ++pp) {
+      const int i = 3 * ln + pp;
+      // the next pair lands in the other buffer while this one is transformed
+      // (that buffer was last read before the previous transform's barriers)
+      if (i < 5) {
+        xp_stage<N>(stage + ((i + 1) & 1) * 2 * RW, src(i + 1, 0), src(i + 1, 1), t);
+        asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+      } else {
+        cp_async_wait_all();
+      }
+      fft_sync<SY>();  // every thread's copies of pair i are visible
+      xp_build<N>(v, stage + (i & 1) * 2 * RW, t, kc);
+      fft_line<N, +1, float2, SmLine<float2, N, true>, SY>(v, t, stw, view);
+      if (pp == 0) {
+        if (umax != nullptr) {
+          float mx = 0.f, my = 0.f;
+#pragma unroll
+          for (int m = 0; m < 8; ++m) {
+            mx = fmaxf(mx, fabsf(v[m].x));
+            my = fmaxf(my, fabsf(v[m].y));
+          }
+          umax_merge1(mx, umax + 0 * kUmaxSlots + blockIdx.x % kUmaxSlots);
+          umax_merge1(my, umax + 1 * kUmaxSlots + blockIdx.x % kUmaxSlots);
+        }
+#pragma unroll
+        for (int m = 0; m < 8; ++m) p0[m] = v[m];
+      } else if (pp == 1) {
+        if (umax != nullptr) {
+          float mz = 0.f;
+#pragma unroll
+          for (int m = 0; m < 8; ++m) mz = fmaxf(mz, fabsf(v[m].x));
+          umax_merge1(mz, umax + 2 * kUmaxSlots + blockIdx.x % kUmaxSlots);
+        }
+#pragma unroll
+        for (int m = 0; m < 8; ++m) p1[m] = v[m];
+      }
+    }
+    // u = (p0.x, p0.y, p1.x), w = (p1.y, v.x, v.y): n = u x w
+    float2 nxy[8];
+    float nz[8];
+#pragma unroll
+    for (int m = 0; m < 8; ++m) {
+      const float ux = p0[m].x, uy = p0[m].y, uz = p1[m].x;
+      const float wx = p1[m].y, wy = v[m].x, wz = v[m].y;
+      nxy[m] = float2{fmaf(uy, wz, -uz * wy), fmaf(uz, wx, -ux * wz)};
+      nz[m] = fmaf(ux, wy, -uy * wx);
+    }
+    fft_line<N, -1, float2, SmLine<float2, N, true>, SY>(nxy, t, stw, view);
+    xp_emit<N, SY>(nxy, t, P, yb + line * hs, yb + fs + line * hs, kc);
+    if (ln == 0) {
+#pragma unroll
+      for (int m = 0; m < 8; ++m) nzA[m] = nz[m];
+    } else {
+      float2 zz[8];
+#pragma unroll
+      for (int m = 0; m < 8; ++m) zz[m] = float2{nzA[m], nz[m]};
+      fft_line<N, -1, float2, SmLine<float2, N, true>, SY>(zz, t, stw, view);
+      xp_emit<N, SY>(zz, t, P, yb + 2 * fs + lineA * hs, yb + 2 * fs + line * hs, kc);
+    }
+  }
+}
+
 // fwd2: y forward of fields 0..nf-1 at plane z = blockIdx.y, keep retained ky;
 // the next field's loads are issued before the current field is transformed.
 template <typename R, int N, int W>
@@ -822,22 +1019,6 @@ __device__ __forceinline__ R stage_dt(const StepBufs<R> &b) {
 }
 
 
-// Asynchronous global -> shared copies of BYTES (4, 8 or 16); a false
-// predicate zero-fills the destination without reading the source.
-template <int BYTES>
-__device__ __forceinline__ void cp_async(void *dst_smem, const void *src, bool pred) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;\n" ::"r"(smem_addr(dst_smem)), "l"(src), "n"(BYTES),
-               "r"(pred ? BYTES : 0)
-               : "memory");
-}
-// 16 bytes, cached in L2 only (streamed operands that would evict L1 data).
-__device__ __forceinline__ void cp_async_cg16(void *dst_smem, const void *src, bool pred) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(smem_addr(dst_smem)), "l"(src),
-               "r"(pred ? 16 : 0)
-               : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
 // Integrating factors of a mode from the per-axis tables: exp(-nu |k|^2 dt)
 // = prod_i exp(-nu k_i^2 dt) (tables indexed by |k_i| = 0 .. kc, computed in
@@ -1409,6 +1590,10 @@ struct Launch3 {
   static constexpr int XW_LPW = XW ? 32 / (N / 16) : 1;
   static constexpr size_t SM_XW =
       (size_t)XW_WPB * (XW_LPW * xw_line_len<N, (XW_LPW > 1)>() + 3 * 8 * 32) * sizeof(C);
+  // paired-field x pass (FP32, 128 <= N <= 512)
+  static constexpr bool XP = sizeof(R) == 4 && N >= 128 && N <= 512;
+  static constexpr int XP_G = xp_groups<N>();
+  static constexpr size_t SM_XPP = (size_t)XP_G * xp_group_elems(N) * sizeof(C);
 
   static int run(int op, const Args &a, cudaStream_t s) {
     const Geo &g = a.g;
@@ -1416,6 +1601,7 @@ struct Launch3 {
     switch (op) {
       case OP_PREPARE:
         if constexpr (XW) set_smem(k3_xpass_w<R, N, XW_WPB>, SM_XW);
+        if constexpr (XP) set_smem(k3_xpass_p<N, XP_G>, SM_XPP);
         set_smem(k3_inv1<R, N, WL, true>, SM_L);
         set_smem(k3_inv1<R, N, WL, false>, SM_L);
         set_smem(k3_inv2<R, N, WYI>, SM_YI);
@@ -1455,7 +1641,11 @@ struct Launch3 {
         break;
       }
       case OP_XPASS:
-        if constexpr (XW) {
+        if constexpr (XP) {
+          const long long lines = (long long)(a.nz > 0 ? a.nz : N) * N;
+          k3_xpass_p<N, XP_G><<<(unsigned)(lines / (2 * XP_G)), (N / 8) * XP_G, SM_XPP, s>>>(
+              g, (long long)a.z0 * N, (float2 *)a.yb, (const float2 *)tw, a.umax);
+        } else if constexpr (XW) {
           const long long lines = (long long)(a.nz > 0 ? a.nz : N) * N;
           k3_xpass_w<R, N, XW_WPB><<<(unsigned)(lines / (XW_WPB * XW_LPW)), 32 * XW_WPB, SM_XW, s>>>(
               g, (long long)a.z0 * N, (C *)a.yb, tw, a.umax);
