@@ -572,12 +572,14 @@ __global__ void __launch_bounds__(32 * WPB, 16 / WPB) k3_xpass_w(Geo g, long lon
 // ---------------------------------------- paired-field x pass (FP32) ---
 // Two real fields travel as one complex line z = x_a + i x_b, so each c2r or
 // r2c of length N is half of one complex FFT of length N with no half-length
-// pre- or post-processing.  A group of T = N/8 threads owns two lines (A, B)
-// and takes them in turn: the three inverse pairs (u_x, u_y), (u_z, w_x),
-// (w_y, w_z) of a line, the product n = u x w at its 8 points per thread,
-// the forward transform of n_x + i n_y, and at the end of line B the forward
-// transform of n_z[A] + i n_z[B].  The physical fields stay in registers
-// (48 values per thread).
+// pre- or post-processing.  A group of T = N/8 threads owns two lines A, B.
+// The roundoff of a paired transform scales with the larger of its two
+// fields, so only fields of like size share one: velocity with velocity,
+// vorticity with vorticity (|w| is about |k| |u|, up to kc |u|).  Inverse:
+// (u_z[A], u_z[B]), (w_z[A], w_z[B]), then per line (u_x, u_y), (w_x, w_y)
+// and the product n = u x w at the line's 8 points per thread; forward:
+// n_x + i n_y per line, and n_z[A] + i n_z[B] at the end.  The physical
+// fields stay in registers.
 //
 // Slots: thread t holds index k = t + T m.  k is retained (k <= kc or
 // k >= N - kc) only for m in {0, 1, 2, 5, 6, 7} (kc < 3N/8), so slots 3 and 4
@@ -678,60 +680,67 @@ __global__ void __launch_bounds__((N / 8) * GPB, xp_min_blocks<N>())
   const long long lineA = line_base + ((long long)blockIdx.x * GPB + grp) * 2;
   const long long fs = g.yb_f, hs = g.hs;
   const int kc = g.kc;
-  // the six input pairs of the group in order: (line A, pairs 0..2), (line B, pairs 0..2)
-  auto src = [&](int i, int r) { return yb + (2 * (i % 3) + r) * fs + (lineA + i / 3) * hs; };
+  // the six input pairs (field, line) in order:
+  //   0: (u_z A, u_z B)  1: (w_z A, w_z B)  2: (u_x A, u_y A)  3: (w_x A, w_y A)  4, 5: as 2, 3 for B
+  auto src = [&](int i, int r) {
+    const int f = i < 2 ? 2 + 3 * i : (i % 2 == 0 ? 0 : 3) + r;
+    const long long ln = i < 2 ? lineA + r : lineA + (i - 2) / 2;
+    return yb + f * fs + ln * hs;
+  };
   xp_stage<N>(stage, src(0, 0), src(0, 1), t);
+  float2 uz[8], wz[8], v[8];
   float nzA[8];
-#pragma unroll 1
+  // the next pair lands in the other buffer while this one is transformed
+  // (that buffer was last read before the previous transform's barriers)
+  auto next_pair = [&](int i) {
+    if (i < 5) {
+      xp_stage<N>(stage + ((i + 1) & 1) * 2 * RW, src(i + 1, 0), src(i + 1, 1), t);
+      asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+    } else {
+      cp_async_wait_all();
+    }
+    fft_sync<SY>();  // every thread's copies of pair i are visible
+    xp_build<N>(v, stage + (i & 1) * 2 * RW, t, kc);
+    fft_line<N, +1, float2, SmLine<float2, N, true>, SY>(v, t, stw, view);
+  };
+  next_pair(0);
+#pragma unroll
+  for (int m = 0; m < 8; ++m) uz[m] = v[m];
+  next_pair(1);
+#pragma unroll
+  for (int m = 0; m < 8; ++m) wz[m] = v[m];
+  if (umax != nullptr) {
+    float mz = 0.f;
+#pragma unroll
+    for (int m = 0; m < 8; ++m) mz = fmaxf(mz, fmaxf(fabsf(uz[m].x), fabsf(uz[m].y)));
+    umax_merge1(mz, umax + 2 * kUmaxSlots + blockIdx.x % kUmaxSlots);
+  }
+#pragma unroll
   for (int ln = 0; ln < 2; ++ln) {
     const long long line = lineA + ln;
-    float2 p0[8], p1[8], v[8];
-#pragma unroll 1
-    for (int pp = 0; pp < 3; ++pp) {
-      const int i = 3 * ln + pp;
-      // the next pair lands in the other buffer while this one is transformed
-      // (that buffer was last read before the previous transform's barriers)
-      if (i < 5) {
-        xp_stage<N>(stage + ((i + 1) & 1) * 2 * RW, src(i + 1, 0), src(i + 1, 1), t);
-        asm volatile("cp.async.wait_group 1;\n" ::: "memory");
-      } else {
-        cp_async_wait_all();
+    next_pair(2 + 2 * ln);
+    float2 uxy[8];
+#pragma unroll
+    for (int m = 0; m < 8; ++m) uxy[m] = v[m];
+    if (umax != nullptr) {
+      float mx = 0.f, my = 0.f;
+#pragma unroll
+      for (int m = 0; m < 8; ++m) {
+        mx = fmaxf(mx, fabsf(uxy[m].x));
+        my = fmaxf(my, fabsf(uxy[m].y));
       }
-      fft_sync<SY>();  // every thread's copies of pair i are visible
-      xp_build<N>(v, stage + (i & 1) * 2 * RW, t, kc);
-      fft_line<N, +1, float2, SmLine<float2, N, true>, SY>(v, t, stw, view);
-      if (pp == 0) {
-        if (umax != nullptr) {
-          float mx = 0.f, my = 0.f;
-#pragma unroll
-          for (int m = 0; m < 8; ++m) {
-            mx = fmaxf(mx, fabsf(v[m].x));
-            my = fmaxf(my, fabsf(v[m].y));
-          }
-          umax_merge1(mx, umax + 0 * kUmaxSlots + blockIdx.x % kUmaxSlots);
-          umax_merge1(my, umax + 1 * kUmaxSlots + blockIdx.x % kUmaxSlots);
-        }
-#pragma unroll
-        for (int m = 0; m < 8; ++m) p0[m] = v[m];
-      } else if (pp == 1) {
-        if (umax != nullptr) {
-          float mz = 0.f;
-#pragma unroll
-          for (int m = 0; m < 8; ++m) mz = fmaxf(mz, fabsf(v[m].x));
-          umax_merge1(mz, umax + 2 * kUmaxSlots + blockIdx.x % kUmaxSlots);
-        }
-#pragma unroll
-        for (int m = 0; m < 8; ++m) p1[m] = v[m];
-      }
+      umax_merge1(mx, umax + 0 * kUmaxSlots + blockIdx.x % kUmaxSlots);
+      umax_merge1(my, umax + 1 * kUmaxSlots + blockIdx.x % kUmaxSlots);
     }
-    // u = (p0.x, p0.y, p1.x), w = (p1.y, v.x, v.y): n = u x w
+    next_pair(3 + 2 * ln);
+    // u = (uxy.x, uxy.y, uz), w = (v.x, v.y, wz) of this line: n = u x w
     float2 nxy[8];
     float nz[8];
 #pragma unroll
     for (int m = 0; m < 8; ++m) {
-      const float ux = p0[m].x, uy = p0[m].y, uz = p1[m].x;
-      const float wx = p1[m].y, wy = v[m].x, wz = v[m].y;
-      nxy[m] = float2{fmaf(uy, wz, -uz * wy), fmaf(uz, wx, -ux * wz)};
+      const float ux = uxy[m].x, uy = uxy[m].y, uzl = ln ? uz[m].y : uz[m].x;
+      const float wx = v[m].x, wy = v[m].y, wzl = ln ? wz[m].y : wz[m].x;
+      nxy[m] = float2{fmaf(uy, wzl, -uzl * wy), fmaf(uzl, wx, -ux * wzl)};
       nz[m] = fmaf(ux, wy, -uy * wx);
     }
     fft_line<N, -1, float2, SmLine<float2, N, true>, SY>(nxy, t, stw, view);
@@ -740,11 +749,10 @@ __global__ void __launch_bounds__((N / 8) * GPB, xp_min_blocks<N>())
 #pragma unroll
       for (int m = 0; m < 8; ++m) nzA[m] = nz[m];
     } else {
-      float2 zz[8];
 #pragma unroll
-      for (int m = 0; m < 8; ++m) zz[m] = float2{nzA[m], nz[m]};
-      fft_line<N, -1, float2, SmLine<float2, N, true>, SY>(zz, t, stw, view);
-      xp_emit<N, SY>(zz, t, P, yb + 2 * fs + lineA * hs, yb + 2 * fs + line * hs, kc);
+      for (int m = 0; m < 8; ++m) v[m] = float2{nzA[m], nz[m]};
+      fft_line<N, -1, float2, SmLine<float2, N, true>, SY>(v, t, stw, view);
+      xp_emit<N, SY>(v, t, P, yb + 2 * fs + lineA * hs, yb + 2 * fs + line * hs, kc);
     }
   }
 }
@@ -1272,6 +1280,152 @@ __global__ void __launch_bounds__((N / 8) * W) k3_fwd1(Geo g, StepBufs<R> b) {
   }
 }
 
+// fwd1 with a shared spectral tile (FP32 at 256 and 512 points): the same
+// arithmetic as k3_fwd1, rearranged so that a thread holds one field at a
+// time and two 512-thread blocks share an SM (64 registers).  Per column
+// tile (ky row, W kx columns), persistent over tiles:
+//   1. the three z forward transforms, each field's retained rows into the
+//      tile Q [3][c][W];
+//   2. per retained mode (thread (w, t): rows t, t + T, ...): normalise,
+//      project, add forcing, RK stage with its operands loaded from global
+//      memory, next stage input back into Q;
+//   3. (INV) the curl and the z inverse of the next stage input from Q: five
+//      transforms for six fields, omega_z = i (kx u_y - ky u_x) formed from
+//      the inverse of u_y and the inverse of u_x this thread has just stored.
+// The other block of the SM overlaps phase 2's memory latency.
+template <typename R, int N, int W>
+__host__ __device__ constexpr size_t fwd1t_smem() {
+  return col_tile_bytes(N, W, 2 * sizeof(R)) + (size_t)3 * trunc_rows(N) * W * 2 * sizeof(R);
+}
+template <typename R, int N, int W, int MODE, bool INV>
+__global__ void __launch_bounds__((N / 8) * W, 2) k3_fwd1t(Geo g, StepBufs<R> b) {
+  using C = typename CplxOf<R>::T;
+  constexpr int T = N / 8;
+  constexpr int P = pitch_of(W, sizeof(C));
+  constexpr int CR = trunc_rows(N);
+  constexpr bool NEED_U = MODE == MODE_RK1 || MODE == MODE_RK2 || MODE == MODE_RK3 || MODE == MODE_M1 || MODE == MODE_M2;
+  constexpr bool NEED_ACC = MODE == MODE_RK2 || MODE == MODE_RK3 || MODE == MODE_RK4;
+  C *sm = dyn_smem<C>();
+  C *Q = sm + N * P;  // [3][CR][W]
+  const int w = threadIdx.x % W, t = threadIdx.x / W;
+  const int nkt = g.hs / W;
+  const int ntiles = g.c * nkt;
+  const long long plane = (long long)g.c * g.hs;
+  const long long st = g.st_comp;
+  const SmCol<C, false> view{sm + w, P, 0};
+  const R scale = (R)1 / ((R)N * (R)N * (R)N);
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int iy = tile / nkt;
+    const int kx = (tile % nkt) * W + w;
+    const bool valid = kx < g.h;
+    const int ky = ktr_of(iy, g.kc, g.c);
+    const long long col = (long long)iy * g.hs + kx;
+    // 1. forward transforms into Q (rows of the retained kz only)
+#pragma unroll 1
+    for (int f = 0; f < 3; ++f) {
+      C v[8];
+#pragma unroll
+      for (int m = 0; m < 8; ++m)
+        v[m] = valid ? ld_stream(b.zb + f * g.zb_f + (long long)(t + T * m) * plane + col) : czero<C>();
+      fft_line<N, -1>(v, t, b.tw + N, view);
+#pragma unroll
+      for (int m = 0; m < 8; ++m) {
+        const int n = t + T * m;
+        if (m != 3 && m != 4 && retained(n, N, g.kc)) Q[(f * CR + compact_of(n, N, g.kc, g.c)) * W + w] = v[m];
+      }
+    }
+    __syncthreads();
+    // 2. projection, forcing and the RK stage per retained mode
+    if (valid) {
+      const R kxr = (R)kx, kyr = (R)ky;
+      const R exy = axis_factor(b.ef, kx) * axis_factor(b.ef, ky);
+      const R exy2 = axis_factor(b.ef2, kx) * axis_factor(b.ef2, ky);
+#pragma unroll 1
+      for (int r = t; r < CR; r += T) {
+        const int kz = ktr_of(r, g.kc, g.c);
+        const R kzr = (R)kz;
+        const int k2 = kx * kx + ky * ky + kz * kz;
+        C ax = cscale(Q[r * W + w], scale), ay = cscale(Q[(CR + r) * W + w], scale),
+          az = cscale(Q[(2 * CR + r) * W + w], scale);
+        if (k2 == 0) {
+          ax = ay = az = czero<C>();
+        } else {
+          const R inv = (R)1 / (R)k2;
+          const C kd = C{(kxr * ax.x + kyr * ay.x + kzr * az.x) * inv, (kxr * ax.y + kyr * ay.y + kzr * az.y) * inv};
+          ax = C{ax.x - kxr * kd.x, ax.y - kxr * kd.y};
+          ay = C{ay.x - kyr * kd.x, ay.y - kyr * kd.y};
+          az = C{az.x - kzr * kd.x, az.y - kzr * kd.y};
+        }
+        const long long idx = (long long)r * plane + col;
+        if (MODE != MODE_PROJ && b.F != nullptr) {
+          ax = cadd(ax, b.F[idx]);
+          ay = cadd(ay, b.F[st + idx]);
+          az = cadd(az, b.F[2 * st + idx]);
+        }
+        R e, e2;
+        if (b.ek2 != nullptr) {
+          e = __ldg(b.ek2 + k2);
+          e2 = __ldg(b.ek22 + k2);
+        } else {
+          e = exy * axis_factor(b.ef, kz);
+          e2 = exy2 * axis_factor(b.ef2, kz);
+        }
+        C uu[3], aa[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          uu[c] = NEED_U ? ld_stream(b.u + c * st + idx) : czero<C>();
+          aa[c] = NEED_ACC ? ld_stream(b.acc + c * st + idx) : czero<C>();
+        }
+        const C nv[3] = {ax, ay, az};
+#pragma unroll
+        for (int c = 0; c < 3; ++c) Q[(c * CR + r) * W + w] = rk_stage<MODE>(nv[c], uu[c], aa[c], e, e2, b, c * st + idx);
+      }
+    }
+    if (INV) {
+      __syncthreads();
+      // 3. curl and z inverse of the next stage input
+      const R kxr = (R)kx, kyr = (R)ky;
+#pragma unroll 1
+      for (int f = 0; f < 5; ++f) {
+        C v[8];
+#pragma unroll
+        for (int m = 0; m < 8; ++m) {
+          const int n = t + T * m;
+          C x = czero<C>();
+          if (m != 3 && m != 4 && retained(n, N, g.kc)) {
+            const int r = compact_of(n, N, g.kc, g.c);
+            const R kzr = (R)kfull_of(n, N, g.kc);
+            if (f < 3) {
+              x = Q[(f * CR + r) * W + w];
+            } else if (f == 3) {  // omega_x = i (ky u_z - kz u_y)
+              const C a2 = Q[(2 * CR + r) * W + w], a1 = Q[(CR + r) * W + w];
+              x = cmuli(C{kyr * a2.x - kzr * a1.x, kyr * a2.y - kzr * a1.y});
+            } else {  // omega_y = i (kz u_x - kx u_z)
+              const C a0 = Q[r * W + w], a2 = Q[(2 * CR + r) * W + w];
+              x = cmuli(C{kzr * a0.x - kxr * a2.x, kzr * a0.y - kxr * a2.y});
+            }
+          }
+          v[m] = x;
+        }
+        fft_line<N, +1>(v, t, b.tw + N, view);
+        if (valid) {
+#pragma unroll
+          for (int m = 0; m < 8; ++m) b.zb[f * g.zb_f + (long long)(t + T * m) * plane + col] = v[m];
+          if (f == 1) {  // omega_z = i (kx u_y - ky u_x), u_x as this thread stored it for f = 0
+#pragma unroll
+            for (int m = 0; m < 8; ++m) {
+              const long long o = (long long)(t + T * m) * plane + col;
+              const C ux = b.zb[o];
+              b.zb[5 * g.zb_f + o] = cmuli(C{kxr * v[m].x - kyr * ux.x, kxr * v[m].y - kyr * ux.y});
+            }
+          }
+        }
+      }
+    }
+    __syncthreads();  // Q and the exchange tile are free for the next tile
+  }
+}
+
 // ================================================================== 2D ====
 // inv1 (2D): y inverse from a state-shaped array.  VEL: four fields
 // u_x = i ky psi, u_y = -i kx psi, d_x w = i kx w, d_y w = i ky w with
@@ -1582,6 +1736,9 @@ struct Launch3 {
   static constexpr size_t SM_F1 = col_tile_bytes(N, WH, sizeof(C)) + (size_t)36 * T * WH * sizeof(C);
   static constexpr size_t SM_F1S = col_tile_bytes(N, WH, sizeof(C)) + (size_t)18 * T * WH * sizeof(C);
   static_assert(SM_F1 <= kSmemMax, "fwd1 shared memory");
+  // fwd1 with the shared spectral tile: FP32, 256 and 512 points
+  static constexpr bool F1T = sizeof(R) == 4 && (N == 256 || N == 512);
+  static constexpr size_t SM_F1T = fwd1t_smem<R, N, WH>();
   static constexpr size_t SM_X = (size_t)L * smline_len(N / 2) * sizeof(C);
   static constexpr size_t SM_XP = SM_X + (size_t)24 * (N / 16) * L * sizeof(C);  // + parked velocity fields
   // warp-per-line x pass when a line fits in one warp
@@ -1619,6 +1776,16 @@ struct Launch3 {
         set_smem(k3_fwd1<R, N, WH, MODE_PROJ, false>, SM_F1S);
         set_smem(k3_fwd1<R, N, WH, MODE_M1, true>, SM_F1S);
         set_smem(k3_fwd1<R, N, WH, MODE_M2, true>, SM_F1S);
+        if constexpr (F1T) {
+          set_smem(k3_fwd1t<R, N, WH, MODE_RK1, true>, SM_F1T);
+          set_smem(k3_fwd1t<R, N, WH, MODE_RK2, true>, SM_F1T);
+          set_smem(k3_fwd1t<R, N, WH, MODE_RK3, true>, SM_F1T);
+          set_smem(k3_fwd1t<R, N, WH, MODE_RK4, true>, SM_F1T);
+          set_smem(k3_fwd1t<R, N, WH, MODE_RHS, false>, SM_F1T);
+          set_smem(k3_fwd1t<R, N, WH, MODE_PROJ, false>, SM_F1T);
+          set_smem(k3_fwd1t<R, N, WH, MODE_M1, true>, SM_F1T);
+          set_smem(k3_fwd1t<R, N, WH, MODE_M2, true>, SM_F1T);
+        }
         break;
       case OP_INV1: {
         const dim3 grid(g.c * (g.hs / WL));
@@ -1675,8 +1842,22 @@ struct Launch3 {
           cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k3_fwd1<R, N, WH, MODE_RK2, true>, T * WH, SM_F1);
           if (per_sm < 1) per_sm = 1;
         }
-        const int grid = cmin(tiles, per_sm * (a.nsm > 0 ? a.nsm : 1));
         const StepBufs<R> b = step_bufs<R>(a);
+        if constexpr (F1T) {
+          const int gt = cmin(tiles, 2 * (a.nsm > 0 ? a.nsm : 1));  // two resident blocks per SM
+          switch (a.mode) {
+            case MODE_RK1: k3_fwd1t<R, N, WH, MODE_RK1, true><<<gt, T * WH, SM_F1T, s>>>(g, b); break;
+            case MODE_RK2: k3_fwd1t<R, N, WH, MODE_RK2, true><<<gt, T * WH, SM_F1T, s>>>(g, b); break;
+            case MODE_RK3: k3_fwd1t<R, N, WH, MODE_RK3, true><<<gt, T * WH, SM_F1T, s>>>(g, b); break;
+            case MODE_RK4: k3_fwd1t<R, N, WH, MODE_RK4, true><<<gt, T * WH, SM_F1T, s>>>(g, b); break;
+            case MODE_RHS: k3_fwd1t<R, N, WH, MODE_RHS, false><<<gt, T * WH, SM_F1T, s>>>(g, b); break;
+            case MODE_M1: k3_fwd1t<R, N, WH, MODE_M1, true><<<gt, T * WH, SM_F1T, s>>>(g, b); break;
+            case MODE_M2: k3_fwd1t<R, N, WH, MODE_M2, true><<<gt, T * WH, SM_F1T, s>>>(g, b); break;
+            default: k3_fwd1t<R, N, WH, MODE_PROJ, false><<<gt, T * WH, SM_F1T, s>>>(g, b); break;
+          }
+          break;
+        }
+        const int grid = cmin(tiles, per_sm * (a.nsm > 0 ? a.nsm : 1));
         switch (a.mode) {
           case MODE_RK1: k3_fwd1<R, N, WH, MODE_RK1, true><<<grid, T * WH, SM_F1S, s>>>(g, b); break;
           case MODE_RK2: k3_fwd1<R, N, WH, MODE_RK2, true><<<grid, T * WH, SM_F1, s>>>(g, b); break;
