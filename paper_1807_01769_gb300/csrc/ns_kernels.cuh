@@ -22,6 +22,7 @@
 // simulations": FFT, RK4, curl, vector product, projection).
 #pragma once
 #include <cuda.h>  // CUtensorMap (a kernel parameter type; no driver calls here)
+#include <cstdlib>
 
 #include "ns_fft.cuh"
 #include "ns_internal.h"
@@ -1297,8 +1298,8 @@ template <typename R, int N, int W>
 __host__ __device__ constexpr size_t fwd1t_smem() {
   return col_tile_bytes(N, W, 2 * sizeof(R)) + (size_t)3 * trunc_rows(N) * W * 2 * sizeof(R);
 }
-template <typename R, int N, int W, int MODE, bool INV>
-__global__ void __launch_bounds__((N / 8) * W, 2) k3_fwd1t(Geo g, StepBufs<R> b) {
+template <typename R, int N, int W, int MODE, bool INV, bool PF = false, int UR = 1, int MINB = 2>
+__global__ void __launch_bounds__((N / 8) * W, MINB) k3_fwd1t(Geo g, StepBufs<R> b) {
   using C = typename CplxOf<R>::T;
   constexpr int T = N / 8;
   constexpr int P = pitch_of(W, sizeof(C));
@@ -1320,13 +1321,29 @@ __global__ void __launch_bounds__((N / 8) * W, 2) k3_fwd1t(Geo g, StepBufs<R> b)
     const bool valid = kx < g.h;
     const int ky = ktr_of(iy, g.kc, g.c);
     const long long col = (long long)iy * g.hs + kx;
-    // 1. forward transforms into Q (rows of the retained kz only)
+    // 1. forward transforms into Q (rows of the retained kz only); PF: the
+    // next field's column is loaded while the current one is transformed
+    C xn[8];
+    if (PF) {
+#pragma unroll
+      for (int m = 0; m < 8; ++m) xn[m] = valid ? ld_stream(b.zb + (long long)(t + T * m) * plane + col) : czero<C>();
+    }
 #pragma unroll 1
     for (int f = 0; f < 3; ++f) {
       C v[8];
+      if (PF) {
 #pragma unroll
-      for (int m = 0; m < 8; ++m)
-        v[m] = valid ? ld_stream(b.zb + f * g.zb_f + (long long)(t + T * m) * plane + col) : czero<C>();
+        for (int m = 0; m < 8; ++m) v[m] = xn[m];
+        if (f < 2) {
+#pragma unroll
+          for (int m = 0; m < 8; ++m)
+            xn[m] = valid ? ld_stream(b.zb + (f + 1) * g.zb_f + (long long)(t + T * m) * plane + col) : czero<C>();
+        }
+      } else {
+#pragma unroll
+        for (int m = 0; m < 8; ++m)
+          v[m] = valid ? ld_stream(b.zb + f * g.zb_f + (long long)(t + T * m) * plane + col) : czero<C>();
+      }
       fft_line<N, -1>(v, t, b.tw + N, view);
 #pragma unroll
       for (int m = 0; m < 8; ++m) {
@@ -1335,50 +1352,62 @@ __global__ void __launch_bounds__((N / 8) * W, 2) k3_fwd1t(Geo g, StepBufs<R> b)
       }
     }
     __syncthreads();
-    // 2. projection, forcing and the RK stage per retained mode
+    // 2. projection, forcing and the RK stage per retained mode (UR rows of
+    // a thread at a time, their operand loads issued together)
     if (valid) {
       const R kxr = (R)kx, kyr = (R)ky;
       const R exy = axis_factor(b.ef, kx) * axis_factor(b.ef, ky);
       const R exy2 = axis_factor(b.ef2, kx) * axis_factor(b.ef2, ky);
 #pragma unroll 1
-      for (int r = t; r < CR; r += T) {
-        const int kz = ktr_of(r, g.kc, g.c);
-        const R kzr = (R)kz;
-        const int k2 = kx * kx + ky * ky + kz * kz;
-        C ax = cscale(Q[r * W + w], scale), ay = cscale(Q[(CR + r) * W + w], scale),
-          az = cscale(Q[(2 * CR + r) * W + w], scale);
-        if (k2 == 0) {
-          ax = ay = az = czero<C>();
-        } else {
-          const R inv = (R)1 / (R)k2;
-          const C kd = C{(kxr * ax.x + kyr * ay.x + kzr * az.x) * inv, (kxr * ax.y + kyr * ay.y + kzr * az.y) * inv};
-          ax = C{ax.x - kxr * kd.x, ax.y - kxr * kd.y};
-          ay = C{ay.x - kyr * kd.x, ay.y - kyr * kd.y};
-          az = C{az.x - kzr * kd.x, az.y - kzr * kd.y};
-        }
-        const long long idx = (long long)r * plane + col;
-        if (MODE != MODE_PROJ && b.F != nullptr) {
-          ax = cadd(ax, b.F[idx]);
-          ay = cadd(ay, b.F[st + idx]);
-          az = cadd(az, b.F[2 * st + idx]);
-        }
-        R e, e2;
-        if (b.ek2 != nullptr) {
-          e = __ldg(b.ek2 + k2);
-          e2 = __ldg(b.ek22 + k2);
-        } else {
-          e = exy * axis_factor(b.ef, kz);
-          e2 = exy2 * axis_factor(b.ef2, kz);
-        }
-        C uu[3], aa[3];
+      for (int r0 = t; r0 < CR; r0 += UR * T) {
+        C uu[UR][3], aa[UR][3];
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
-          uu[c] = NEED_U ? ld_stream(b.u + c * st + idx) : czero<C>();
-          aa[c] = NEED_ACC ? ld_stream(b.acc + c * st + idx) : czero<C>();
-        }
-        const C nv[3] = {ax, ay, az};
+        for (int q = 0; q < UR; ++q) {
+          const int r = r0 + q * T;
+          const long long idx = (long long)(r < CR ? r : 0) * plane + col;
 #pragma unroll
-        for (int c = 0; c < 3; ++c) Q[(c * CR + r) * W + w] = rk_stage<MODE>(nv[c], uu[c], aa[c], e, e2, b, c * st + idx);
+          for (int c = 0; c < 3; ++c) {
+            uu[q][c] = NEED_U && r < CR ? ld_stream(b.u + c * st + idx) : czero<C>();
+            aa[q][c] = NEED_ACC && r < CR ? ld_stream(b.acc + c * st + idx) : czero<C>();
+          }
+        }
+#pragma unroll
+        for (int q = 0; q < UR; ++q) {
+          const int r = r0 + q * T;
+          if (r >= CR) break;
+          const int kz = ktr_of(r, g.kc, g.c);
+          const R kzr = (R)kz;
+          const int k2 = kx * kx + ky * ky + kz * kz;
+          C ax = cscale(Q[r * W + w], scale), ay = cscale(Q[(CR + r) * W + w], scale),
+            az = cscale(Q[(2 * CR + r) * W + w], scale);
+          if (k2 == 0) {
+            ax = ay = az = czero<C>();
+          } else {
+            const R inv = (R)1 / (R)k2;
+            const C kd = C{(kxr * ax.x + kyr * ay.x + kzr * az.x) * inv, (kxr * ax.y + kyr * ay.y + kzr * az.y) * inv};
+            ax = C{ax.x - kxr * kd.x, ax.y - kxr * kd.y};
+            ay = C{ay.x - kyr * kd.x, ay.y - kyr * kd.y};
+            az = C{az.x - kzr * kd.x, az.y - kzr * kd.y};
+          }
+          const long long idx = (long long)r * plane + col;
+          if (MODE != MODE_PROJ && b.F != nullptr) {
+            ax = cadd(ax, b.F[idx]);
+            ay = cadd(ay, b.F[st + idx]);
+            az = cadd(az, b.F[2 * st + idx]);
+          }
+          R e, e2;
+          if (b.ek2 != nullptr) {
+            e = __ldg(b.ek2 + k2);
+            e2 = __ldg(b.ek22 + k2);
+          } else {
+            e = exy * axis_factor(b.ef, kz);
+            e2 = exy2 * axis_factor(b.ef2, kz);
+          }
+          const C nv[3] = {ax, ay, az};
+#pragma unroll
+          for (int c = 0; c < 3; ++c)
+            Q[(c * CR + r) * W + w] = rk_stage<MODE>(nv[c], uu[q][c], aa[q][c], e, e2, b, c * st + idx);
+        }
       }
     }
     if (INV) {
@@ -1713,6 +1742,38 @@ inline StepBufs<R> step_bufs(const Args &a) {
   return b;
 }
 
+// fwd1 variants with the shared spectral tile (RK stages only)
+template <typename R, int N, int W, bool PF, int UR, int MINB>
+struct Fwd1T {
+  static constexpr size_t SM = fwd1t_smem<R, N, W>();
+  static void prepare() {
+    set_smem(k3_fwd1t<R, N, W, MODE_RK1, true, PF, UR, MINB>, SM);
+    set_smem(k3_fwd1t<R, N, W, MODE_RK2, true, PF, UR, MINB>, SM);
+    set_smem(k3_fwd1t<R, N, W, MODE_RK3, true, PF, UR, MINB>, SM);
+    set_smem(k3_fwd1t<R, N, W, MODE_RK4, true, PF, UR, MINB>, SM);
+  }
+  // false: not an RK stage (the caller launches another form)
+  static bool launch(int mode, int nsm, const Geo &g, const StepBufs<R> &b, cudaStream_t s) {
+    const int tiles = g.c * (g.hs / W), grid = cmin(tiles, MINB * (nsm > 0 ? nsm : 1));
+    constexpr int NT = (N / 8) * W;
+    switch (mode) {
+      case MODE_RK1: k3_fwd1t<R, N, W, MODE_RK1, true, PF, UR, MINB><<<grid, NT, SM, s>>>(g, b); return true;
+      case MODE_RK2: k3_fwd1t<R, N, W, MODE_RK2, true, PF, UR, MINB><<<grid, NT, SM, s>>>(g, b); return true;
+      case MODE_RK3: k3_fwd1t<R, N, W, MODE_RK3, true, PF, UR, MINB><<<grid, NT, SM, s>>>(g, b); return true;
+      case MODE_RK4: k3_fwd1t<R, N, W, MODE_RK4, true, PF, UR, MINB><<<grid, NT, SM, s>>>(g, b); return true;
+      default: return false;
+    }
+  }
+};
+inline int fwd1_variant() {
+  static int v = -1;
+  if (v < 0) {
+    const char *e = std::getenv("NS_FWD1");
+    v = e ? std::atoi(e) : 0;
+  }
+  return v;
+}
+
 template <typename R, int N>
 struct Launch3 {
   using C = typename CplxOf<R>::T;
@@ -1776,6 +1837,12 @@ struct Launch3 {
         set_smem(k3_fwd1<R, N, WH, MODE_PROJ, false>, SM_F1S);
         set_smem(k3_fwd1<R, N, WH, MODE_M1, true>, SM_F1S);
         set_smem(k3_fwd1<R, N, WH, MODE_M2, true>, SM_F1S);
+        if constexpr (F1T && N == 512) {
+          Fwd1T<R, N, 8, true, 2, 2>::prepare();
+          Fwd1T<R, N, 8, false, 2, 2>::prepare();
+          Fwd1T<R, N, 16, false, 2, 1>::prepare();
+          Fwd1T<R, N, 16, true, 2, 1>::prepare();
+        }
         if constexpr (F1T) {
           set_smem(k3_fwd1t<R, N, WH, MODE_RK1, true>, SM_F1T);
           set_smem(k3_fwd1t<R, N, WH, MODE_RK2, true>, SM_F1T);
@@ -1843,7 +1910,16 @@ struct Launch3 {
           if (per_sm < 1) per_sm = 1;
         }
         const StepBufs<R> b = step_bufs<R>(a);
-        if constexpr (F1T) {
+        if constexpr (F1T && N == 512) {
+          const int var = fwd1_variant();
+          bool done = false;
+          if (var == 2) done = Fwd1T<R, N, 8, true, 2, 2>::launch(a.mode, a.nsm, g, b, s);
+          if (var == 3) done = Fwd1T<R, N, 8, false, 2, 2>::launch(a.mode, a.nsm, g, b, s);
+          if (var == 4) done = Fwd1T<R, N, 16, false, 2, 1>::launch(a.mode, a.nsm, g, b, s);
+          if (var == 5) done = Fwd1T<R, N, 16, true, 2, 1>::launch(a.mode, a.nsm, g, b, s);
+          if (done) break;
+        }
+        if (F1T && fwd1_variant() != 0) {
           const int gt = cmin(tiles, 2 * (a.nsm > 0 ? a.nsm : 1));  // two resident blocks per SM
           switch (a.mode) {
             case MODE_RK1: k3_fwd1t<R, N, WH, MODE_RK1, true><<<gt, T * WH, SM_F1T, s>>>(g, b); break;
