@@ -200,6 +200,31 @@ struct SmLine {
   }
 };
 __host__ __device__ constexpr int smline_len(int L) { return L + L / 8; }
+//   contiguous line of a length-512 transform held by 64 threads, unpadded
+//   and XOR-swizzled within rows of 16 entries: entry n lives at
+//   16 a + ((n mod 16) xor phi(a)), a = n / 16, phi(a) = (a & 7) | ((a & 4) << 1).
+//   Every half-warp access of the plan (contiguous loads, the stride-8 stores
+//   of stage 0, the grouped stores of stage 1) then touches 16 distinct
+//   8-byte bank pairs, where the 1-in-8 padding costs the contiguous loads an
+//   extra wavefront.
+template <typename C, bool DBUF = false>
+struct SmLineX {
+  static constexpr bool DB = DBUF;
+  C *base;
+  int bofs;
+  static __device__ __forceinline__ int swz(int n) {
+    const int a = n >> 4;
+    return (n & ~15) | ((n & 15) ^ ((a & 7) | ((a & 4) << 1)));
+  }
+  template <int X>
+  __device__ __forceinline__ C ld(int n) const {
+    return base[(DB && (X & 1) ? bofs : 0) + swz(n)];
+  }
+  template <int X>
+  __device__ __forceinline__ void st(int n, C v) const {
+    base[(DB && (X & 1) ? bofs : 0) + swz(n)] = v;
+  }
+};
 
 // One radix-R stage of span NS on a line of length L (see file header).
 template <int L, int R, int NS, int TWOFF, int DIR, bool LAST, int XS, typename C, typename SM>

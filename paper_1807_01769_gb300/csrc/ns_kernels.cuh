@@ -589,8 +589,18 @@ __host__ __device__ constexpr int xp_sync(int T) { return T >= 64 ? T : SYNC_WAR
 // per group: the double-buffered exchange line, the partner region (3T) and
 // two staging buffers of the two input rows of a pair ([2][2][xp_row(N)])
 __host__ __device__ constexpr int xp_row(int N) { return ((N - 1) / 3 + 2) / 2 * 2; }
+// exchange line: swizzled and unpadded for 512 points (SmLineX), padded otherwise
+__host__ __device__ constexpr int xp_line(int N) { return N == 512 ? N : smline_len(N); }
+template <int N>
+struct XpView {
+  using T = SmLine<float2, N, true>;
+};
+template <>
+struct XpView<512> {
+  using T = SmLineX<float2, true>;
+};
 __host__ __device__ constexpr size_t xp_group_elems(int N) {
-  return 2 * (size_t)smline_len(N) + 3 * (N / 8) + 4 * (size_t)xp_row(N);
+  return 2 * (size_t)xp_line(N) + 3 * (N / 8) + 4 * (size_t)xp_row(N);
 }
 
 // Copy the retained part of the rows X_a, X_b of one pair (h complex each,
@@ -674,8 +684,9 @@ __global__ void __launch_bounds__((N / 8) * GPB, xp_min_blocks<N>())
   float2 *S = dyn_smem<float2>();
   const int grp = threadIdx.x / T, t = threadIdx.x % T;
   float2 *gs = S + grp * xp_group_elems(N);
-  const SmLine<float2, N, true> view{gs, smline_len(N)};
-  float2 *P = gs + 2 * smline_len(N);
+  using View = typename XpView<N>::T;
+  const View view{gs, xp_line(N)};
+  float2 *P = gs + 2 * xp_line(N);
   float2 *stage = P + 3 * T;  // [2 buffers][2 rows][RW]
   const float2 *stw = tw + N;  // stage tables of the length-N transform
   const long long lineA = line_base + ((long long)blockIdx.x * GPB + grp) * 2;
@@ -702,7 +713,7 @@ __global__ void __launch_bounds__((N / 8) * GPB, xp_min_blocks<N>())
     }
     fft_sync<SY>();  // every thread's copies of pair i are visible
     xp_build<N>(v, stage + (i & 1) * 2 * RW, t, kc);
-    fft_line<N, +1, float2, SmLine<float2, N, true>, SY>(v, t, stw, view);
+    fft_line<N, +1, float2, View, SY>(v, t, stw, view);
   };
   next_pair(0);
 #pragma unroll
@@ -744,7 +755,7 @@ __global__ void __launch_bounds__((N / 8) * GPB, xp_min_blocks<N>())
       nxy[m] = float2{fmaf(uy, wzl, -uzl * wy), fmaf(uzl, wx, -ux * wzl)};
       nz[m] = fmaf(ux, wy, -uy * wx);
     }
-    fft_line<N, -1, float2, SmLine<float2, N, true>, SY>(nxy, t, stw, view);
+    fft_line<N, -1, float2, View, SY>(nxy, t, stw, view);
     xp_emit<N, SY>(nxy, t, P, yb + line * hs, yb + fs + line * hs, kc);
     if (ln == 0) {
 #pragma unroll
@@ -752,7 +763,7 @@ __global__ void __launch_bounds__((N / 8) * GPB, xp_min_blocks<N>())
     } else {
 #pragma unroll
       for (int m = 0; m < 8; ++m) v[m] = float2{nzA[m], nz[m]};
-      fft_line<N, -1, float2, SmLine<float2, N, true>, SY>(v, t, stw, view);
+      fft_line<N, -1, float2, View, SY>(v, t, stw, view);
       xp_emit<N, SY>(v, t, P, yb + 2 * fs + lineA * hs, yb + 2 * fs + line * hs, kc);
     }
   }
@@ -1742,7 +1753,8 @@ inline StepBufs<R> step_bufs(const Args &a) {
   return b;
 }
 
-// fwd1 variants with the shared spectral tile (RK stages only)
+// fwd1 with the shared spectral tile in a given shape: W columns, next-field
+// prefetch PF, UR rows of RK operands in flight, MINB resident blocks per SM
 template <typename R, int N, int W, bool PF, int UR, int MINB>
 struct Fwd1T {
   static constexpr size_t SM = fwd1t_smem<R, N, W>();
@@ -1751,17 +1763,23 @@ struct Fwd1T {
     set_smem(k3_fwd1t<R, N, W, MODE_RK2, true, PF, UR, MINB>, SM);
     set_smem(k3_fwd1t<R, N, W, MODE_RK3, true, PF, UR, MINB>, SM);
     set_smem(k3_fwd1t<R, N, W, MODE_RK4, true, PF, UR, MINB>, SM);
+    set_smem(k3_fwd1t<R, N, W, MODE_RHS, false, PF, UR, MINB>, SM);
+    set_smem(k3_fwd1t<R, N, W, MODE_PROJ, false, PF, UR, MINB>, SM);
+    set_smem(k3_fwd1t<R, N, W, MODE_M1, true, PF, UR, MINB>, SM);
+    set_smem(k3_fwd1t<R, N, W, MODE_M2, true, PF, UR, MINB>, SM);
   }
-  // false: not an RK stage (the caller launches another form)
-  static bool launch(int mode, int nsm, const Geo &g, const StepBufs<R> &b, cudaStream_t s) {
+  static void launch(int mode, int nsm, const Geo &g, const StepBufs<R> &b, cudaStream_t s) {
     const int tiles = g.c * (g.hs / W), grid = cmin(tiles, MINB * (nsm > 0 ? nsm : 1));
     constexpr int NT = (N / 8) * W;
     switch (mode) {
-      case MODE_RK1: k3_fwd1t<R, N, W, MODE_RK1, true, PF, UR, MINB><<<grid, NT, SM, s>>>(g, b); return true;
-      case MODE_RK2: k3_fwd1t<R, N, W, MODE_RK2, true, PF, UR, MINB><<<grid, NT, SM, s>>>(g, b); return true;
-      case MODE_RK3: k3_fwd1t<R, N, W, MODE_RK3, true, PF, UR, MINB><<<grid, NT, SM, s>>>(g, b); return true;
-      case MODE_RK4: k3_fwd1t<R, N, W, MODE_RK4, true, PF, UR, MINB><<<grid, NT, SM, s>>>(g, b); return true;
-      default: return false;
+      case MODE_RK1: k3_fwd1t<R, N, W, MODE_RK1, true, PF, UR, MINB><<<grid, NT, SM, s>>>(g, b); break;
+      case MODE_RK2: k3_fwd1t<R, N, W, MODE_RK2, true, PF, UR, MINB><<<grid, NT, SM, s>>>(g, b); break;
+      case MODE_RK3: k3_fwd1t<R, N, W, MODE_RK3, true, PF, UR, MINB><<<grid, NT, SM, s>>>(g, b); break;
+      case MODE_RK4: k3_fwd1t<R, N, W, MODE_RK4, true, PF, UR, MINB><<<grid, NT, SM, s>>>(g, b); break;
+      case MODE_RHS: k3_fwd1t<R, N, W, MODE_RHS, false, PF, UR, MINB><<<grid, NT, SM, s>>>(g, b); break;
+      case MODE_M1: k3_fwd1t<R, N, W, MODE_M1, true, PF, UR, MINB><<<grid, NT, SM, s>>>(g, b); break;
+      case MODE_M2: k3_fwd1t<R, N, W, MODE_M2, true, PF, UR, MINB><<<grid, NT, SM, s>>>(g, b); break;
+      default: k3_fwd1t<R, N, W, MODE_PROJ, false, PF, UR, MINB><<<grid, NT, SM, s>>>(g, b); break;
     }
   }
 };
@@ -1769,10 +1787,17 @@ inline int fwd1_variant() {
   static int v = -1;
   if (v < 0) {
     const char *e = std::getenv("NS_FWD1");
-    v = e ? std::atoi(e) : 0;
+    v = e ? std::atoi(e) : 1;
   }
   return v;
 }
+// 512 points: 16 columns (128-byte rows), 1024 threads, one block per SM
+// (fwd1 1.146 -> 1.036 ms per launch against the register-resident form)
+template <typename R, int N>
+struct Fwd1Pick {
+  using A = Fwd1T<R, N, (N == 512 ? 16 : 16), true, 2, (N == 512 ? 1 : 2)>;
+  using B = Fwd1T<R, N, (N == 512 ? 16 : 32), true, 2, 1>;
+};
 
 template <typename R, int N>
 struct Launch3 {
@@ -1799,7 +1824,6 @@ struct Launch3 {
   static_assert(SM_F1 <= kSmemMax, "fwd1 shared memory");
   // fwd1 with the shared spectral tile: FP32, 256 and 512 points
   static constexpr bool F1T = sizeof(R) == 4 && (N == 256 || N == 512);
-  static constexpr size_t SM_F1T = fwd1t_smem<R, N, WH>();
   static constexpr size_t SM_X = (size_t)L * smline_len(N / 2) * sizeof(C);
   static constexpr size_t SM_XP = SM_X + (size_t)24 * (N / 16) * L * sizeof(C);  // + parked velocity fields
   // warp-per-line x pass when a line fits in one warp
@@ -1837,21 +1861,9 @@ struct Launch3 {
         set_smem(k3_fwd1<R, N, WH, MODE_PROJ, false>, SM_F1S);
         set_smem(k3_fwd1<R, N, WH, MODE_M1, true>, SM_F1S);
         set_smem(k3_fwd1<R, N, WH, MODE_M2, true>, SM_F1S);
-        if constexpr (F1T && N == 512) {
-          Fwd1T<R, N, 8, true, 2, 2>::prepare();
-          Fwd1T<R, N, 8, false, 2, 2>::prepare();
-          Fwd1T<R, N, 16, false, 2, 1>::prepare();
-          Fwd1T<R, N, 16, true, 2, 1>::prepare();
-        }
         if constexpr (F1T) {
-          set_smem(k3_fwd1t<R, N, WH, MODE_RK1, true>, SM_F1T);
-          set_smem(k3_fwd1t<R, N, WH, MODE_RK2, true>, SM_F1T);
-          set_smem(k3_fwd1t<R, N, WH, MODE_RK3, true>, SM_F1T);
-          set_smem(k3_fwd1t<R, N, WH, MODE_RK4, true>, SM_F1T);
-          set_smem(k3_fwd1t<R, N, WH, MODE_RHS, false>, SM_F1T);
-          set_smem(k3_fwd1t<R, N, WH, MODE_PROJ, false>, SM_F1T);
-          set_smem(k3_fwd1t<R, N, WH, MODE_M1, true>, SM_F1T);
-          set_smem(k3_fwd1t<R, N, WH, MODE_M2, true>, SM_F1T);
+          Fwd1Pick<R, N>::A::prepare();
+          Fwd1Pick<R, N>::B::prepare();
         }
         break;
       case OP_INV1: {
@@ -1910,28 +1922,16 @@ struct Launch3 {
           if (per_sm < 1) per_sm = 1;
         }
         const StepBufs<R> b = step_bufs<R>(a);
-        if constexpr (F1T && N == 512) {
+        if constexpr (F1T) {
           const int var = fwd1_variant();
-          bool done = false;
-          if (var == 2) done = Fwd1T<R, N, 8, true, 2, 2>::launch(a.mode, a.nsm, g, b, s);
-          if (var == 3) done = Fwd1T<R, N, 8, false, 2, 2>::launch(a.mode, a.nsm, g, b, s);
-          if (var == 4) done = Fwd1T<R, N, 16, false, 2, 1>::launch(a.mode, a.nsm, g, b, s);
-          if (var == 5) done = Fwd1T<R, N, 16, true, 2, 1>::launch(a.mode, a.nsm, g, b, s);
-          if (done) break;
-        }
-        if (F1T && fwd1_variant() != 0) {
-          const int gt = cmin(tiles, 2 * (a.nsm > 0 ? a.nsm : 1));  // two resident blocks per SM
-          switch (a.mode) {
-            case MODE_RK1: k3_fwd1t<R, N, WH, MODE_RK1, true><<<gt, T * WH, SM_F1T, s>>>(g, b); break;
-            case MODE_RK2: k3_fwd1t<R, N, WH, MODE_RK2, true><<<gt, T * WH, SM_F1T, s>>>(g, b); break;
-            case MODE_RK3: k3_fwd1t<R, N, WH, MODE_RK3, true><<<gt, T * WH, SM_F1T, s>>>(g, b); break;
-            case MODE_RK4: k3_fwd1t<R, N, WH, MODE_RK4, true><<<gt, T * WH, SM_F1T, s>>>(g, b); break;
-            case MODE_RHS: k3_fwd1t<R, N, WH, MODE_RHS, false><<<gt, T * WH, SM_F1T, s>>>(g, b); break;
-            case MODE_M1: k3_fwd1t<R, N, WH, MODE_M1, true><<<gt, T * WH, SM_F1T, s>>>(g, b); break;
-            case MODE_M2: k3_fwd1t<R, N, WH, MODE_M2, true><<<gt, T * WH, SM_F1T, s>>>(g, b); break;
-            default: k3_fwd1t<R, N, WH, MODE_PROJ, false><<<gt, T * WH, SM_F1T, s>>>(g, b); break;
+          if (var == 1) {
+            Fwd1Pick<R, N>::A::launch(a.mode, a.nsm, g, b, s);
+            break;
           }
-          break;
+          if (var == 2) {
+            Fwd1Pick<R, N>::B::launch(a.mode, a.nsm, g, b, s);
+            break;
+          }
         }
         const int grid = cmin(tiles, per_sm * (a.nsm > 0 ? a.nsm : 1));
         switch (a.mode) {
