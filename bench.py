@@ -256,6 +256,7 @@ def ensemble_bench(steps=50):
         torch.cuda.synchronize()
         ms = ev0.elapsed_time(ev1) / steps
         sched = e.schedule()
+        tiles = e.tiles()
     solvers = [ns.Solver(2, n, ns.NS_FP32, nu=5e-4, dt=5e-4) for n in sizes]
     for s, u in zip(solvers, u0):
         s.set_stream(stream.cuda_stream)
@@ -274,7 +275,8 @@ def ensemble_bench(steps=50):
     return {"workload": ENSEMBLE_WORKLOAD, "metric": "Mpoint*RK4-steps/s", "steps": steps,
             "value": pts / (ms / 1e3) / 1e6, "ms_per_step": ms, "plain_value": pts / (ms_plain / 1e3) / 1e6,
             "plain_ms_per_step": ms_plain, "speedup_vs_plain": ms_plain / ms,
-            "schedule": {"x_blocks_per_sm": sched[0], "y_blocks_per_sm": sched[1],
+            "schedule": {"y_block_threads": tiles[0], "x_block_warps": tiles[1],
+                         "x_blocks_per_sm": sched[0], "y_blocks_per_sm": sched[1],
                          "task_order": ["member-major", "round-robin"][sched[2]]}}
 
 

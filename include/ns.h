@@ -228,16 +228,25 @@ long long ns_device_bytes(const ns_state *s);
 typedef struct ns_ensemble ns_ensemble;
 
 /* Create an ensemble on the current device; all states start at zero.
- * autotune != 0 times the schedule candidates (blocks per SM of each pass:
- * x in {2, 4, 8}, y in {1, 2, 4}; task order member-major or round robin)
- * on the zero state and keeps the fastest; otherwise x = 4, y = 2,
- * member-major.  NS_EUNSUPPORTED for a grid size outside the set above. */
+ * autotune != 0 times the schedule candidates on the zero state and keeps
+ * the fastest: the tile shapes (fused y pass in blocks of 256 or 512 threads,
+ * i.e. kx tiles of 2048/N or 4096/N columns; x pass in blocks of 4 or 8
+ * warps), blocks per SM of each pass (x in {1, 2, 4, 8}, y in {1, 2, 4},
+ * at most 2048 resident threads) and the task order (member-major or round
+ * robin); otherwise 256-thread y tiles, 4-warp x blocks, x = 4, y = 2,
+ * member-major.  Every schedule gives the same result bit for bit (the
+ * transforms' radix plan is fixed, as in ns_step).  NS_EUNSUPPORTED for a
+ * grid size outside the set above. */
 int ns_ensemble_init(ns_ensemble **out, int count, const int *n, int precision, double nu, double dt, int autotune);
 
 /* Current schedule / set a schedule (task_order 0 = member by member,
  * 1 = round robin over members).  Set synchronises the ensemble's stream. */
 int ns_ensemble_schedule(const ns_ensemble *e, int *x_blocks_per_sm, int *y_blocks_per_sm, int *task_order);
 int ns_ensemble_set_schedule(ns_ensemble *e, int x_blocks_per_sm, int y_blocks_per_sm, int task_order);
+/* Current tile shapes / set them (y_threads 256 or 512, x_warps 4 or 8;
+ * else NS_EINVAL).  Set synchronises the ensemble's stream. */
+int ns_ensemble_tiles(const ns_ensemble *e, int *y_threads, int *x_warps);
+int ns_ensemble_set_tiles(ns_ensemble *e, int y_threads, int x_warps);
 
 /* Member state in the canonical 2D truncated spectral layout (host complex128
  * as double pairs, [c][h] of that member's grid).  Synchronise. */

@@ -35,12 +35,13 @@ struct EnsMember {
   StepBufs<R> b;
 };
 
-// y-pass tile width for the ensemble's 256-thread blocks
-__host__ __device__ constexpr int ens_w(int n) { return 256 / (n / 8); }
+// y-pass tile width (kx columns) for the ensemble's YT-thread blocks (a tile
+// shape of the schedule: YT = 256 or 512)
+__host__ __device__ constexpr int ens_w(int n, int yt = 256) { return yt / (n / 8); }
 
-template <typename R>
-__global__ void __launch_bounds__(256) k2e_inv1(const EnsMember<R> *__restrict__ mem, const int2 *__restrict__ tasks,
-                                               int ntasks) {
+template <typename R, int YT = 256>
+__global__ void __launch_bounds__(YT) k2e_inv1(const EnsMember<R> *__restrict__ mem, const int2 *__restrict__ tasks,
+                                              int ntasks) {
   using C = typename CplxOf<R>::T;
   C *sm = dyn_smem<C>();
   for (int i = blockIdx.x; i < ntasks; i += gridDim.x) {
@@ -48,10 +49,10 @@ __global__ void __launch_bounds__(256) k2e_inv1(const EnsMember<R> *__restrict__
     const Geo g = mem[tk.x].g;
     const StepBufs<R> b = mem[tk.x].b;
     switch (g.N) {
-      case 64: inv1_2d_unit<R, 64, ens_w(64), true>(g, b.u, b.yb, b.tw, tk.y, sm); break;
-      case 128: inv1_2d_unit<R, 128, ens_w(128), true>(g, b.u, b.yb, b.tw, tk.y, sm); break;
-      case 256: inv1_2d_unit<R, 256, ens_w(256), true>(g, b.u, b.yb, b.tw, tk.y, sm); break;
-      default: inv1_2d_unit<R, 512, ens_w(512), true>(g, b.u, b.yb, b.tw, tk.y, sm); break;
+      case 64: inv1_2d_unit<R, 64, ens_w(64, YT), true>(g, b.u, b.yb, b.tw, tk.y, sm); break;
+      case 128: inv1_2d_unit<R, 128, ens_w(128, YT), true>(g, b.u, b.yb, b.tw, tk.y, sm); break;
+      case 256: inv1_2d_unit<R, 256, ens_w(256, YT), true>(g, b.u, b.yb, b.tw, tk.y, sm); break;
+      default: inv1_2d_unit<R, 512, ens_w(512, YT), true>(g, b.u, b.yb, b.tw, tk.y, sm); break;
     }
     __syncthreads();  // the next unit may use another layout of the shared tile
   }
@@ -65,9 +66,10 @@ __host__ __device__ constexpr int ens_warp_region() {
               cmax(2 * xw_line_len<256, true>(), 1 * xw_line_len<512, false>()));
 }
 
-template <typename R>
-__global__ void __launch_bounds__(128) k2e_xpass(const EnsMember<R> *__restrict__ mem, const int2 *__restrict__ tasks,
-                                                int ntasks) {
+// XW warps per block (a tile shape of the schedule: 4 or 8)
+template <typename R, int XW = 4>
+__global__ void __launch_bounds__(32 * XW) k2e_xpass(const EnsMember<R> *__restrict__ mem, const int2 *__restrict__ tasks,
+                                                    int ntasks) {
   using C = typename CplxOf<R>::T;
   C *sm = dyn_smem<C>() + (threadIdx.x >> 5) * ens_warp_region();
   for (int i = blockIdx.x; i < ntasks; i += gridDim.x) {
@@ -75,18 +77,18 @@ __global__ void __launch_bounds__(128) k2e_xpass(const EnsMember<R> *__restrict_
     const Geo g = mem[tk.x].g;
     const StepBufs<R> b = mem[tk.x].b;
     switch (g.N) {
-      case 64: xpass_2d_unit<R, 64, 4>(g, b.yb, b.tw, tk.y, sm); break;
-      case 128: xpass_2d_unit<R, 128, 4>(g, b.yb, b.tw, tk.y, sm); break;
-      case 256: xpass_2d_unit<R, 256, 4>(g, b.yb, b.tw, tk.y, sm); break;
-      default: xpass_2d_unit<R, 512, 4>(g, b.yb, b.tw, tk.y, sm); break;
+      case 64: xpass_2d_unit<R, 64, XW>(g, b.yb, b.tw, tk.y, sm); break;
+      case 128: xpass_2d_unit<R, 128, XW>(g, b.yb, b.tw, tk.y, sm); break;
+      case 256: xpass_2d_unit<R, 256, XW>(g, b.yb, b.tw, tk.y, sm); break;
+      default: xpass_2d_unit<R, 512, XW>(g, b.yb, b.tw, tk.y, sm); break;
     }
     __syncwarp();
   }
 }
 
-template <typename R, int MODE>
-__global__ void __launch_bounds__(256) k2e_fwd1(const EnsMember<R> *__restrict__ mem, const int2 *__restrict__ tasks,
-                                               int ntasks) {
+template <typename R, int MODE, int YT = 256>
+__global__ void __launch_bounds__(YT) k2e_fwd1(const EnsMember<R> *__restrict__ mem, const int2 *__restrict__ tasks,
+                                              int ntasks) {
   using C = typename CplxOf<R>::T;
   C *sm = dyn_smem<C>();
   for (int i = blockIdx.x; i < ntasks; i += gridDim.x) {
@@ -94,64 +96,88 @@ __global__ void __launch_bounds__(256) k2e_fwd1(const EnsMember<R> *__restrict__
     const Geo g = mem[tk.x].g;
     const StepBufs<R> b = mem[tk.x].b;
     switch (g.N) {
-      case 64: fwd1_2d_unit<R, 64, ens_w(64), MODE, true>(g, b, tk.y, sm); break;
-      case 128: fwd1_2d_unit<R, 128, ens_w(128), MODE, true>(g, b, tk.y, sm); break;
-      case 256: fwd1_2d_unit<R, 256, ens_w(256), MODE, true>(g, b, tk.y, sm); break;
-      default: fwd1_2d_unit<R, 512, ens_w(512), MODE, true>(g, b, tk.y, sm); break;
+      case 64: fwd1_2d_unit<R, 64, ens_w(64, YT), MODE, true>(g, b, tk.y, sm); break;
+      case 128: fwd1_2d_unit<R, 128, ens_w(128, YT), MODE, true>(g, b, tk.y, sm); break;
+      case 256: fwd1_2d_unit<R, 256, ens_w(256, YT), MODE, true>(g, b, tk.y, sm); break;
+      default: fwd1_2d_unit<R, 512, ens_w(512, YT), MODE, true>(g, b, tk.y, sm); break;
     }
     __syncthreads();
   }
 }
 
-template <typename C>
+template <typename C, int YT = 256>
 constexpr size_t ens_smem_y() {
   size_t m = 0;
-  for (int n = 64; n <= 512; n *= 2) m = std::max(m, col_smem(n, ens_w(n), sizeof(C), 0));
+  for (int n = 64; n <= 512; n *= 2) m = std::max(m, col_smem(n, ens_w(n, YT), sizeof(C), 0));
   return m;
 }
-// x pass: 4 warps, each with its own region
-template <typename C>
+// x pass: XW warps, each with its own region
+template <typename C, int XW = 4>
 constexpr size_t ens_smem_x() {
-  return (size_t)4 * ens_warp_region() * sizeof(C);
+  return (size_t)XW * ens_warp_region() * sizeof(C);
 }
 
 struct EnsLaunch {
   const void *mem;
   const int2 *xt, *yt;
   int nx, ny, gx, gy;
+  int ythreads, xwarps;  // tile shapes: y-pass block threads (256, 512), x-pass warps per block (4, 8)
 };
 
+template <typename R, int YT, int XW>
+void ens_prepare_shape() {
+  using C = typename CplxOf<R>::T;
+  set_smem(k2e_inv1<R, YT>, ens_smem_y<C, YT>());
+  set_smem(k2e_xpass<R, XW>, ens_smem_x<C, XW>());
+  set_smem(k2e_fwd1<R, MODE_RK1, YT>, ens_smem_y<C, YT>());
+  set_smem(k2e_fwd1<R, MODE_RK2, YT>, ens_smem_y<C, YT>());
+  set_smem(k2e_fwd1<R, MODE_RK3, YT>, ens_smem_y<C, YT>());
+  set_smem(k2e_fwd1<R, MODE_RK4, YT>, ens_smem_y<C, YT>());
+}
 template <typename R>
 int ens_prepare() {
-  using C = typename CplxOf<R>::T;
-  set_smem(k2e_inv1<R>, ens_smem_y<C>());
-  set_smem(k2e_xpass<R>, ens_smem_x<C>());
-  set_smem(k2e_fwd1<R, MODE_RK1>, ens_smem_y<C>());
-  set_smem(k2e_fwd1<R, MODE_RK2>, ens_smem_y<C>());
-  set_smem(k2e_fwd1<R, MODE_RK3>, ens_smem_y<C>());
-  set_smem(k2e_fwd1<R, MODE_RK4>, ens_smem_y<C>());
+  ens_prepare_shape<R, 256, 4>();
+  ens_prepare_shape<R, 512, 8>();
   return (int)cudaGetLastError();
 }
 
+template <typename R, int YT>
+void ens_inv1_y(const EnsLaunch &l, cudaStream_t s) {
+  using C = typename CplxOf<R>::T;
+  k2e_inv1<R, YT><<<l.gy, YT, ens_smem_y<C, YT>(), s>>>((const EnsMember<R> *)l.mem, l.yt, l.ny);
+}
 template <typename R>
 int ens_inv1(const EnsLaunch &l, cudaStream_t s) {
-  using C = typename CplxOf<R>::T;
-  k2e_inv1<R><<<l.gy, 256, ens_smem_y<C>(), s>>>((const EnsMember<R> *)l.mem, l.yt, l.ny);
+  if (l.ythreads == 512)
+    ens_inv1_y<R, 512>(l, s);
+  else
+    ens_inv1_y<R, 256>(l, s);
   return (int)cudaGetLastError();
 }
 
-template <typename R>
-int ens_stage(const EnsLaunch &l, int mode, cudaStream_t s) {
+template <typename R, int YT, int XW>
+void ens_stage_shape(const EnsLaunch &l, int mode, cudaStream_t s) {
   using C = typename CplxOf<R>::T;
   const EnsMember<R> *m = (const EnsMember<R> *)l.mem;
-  k2e_xpass<R><<<l.gx, 128, ens_smem_x<C>(), s>>>(m, l.xt, l.nx);
-  const size_t sy = ens_smem_y<C>();
+  k2e_xpass<R, XW><<<l.gx, 32 * XW, ens_smem_x<C, XW>(), s>>>(m, l.xt, l.nx);
+  const size_t sy = ens_smem_y<C, YT>();
   switch (mode) {
-    case MODE_RK1: k2e_fwd1<R, MODE_RK1><<<l.gy, 256, sy, s>>>(m, l.yt, l.ny); break;
-    case MODE_RK2: k2e_fwd1<R, MODE_RK2><<<l.gy, 256, sy, s>>>(m, l.yt, l.ny); break;
-    case MODE_RK3: k2e_fwd1<R, MODE_RK3><<<l.gy, 256, sy, s>>>(m, l.yt, l.ny); break;
-    default: k2e_fwd1<R, MODE_RK4><<<l.gy, 256, sy, s>>>(m, l.yt, l.ny); break;
+    case MODE_RK1: k2e_fwd1<R, MODE_RK1, YT><<<l.gy, YT, sy, s>>>(m, l.yt, l.ny); break;
+    case MODE_RK2: k2e_fwd1<R, MODE_RK2, YT><<<l.gy, YT, sy, s>>>(m, l.yt, l.ny); break;
+    case MODE_RK3: k2e_fwd1<R, MODE_RK3, YT><<<l.gy, YT, sy, s>>>(m, l.yt, l.ny); break;
+    default: k2e_fwd1<R, MODE_RK4, YT><<<l.gy, YT, sy, s>>>(m, l.yt, l.ny); break;
   }
+}
+template <typename R>
+int ens_stage(const EnsLaunch &l, int mode, cudaStream_t s) {
+  if (l.ythreads == 512 && l.xwarps == 8)
+    ens_stage_shape<R, 512, 8>(l, mode, s);
+  else if (l.ythreads == 512)
+    ens_stage_shape<R, 512, 4>(l, mode, s);
+  else if (l.xwarps == 8)
+    ens_stage_shape<R, 256, 8>(l, mode, s);
+  else
+    ens_stage_shape<R, 256, 4>(l, mode, s);
   return (int)cudaGetLastError();
 }
 
@@ -186,6 +212,7 @@ struct ns_ensemble {
   std::map<int, void *> tw, ef, ef2;
   void *mem = nullptr, *xt = nullptr, *yt = nullptr, *staging = nullptr, *diag = nullptr;
   int nx = 0, ny = 0, xb = 4, yb_per_sm = 2, order = 0;
+  int ythreads = 256, xwarps = 4;  // tile shapes of the schedule
   long long diag_scratch = 0;
   int max_bins = 0;
   cudaStream_t own = nullptr, stream = nullptr, cap = nullptr;
@@ -227,7 +254,7 @@ int emalloc(ns_ensemble *e, void **p, size_t bytes) {
   return NS_OK;
 }
 
-int lines_per_unit(int n) { return 4 * (32 / (n / 16)); }
+int lines_per_unit(int n, int xwarps) { return xwarps * (32 / (n / 16)); }
 
 // task lists: order 0 = member by member, 1 = round robin over members
 void build_tasks(const ns_ensemble *e, int order, std::vector<int2> &xt, std::vector<int2> &yt) {
@@ -235,8 +262,9 @@ void build_tasks(const ns_ensemble *e, int order, std::vector<int2> &xt, std::ve
   yt.clear();
   std::vector<int> xu(e->count), yu(e->count);
   for (int m = 0; m < e->count; ++m) {
-    xu[m] = e->n[m] / lines_per_unit(e->n[m]);
-    yu[m] = (e->geo[m].hs + nsk::ens_w(e->n[m]) - 1) / nsk::ens_w(e->n[m]);  // columns >= h are skipped
+    const int w = nsk::ens_w(e->n[m], e->ythreads);
+    xu[m] = e->n[m] / lines_per_unit(e->n[m], e->xwarps);
+    yu[m] = (e->geo[m].hs + w - 1) / w;  // columns >= h are skipped
   }
   auto emit = [&](std::vector<int2> &out, const std::vector<int> &units) {
     if (order == 0) {
@@ -273,6 +301,8 @@ nsk::EnsLaunch launch_of(const ns_ensemble *e) {
   l.ny = e->ny;
   l.gx = std::max(1, std::min(e->nx, e->xb * e->nsm));
   l.gy = std::max(1, std::min(e->ny, e->yb_per_sm * e->nsm));
+  l.ythreads = e->ythreads;
+  l.xwarps = e->xwarps;
   return l;
 }
 
@@ -496,28 +526,39 @@ int ns_ensemble_init(ns_ensemble **out, int count, const int *n, int precision, 
   if ((rc = upload_tasks(e, 0))) return bail(rc);
   if (autotune) {
     // schedule candidates timed on the zero state (every transform costs the
-    // same whatever the data): blocks per SM of each pass and the task order
+    // same whatever the data): the tile shapes (y-pass block of 256 or 512
+    // threads, i.e. kx tiles of W or 2W columns; x-pass blocks of 4 or 8
+    // warps), blocks per SM of each pass and the task order
     float best = 1e30f;
-    int bx = e->xb, by = e->yb_per_sm, bo = 0;
-    for (int order = 0; order < 2; ++order) {
-      if ((rc = upload_tasks(e, order))) return bail(rc);
-      for (int xb : {2, 4, 8})
-        for (int ybp : {1, 2, 4}) {
-          e->xb = xb;
-          e->yb_per_sm = ybp;
-          const float ms = time_stage(e, 3);
-          if (cudaGetLastError() != cudaSuccess) {
-            efail(e, NS_ECUDA, "autotune launch failed");
-            return bail(NS_ECUDA);
-          }
-          if (ms < best) {
-            best = ms;
-            bx = xb;
-            by = ybp;
-            bo = order;
-          }
+    int bx = e->xb, by = e->yb_per_sm, bo = 0, byt = 256, bxw = 4;
+    for (int yt : {256, 512})
+      for (int xw : {4, 8})
+        for (int order = 0; order < 2; ++order) {
+          e->ythreads = yt;
+          e->xwarps = xw;
+          if ((rc = upload_tasks(e, order))) return bail(rc);
+          for (int xb : {1, 2, 4, 8})
+            for (int ybp : {1, 2, 4}) {
+              if (xb * 32 * xw > 2048 || ybp * yt > 2048) continue;  // resident threads per SM
+              e->xb = xb;
+              e->yb_per_sm = ybp;
+              const float ms = time_stage(e, 3);
+              if (cudaGetLastError() != cudaSuccess) {
+                efail(e, NS_ECUDA, "autotune launch failed");
+                return bail(NS_ECUDA);
+              }
+              if (ms < best) {
+                best = ms;
+                bx = xb;
+                by = ybp;
+                bo = order;
+                byt = yt;
+                bxw = xw;
+              }
+            }
         }
-    }
+    e->ythreads = byt;
+    e->xwarps = bxw;
     e->xb = bx;
     e->yb_per_sm = by;
     if ((rc = upload_tasks(e, bo))) return bail(rc);
@@ -550,6 +591,26 @@ int ns_ensemble_set_schedule(ns_ensemble *e, int x_blocks_per_sm, int y_blocks_p
   e->xb = x_blocks_per_sm;
   e->yb_per_sm = y_blocks_per_sm;
   int rc = upload_tasks(e, task_order);
+  if (rc) return rc;
+  drop_graph(e);
+  return NS_OK;
+}
+
+int ns_ensemble_tiles(const ns_ensemble *e, int *y_threads, int *x_warps) {
+  if (!e) return NS_EINVAL;
+  if (y_threads) *y_threads = e->ythreads;
+  if (x_warps) *x_warps = e->xwarps;
+  return NS_OK;
+}
+
+int ns_ensemble_set_tiles(ns_ensemble *e, int y_threads, int x_warps) {
+  if (!e || (y_threads != 256 && y_threads != 512) || (x_warps != 4 && x_warps != 8))
+    return e ? efail(e, NS_EINVAL, "ns_ensemble_set_tiles: y_threads 256|512, x_warps 4|8") : NS_EINVAL;
+  DevGuardE dg(e->dev);
+  ENS_CK(e, cudaStreamSynchronize(e->stream));
+  e->ythreads = y_threads;
+  e->xwarps = x_warps;
+  int rc = upload_tasks(e, e->order);
   if (rc) return rc;
   drop_graph(e);
   return NS_OK;

@@ -22,7 +22,6 @@
 // simulations": FFT, RK4, curl, vector product, projection).
 #pragma once
 #include <cuda.h>  // CUtensorMap (a kernel parameter type; no driver calls here)
-#include <cstdlib>
 
 #include "ns_fft.cuh"
 #include "ns_internal.h"
@@ -1783,21 +1782,13 @@ struct Fwd1T {
     }
   }
 };
-inline int fwd1_variant() {
-  static int v = -1;
-  if (v < 0) {
-    const char *e = std::getenv("NS_FWD1");
-    v = e ? std::atoi(e) : 1;
-  }
-  return v;
-}
-// 512 points: 16 columns (128-byte rows), 1024 threads, one block per SM
-// (fwd1 1.146 -> 1.036 ms per launch against the register-resident form)
+// The shape used: 16 columns (128-byte rows) with the next field prefetched
+// and two rows of RK operands in flight; 512 points: 1024 threads, one block
+// per SM (fwd1 1.146 -> 1.034 ms per launch against the register-resident
+// form); 256 points: 512 threads, two blocks per SM (0.154 -> 0.148 ms;
+// 32 columns: 0.164 ms).
 template <typename R, int N>
-struct Fwd1Pick {
-  using A = Fwd1T<R, N, (N == 512 ? 16 : 16), true, 2, (N == 512 ? 1 : 2)>;
-  using B = Fwd1T<R, N, (N == 512 ? 16 : 32), true, 2, 1>;
-};
+using Fwd1Pick = Fwd1T<R, N, 16, true, 2, (N == 512 ? 1 : 2)>;
 
 template <typename R, int N>
 struct Launch3 {
@@ -1842,8 +1833,10 @@ struct Launch3 {
     const C *tw = (const C *)a.tw;
     switch (op) {
       case OP_PREPARE:
-        if constexpr (XW) set_smem(k3_xpass_w<R, N, XW_WPB>, SM_XW);
-        if constexpr (XP) set_smem(k3_xpass_p<N, XP_G>, SM_XPP);
+        if constexpr (XP)
+          set_smem(k3_xpass_p<N, XP_G>, SM_XPP);
+        else if constexpr (XW)
+          set_smem(k3_xpass_w<R, N, XW_WPB>, SM_XW);
         set_smem(k3_inv1<R, N, WL, true>, SM_L);
         set_smem(k3_inv1<R, N, WL, false>, SM_L);
         set_smem(k3_inv2<R, N, WYI>, SM_YI);
@@ -1853,17 +1846,17 @@ struct Launch3 {
         if constexpr (!XW) set_smem(k3_xpass<R, N, L>, SM_XP);
         set_smem(k_xfwd_real<R, N, L>, SM_X);
         set_smem(k_xinv_real<R, N, L>, SM_X);
-        set_smem(k3_fwd1<R, N, WH, MODE_RK1, true>, SM_F1S);
-        set_smem(k3_fwd1<R, N, WH, MODE_RK2, true>, SM_F1);
-        set_smem(k3_fwd1<R, N, WH, MODE_RK3, true>, SM_F1);
-        set_smem(k3_fwd1<R, N, WH, MODE_RK4, true>, SM_F1S);
-        set_smem(k3_fwd1<R, N, WH, MODE_RHS, false>, SM_F1S);
-        set_smem(k3_fwd1<R, N, WH, MODE_PROJ, false>, SM_F1S);
-        set_smem(k3_fwd1<R, N, WH, MODE_M1, true>, SM_F1S);
-        set_smem(k3_fwd1<R, N, WH, MODE_M2, true>, SM_F1S);
         if constexpr (F1T) {
-          Fwd1Pick<R, N>::A::prepare();
-          Fwd1Pick<R, N>::B::prepare();
+          Fwd1Pick<R, N>::prepare();
+        } else {
+          set_smem(k3_fwd1<R, N, WH, MODE_RK1, true>, SM_F1S);
+          set_smem(k3_fwd1<R, N, WH, MODE_RK2, true>, SM_F1);
+          set_smem(k3_fwd1<R, N, WH, MODE_RK3, true>, SM_F1);
+          set_smem(k3_fwd1<R, N, WH, MODE_RK4, true>, SM_F1S);
+          set_smem(k3_fwd1<R, N, WH, MODE_RHS, false>, SM_F1S);
+          set_smem(k3_fwd1<R, N, WH, MODE_PROJ, false>, SM_F1S);
+          set_smem(k3_fwd1<R, N, WH, MODE_M1, true>, SM_F1S);
+          set_smem(k3_fwd1<R, N, WH, MODE_M2, true>, SM_F1S);
         }
         break;
       case OP_INV1: {
@@ -1914,35 +1907,28 @@ struct Launch3 {
         break;
       }
       case OP_FWD1: {
-        // persistent: one wave of resident blocks (the kernel walks the tiles)
-        const int tiles = g.c * (g.hs / WH);
-        static int per_sm = 0;
-        if (per_sm == 0) {
-          cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k3_fwd1<R, N, WH, MODE_RK2, true>, T * WH, SM_F1);
-          if (per_sm < 1) per_sm = 1;
-        }
         const StepBufs<R> b = step_bufs<R>(a);
         if constexpr (F1T) {
-          const int var = fwd1_variant();
-          if (var == 1) {
-            Fwd1Pick<R, N>::A::launch(a.mode, a.nsm, g, b, s);
-            break;
+          Fwd1Pick<R, N>::launch(a.mode, a.nsm, g, b, s);
+        } else {
+          // persistent: one wave of resident blocks (the kernel walks the tiles)
+          const int tiles = g.c * (g.hs / WH);
+          static int per_sm = 0;
+          if (per_sm == 0) {
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k3_fwd1<R, N, WH, MODE_RK2, true>, T * WH, SM_F1);
+            if (per_sm < 1) per_sm = 1;
           }
-          if (var == 2) {
-            Fwd1Pick<R, N>::B::launch(a.mode, a.nsm, g, b, s);
-            break;
+          const int grid = cmin(tiles, per_sm * (a.nsm > 0 ? a.nsm : 1));
+          switch (a.mode) {
+            case MODE_RK1: k3_fwd1<R, N, WH, MODE_RK1, true><<<grid, T * WH, SM_F1S, s>>>(g, b); break;
+            case MODE_RK2: k3_fwd1<R, N, WH, MODE_RK2, true><<<grid, T * WH, SM_F1, s>>>(g, b); break;
+            case MODE_RK3: k3_fwd1<R, N, WH, MODE_RK3, true><<<grid, T * WH, SM_F1, s>>>(g, b); break;
+            case MODE_RK4: k3_fwd1<R, N, WH, MODE_RK4, true><<<grid, T * WH, SM_F1S, s>>>(g, b); break;
+            case MODE_RHS: k3_fwd1<R, N, WH, MODE_RHS, false><<<grid, T * WH, SM_F1S, s>>>(g, b); break;
+            case MODE_M1: k3_fwd1<R, N, WH, MODE_M1, true><<<grid, T * WH, SM_F1S, s>>>(g, b); break;
+            case MODE_M2: k3_fwd1<R, N, WH, MODE_M2, true><<<grid, T * WH, SM_F1S, s>>>(g, b); break;
+            default: k3_fwd1<R, N, WH, MODE_PROJ, false><<<grid, T * WH, SM_F1S, s>>>(g, b); break;
           }
-        }
-        const int grid = cmin(tiles, per_sm * (a.nsm > 0 ? a.nsm : 1));
-        switch (a.mode) {
-          case MODE_RK1: k3_fwd1<R, N, WH, MODE_RK1, true><<<grid, T * WH, SM_F1S, s>>>(g, b); break;
-          case MODE_RK2: k3_fwd1<R, N, WH, MODE_RK2, true><<<grid, T * WH, SM_F1, s>>>(g, b); break;
-          case MODE_RK3: k3_fwd1<R, N, WH, MODE_RK3, true><<<grid, T * WH, SM_F1, s>>>(g, b); break;
-          case MODE_RK4: k3_fwd1<R, N, WH, MODE_RK4, true><<<grid, T * WH, SM_F1S, s>>>(g, b); break;
-          case MODE_RHS: k3_fwd1<R, N, WH, MODE_RHS, false><<<grid, T * WH, SM_F1S, s>>>(g, b); break;
-          case MODE_M1: k3_fwd1<R, N, WH, MODE_M1, true><<<grid, T * WH, SM_F1S, s>>>(g, b); break;
-          case MODE_M2: k3_fwd1<R, N, WH, MODE_M2, true><<<grid, T * WH, SM_F1S, s>>>(g, b); break;
-          default: k3_fwd1<R, N, WH, MODE_PROJ, false><<<grid, T * WH, SM_F1S, s>>>(g, b); break;
         }
         break;
       }

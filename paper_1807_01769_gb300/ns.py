@@ -66,6 +66,8 @@ SIGNATURES = {
     "ns_ensemble_init": ([ctypes.POINTER(_P), _I, _P, _I, _D, _D, _I], _I),
     "ns_ensemble_schedule": ([_P, _PI, _PI, _PI], _I),
     "ns_ensemble_set_schedule": ([_P, _I, _I, _I], _I),
+    "ns_ensemble_tiles": ([_P, _PI, _PI], _I),
+    "ns_ensemble_set_tiles": ([_P, _I, _I], _I),
     "ns_ensemble_set_state_spectral": ([_P, _I, _P], _I),
     "ns_ensemble_get_state_spectral": ([_P, _I, _P], _I),
     "ns_ensemble_step": ([_P, _I], _I),
@@ -331,6 +333,15 @@ class Ensemble:
 
     def set_schedule(self, x_blocks: int, y_blocks: int, order: int) -> None:
         _echeck(lib.ns_ensemble_set_schedule(self.ens, x_blocks, y_blocks, order), self.ens)
+
+    def tiles(self):
+        """(y-pass block threads, x-pass warps per block) of the schedule."""
+        a, b = _I(), _I()
+        _echeck(lib.ns_ensemble_tiles(self.ens, ctypes.byref(a), ctypes.byref(b)), self.ens)
+        return a.value, b.value
+
+    def set_tiles(self, y_threads: int, x_warps: int) -> None:
+        _echeck(lib.ns_ensemble_set_tiles(self.ens, int(y_threads), int(x_warps)), self.ens)
 
     def set_state_spectral(self, member: int, spec) -> None:
         s = np.ascontiguousarray(spec, dtype=np.complex128).reshape(self.shapes[member])

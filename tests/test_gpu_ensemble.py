@@ -42,14 +42,23 @@ def test_members_bitwise_equal_single_runs_for_every_schedule(ns, prec):
     u0 = [ic(n, seed) for seed, n in enumerate(sizes)]
     ref = [single(ns, n, prec, nu, dt, steps, u) for n, u in zip(sizes, u0)]
     with ns.Ensemble(sizes, prec, nu=nu, dt=dt, autotune=True) as e:
-        for sched in [None, (2, 1, 0), (8, 4, 1), (4, 2, 1)]:
-            if sched is not None:
+        yt, xw = e.tiles()
+        assert yt in (256, 512) and xw in (4, 8)
+        # the autotuned schedule, then every tile shape with several grid and
+        # order settings
+        cases = [(None, None)] + [((yt, xw), sched) for yt in (256, 512) for xw in (4, 8)
+                                  for sched in [(2, 1, 0), (8, 4, 1), (1, 2, 1)]]
+        for tiles, sched in cases:
+            if tiles is not None:
+                e.set_tiles(*tiles)
                 e.set_schedule(*sched)
             for m, u in enumerate(u0):
                 e.set_state_spectral(m, u)
             e.step(steps)
             for m in range(len(sizes)):
-                assert np.array_equal(e.get_state_spectral(m), ref[m]), (sched, m)
+                assert np.array_equal(e.get_state_spectral(m), ref[m]), (tiles, sched, m)
+        with pytest.raises(ns.NSError):
+            e.set_tiles(384, 4)
 
 
 def test_members_match_oracle(ns, orc):
@@ -99,10 +108,11 @@ def test_all_64_members_bitwise_under_mixed_schedules(ns):
     u0 = [ic(n, seed) for seed, n in enumerate(sizes)]
     ref = [single(ns, n, FP32, nu, dt, steps, u) for n, u in zip(sizes, u0)]
     with ns.Ensemble(sizes, FP32, nu=nu, dt=dt, autotune=False) as e:
-        for sched in [(4, 2, 0), (8, 4, 1), (1, 1, 0)]:
+        for tiles, sched in [((256, 4), (4, 2, 0)), ((512, 8), (8, 4, 1)), ((512, 4), (1, 1, 0))]:
+            e.set_tiles(*tiles)
             e.set_schedule(*sched)
             for m, u in enumerate(u0):
                 e.set_state_spectral(m, u)
             e.step(steps)
             bad = [m for m in range(len(sizes)) if not np.array_equal(e.get_state_spectral(m), ref[m])]
-            assert not bad, (sched, bad[:8])
+            assert not bad, (tiles, sched, bad[:8])
