@@ -29,6 +29,7 @@
 #include <vector>
 
 #include "ns.h"
+#include "ns_tc.cuh"
 
 namespace {
 
@@ -113,6 +114,176 @@ __global__ void __launch_bounds__(TILE *TILE) conv_fwd(const TIN *__restrict__ x
       out[o] = (TOUT)acc[co];
     }
   }
+}
+
+// ------------------------------------------- 32 -> 32 on the tensor cores ---
+// The same convolution as conv_fwd<32, 32, EPI> as an implicit GEMM on
+// tcgen05: per image row segment of 128 pixels, D[pixel][co] = sum over the 9
+// taps of A_tap[pixel][ci] B_tap[ci][co] with A_tap(p, ci) = x[ci](p + off(tap))
+// and B_tap(ci, co) = w[co][ci][tap]; M = 128 pixels, N = 32, K = 32 per tap
+// (two MMAs of K = 16), FP32 accumulation in tensor memory.  BF16 inputs are
+// exact operands; FP32 inputs (the data gradient) are split x = hi + lo into
+// two BF16 operands and multiplied separately (relative error ~2^-17).
+//
+// A block owns a strip of 128 columns of one image over a range of rows and
+// walks down it: a ring of four input rows lives in shared memory as
+// [slot][channel chunk c][pixel q][8 channels] (16 bytes per (c, q), halo
+// pixels q = 0 and 129 wrap periodically), so the A operand of a tap is the
+// K-major descriptor at slot (y + dy) mod 4, pixel 1 + dx: leading byte
+// offset = the chunk stride (along K), stride byte offset = 128 (8 pixels
+// along M).  Row y + 1 is loaded while the MMAs of row y run; the tensor
+// memory holds two accumulators, so the epilogue of row y - 1 (bias, GELU or
+// GELU', planar stores) overlaps the MMAs of row y.  One thread issues the
+// MMAs and commits them to the mbarrier of their accumulator; every wait is
+// bounded (on expiry the block records code 3 in the error word and leaves).
+namespace ctc {
+constexpr int kQ = 130;                        // pixels of a ring row (128 + halo)
+constexpr unsigned kChunk = kQ * 16;           // bytes of one channel chunk of a row
+constexpr unsigned kSlot = 4 * kChunk;         // one ring row: 4 chunks of 8 channels
+constexpr unsigned kRing = 4 * kSlot;          // four rows
+constexpr unsigned kWB = 9 * 32 * 32 * 2;      // B operands of the 9 taps
+constexpr unsigned kIdesc = nsk::tc::idesc_bf16(128, 32, false);
+__host__ __device__ constexpr unsigned smem_bytes(bool split) { return kWB + (split ? 2 : 1) * kRing + 128; }
+// byte offset of w[co][ci][tap] in the B tiles: K-major [tap][co / 8][ci / 8][co % 8][ci % 8]
+__device__ __forceinline__ unsigned woff(int tap, int co, int ci) {
+  return (unsigned)(tap * 2048 + (co >> 3) * 512 + (ci >> 3) * 128 + (co & 7) * 16 + (ci & 7) * 2);
+}
+}  // namespace ctc
+
+template <int EPI, typename TIN, typename TOUT>
+__global__ void __launch_bounds__(128) conv32_tc(const TIN *__restrict__ x, const bf16 *__restrict__ w,
+                                                 const float *__restrict__ bias, const bf16 *__restrict__ zin,
+                                                 bf16 *__restrict__ zout, TOUT *__restrict__ out, int H, int W,
+                                                 int rows_per_block, int *err) {
+  using namespace ctc;
+  namespace tc = nsk::tc;
+  constexpr bool SPLIT = sizeof(TIN) == 4;
+  extern __shared__ __align__(128) unsigned char csmb[];
+  unsigned char *wb = csmb, *ring = csmb + kWB;  // ring hi, then ring lo (SPLIT)
+  __shared__ __align__(8) unsigned long long bars[2];
+  __shared__ unsigned tslot;
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int strips = W / 128, segs = (H + rows_per_block - 1) / rows_per_block;
+  const int b = blockIdx.x / (strips * segs), rem = blockIdx.x % (strips * segs);
+  const int x0 = (rem / segs) * 128, y0 = (rem % segs) * rows_per_block;
+  const int y1 = min(H, y0 + rows_per_block);
+  const long long img = (long long)H * W;
+  const unsigned sbase = nsk::smem_addr(csmb);
+  for (int i = tid; i < 9 * 32 * 32; i += 128) {
+    const int co = i / 288, r = i % 288, ci = r / 9, tap = r % 9;  // w[co][ci][tap]
+    *reinterpret_cast<bf16 *>(wb + woff(tap, co, ci)) = w[i];
+  }
+  if (warp == 0) tc::tmem_alloc(&tslot, 64);
+  if (tid == 0) {
+    nsk::mbar_init(&bars[0], 1);
+    nsk::mbar_init(&bars[1], 1);
+  }
+  // input row yy (wrapped) into ring slot yy mod 4: thread item (chunk c,
+  // pixel q) gathers 8 channels (one coalesced load per channel across the
+  // warp) into one 16-byte store (two for a split input)
+  auto load_row = [&](int yy) {
+    const int gy = ((yy % H) + H) % H, slot = yy & 3;
+    for (int i = tid; i < 4 * kQ; i += 128) {
+      const int c = i / kQ, q = i % kQ;
+      const int gx = (x0 - 1 + q + W) % W;
+      const TIN *src = x + ((long long)b * 32 + 8 * c) * img + (long long)gy * W + gx;
+      float v[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) v[j] = ldf(src + j * img);
+      const unsigned o = slot * kSlot + c * kChunk + q * 16;
+      if constexpr (SPLIT) {
+        uint4 hi, lo;
+        tc::split2(v[0], v[1], hi.x, lo.x);
+        tc::split2(v[2], v[3], hi.y, lo.y);
+        tc::split2(v[4], v[5], hi.z, lo.z);
+        tc::split2(v[6], v[7], hi.w, lo.w);
+        *reinterpret_cast<uint4 *>(ring + o) = hi;
+        *reinterpret_cast<uint4 *>(ring + kRing + o) = lo;
+      } else {
+        uint4 hv;
+        const __nv_bfloat162 p0 = __floats2bfloat162_rn(v[0], v[1]), p1 = __floats2bfloat162_rn(v[2], v[3]),
+                             p2 = __floats2bfloat162_rn(v[4], v[5]), p3 = __floats2bfloat162_rn(v[6], v[7]);
+        hv.x = *reinterpret_cast<const unsigned *>(&p0);
+        hv.y = *reinterpret_cast<const unsigned *>(&p1);
+        hv.z = *reinterpret_cast<const unsigned *>(&p2);
+        hv.w = *reinterpret_cast<const unsigned *>(&p3);
+        *reinterpret_cast<uint4 *>(ring + o) = hv;
+      }
+    }
+  };
+  // epilogue of output row yy from accumulator buf: this thread = pixel x0 + tid
+  auto epilogue = [&](int yy, int buf) {
+    float acc[32];
+    tc::tmem_ld<32>(tslot + ((unsigned)(warp * 32) << 16) + buf * 32, acc);
+    tc::tmem_wait_ld();
+    const long long p = (long long)yy * W + x0 + tid;
+#pragma unroll
+    for (int co = 0; co < 32; ++co) {
+      const long long o = ((long long)b * 32 + co) * img + p;
+      if (EPI == EPI_GELU) {
+        const float v = acc[co] + (bias ? bias[co] : 0.0f);
+        zout[o] = __float2bfloat16(v);
+        out[o] = (TOUT)__float2bfloat16(gelu_f(v));
+      } else if (EPI == EPI_GELU_BWD) {
+        out[o] = (TOUT)(acc[co] * gelu_d(__bfloat162float(zin[o])));
+      } else {
+        out[o] = (TOUT)(acc[co] + (bias ? bias[co] : 0.0f));
+      }
+    }
+  };
+  load_row(y0 - 1);
+  load_row(y0);
+  unsigned ph[2] = {0u, 0u};
+  bool bad = false;
+  for (int y = y0; y < y1; ++y) {
+    load_row(y + 1);  // its slot was last read by the MMAs of row y - 2, already waited for
+    tc::fence_async_smem();
+    tc::fence_before();
+    if (__syncthreads_or(bad)) break;  // ring row visible; epilogue reads of this accumulator done
+    tc::fence_after();
+    const int buf = y & 1;
+    if (tid == 0) {
+      const unsigned d = tslot + buf * 32;
+      int n = 0;
+#pragma unroll 1
+      for (int tap = 0; tap < 9; ++tap) {
+        const int dy = tap / 3 - 1, dx = tap % 3 - 1;
+        const unsigned a0 = sbase + kWB + ((y + dy) & 3) * kSlot + (1 + dx) * 16;
+#pragma unroll
+        for (int part = 0; part < (SPLIT ? 2 : 1); ++part)
+#pragma unroll
+          for (int kh = 0; kh < 2; ++kh) {
+            const unsigned a = a0 + part * kRing + kh * 2 * kChunk;
+            const unsigned bo = sbase + tap * 2048 + kh * 256;
+            tc::mma(d, tc::sdesc(a, kChunk, 128), tc::sdesc(bo, 128, 512), kIdesc, n++ != 0);
+          }
+      }
+      tc::commit(&bars[buf]);
+    }
+    if (y > y0) {
+      const int pb = (y - 1) & 1;
+      bad |= !nsk::mbar_wait_bounded(&bars[pb], ph[pb]);
+      ph[pb] ^= 1u;
+      tc::fence_after();
+      if (!bad) epilogue(y - 1, pb);
+    }
+  }
+  // the last row
+  if (!bad && y1 > y0) {
+    const int pb = (y1 - 1) & 1;
+    bad |= !nsk::mbar_wait_bounded(&bars[pb], ph[pb]);
+    tc::fence_after();
+    if (!bad) epilogue(y1 - 1, pb);
+  }
+  if (bad) {
+    if (tid == 0) atomicExch(err, 3);
+    // MMAs still in flight may write the accumulators: a last bounded wait on both
+    nsk::mbar_wait_bounded(&bars[0], ph[0]);
+    nsk::mbar_wait_bounded(&bars[1], ph[1]);
+  }
+  tc::fence_before();
+  __syncthreads();
+  if (warp == 0) tc::tmem_dealloc(tslot, 64);
 }
 
 // dw[co][ci][k] += sum_b sum_p dz[b][co][p] a[b][ci][p + off(k)];  db[co] += sum dz[b][co][p]
@@ -254,6 +425,8 @@ struct ns_cnn {
   bf16 *wt[4] = {nullptr, nullptr, nullptr, nullptr};             // flipped weights
   bf16 *z[3] = {nullptr, nullptr, nullptr}, *a[3] = {nullptr, nullptr, nullptr};
   float *y = nullptr, *dy = nullptr, *dza = nullptr, *dzb = nullptr, *loss = nullptr;
+  int *errw = nullptr;  // device error word of the tensor-core convolutions (bounded waits)
+  int nsm = 1;
   int step = 0;
   std::string err;
 };
@@ -287,6 +460,22 @@ int launch_fwd(const TIN *x, const bf16 *w, const float *bias, const bf16 *zin, 
   return (int)cudaGetLastError();
 }
 
+// the 32 -> 32 convolution on the tensor cores when the width is a multiple
+// of 128 (row segments of 128 pixels), else conv_fwd on the CUDA cores; rows
+// per block chosen so that about two blocks per SM are launched
+template <int EPI, typename TIN, typename TOUT>
+int launch_c32(const ns_cnn *c, const TIN *x, const bf16 *w, const float *bias, const bf16 *zin, bf16 *zout, TOUT *out,
+               int B, int H, int W, cudaStream_t s) {
+  if (W % 128 != 0) return launch_fwd<32, 32, EPI, TIN, TOUT>(x, w, bias, zin, zout, out, B, H, W, s);
+  const int strips = W / 128;
+  const int segs = std::max(1, std::min(H, (2 * c->nsm + B * strips - 1) / (B * strips)));
+  const int rows = (H + segs - 1) / segs;
+  const int blocks = B * strips * ((H + rows - 1) / rows);
+  conv32_tc<EPI, TIN, TOUT><<<blocks, 128, ctc::smem_bytes(sizeof(TIN) == 4), s>>>(x, w, bias, zin, zout, out, H, W,
+                                                                                   rows, c->errw);
+  return (int)cudaGetLastError();
+}
+
 template <int CIN, int COUT, typename TA>
 int launch_bww(const TA *a, const float *dz, float *dw, float *db, int B, int H, int W, cudaStream_t s) {
   conv_bwd_weight<CIN, COUT, TA><<<dim3(W / 64, H / 64, B), 256, bww_smem(CIN, COUT), s>>>(a, dz, dw, db, H, W);
@@ -314,6 +503,10 @@ void set_attributes() {
   bww_attr<32, 1, bf16>();
   bww_attr<32, 32, bf16>();
   bww_attr<1, 32, float>();
+  cudaFuncSetAttribute(conv32_tc<EPI_GELU, bf16, bf16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)ctc::smem_bytes(false));
+  cudaFuncSetAttribute(conv32_tc<EPI_GELU_BWD, float, float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)ctc::smem_bytes(true));
 }
 
 // forward pass through all layers; keeps z_l, a_l for the backward pass
@@ -324,11 +517,11 @@ int forward(ns_cnn *c, const float *x, int B, cudaStream_t s) {
   if ((rc = launch_fwd<1, 32, EPI_GELU, float, bf16>(x, c->wb[0], p + c->boff[0], nullptr, c->z[0], c->a[0], B, H, W,
                                                       s)))
     return rc;
-  if ((rc = launch_fwd<32, 32, EPI_GELU, bf16, bf16>(c->a[0], c->wb[1], p + c->boff[1], nullptr, c->z[1], c->a[1], B,
-                                                      H, W, s)))
+  if ((rc = launch_c32<EPI_GELU, bf16, bf16>(c, c->a[0], c->wb[1], p + c->boff[1], nullptr, c->z[1], c->a[1], B, H,
+                                              W, s)))
     return rc;
-  if ((rc = launch_fwd<32, 32, EPI_GELU, bf16, bf16>(c->a[1], c->wb[2], p + c->boff[2], nullptr, c->z[2], c->a[2], B,
-                                                      H, W, s)))
+  if ((rc = launch_c32<EPI_GELU, bf16, bf16>(c, c->a[1], c->wb[2], p + c->boff[2], nullptr, c->z[2], c->a[2], B, H,
+                                              W, s)))
     return rc;
   return launch_fwd<32, 1, EPI_LINEAR, bf16, float>(c->a[2], c->wb[3], p + c->boff[3], nullptr, nullptr, c->y, B, H,
                                                     W, s);
@@ -351,14 +544,24 @@ int backward(ns_cnn *c, const float *x, const float *t, int B, cudaStream_t s) {
                                                           s)))
     return rc;  // dz2
   if ((rc = launch_bww<32, 32, bf16>(c->a[1], c->dza, g + c->woff[2], g + c->boff[2], B, H, W, s))) return rc;
-  if ((rc = launch_fwd<32, 32, EPI_GELU_BWD, float, float>(c->dza, c->wt[2], nullptr, c->z[1], nullptr, c->dzb, B, H,
-                                                           W, s)))
+  if ((rc = launch_c32<EPI_GELU_BWD, float, float>(c, c->dza, c->wt[2], nullptr, c->z[1], nullptr, c->dzb, B, H, W,
+                                                    s)))
     return rc;  // dz1
   if ((rc = launch_bww<32, 32, bf16>(c->a[0], c->dzb, g + c->woff[1], g + c->boff[1], B, H, W, s))) return rc;
-  if ((rc = launch_fwd<32, 32, EPI_GELU_BWD, float, float>(c->dzb, c->wt[1], nullptr, c->z[0], nullptr, c->dza, B, H,
-                                                           W, s)))
+  if ((rc = launch_c32<EPI_GELU_BWD, float, float>(c, c->dzb, c->wt[1], nullptr, c->z[0], nullptr, c->dza, B, H, W,
+                                                    s)))
     return rc;  // dz0
   return launch_bww<1, 32, float>(x, c->dza, g + c->woff[0], g + c->boff[0], B, H, W, s);
+}
+
+// the device error word (a tensor-core convolution whose bounded wait expired
+// wrote a nonzero code): NS_ETIMEOUT once, then cleared
+int check_err(ns_cnn *c) {
+  int e = 0;
+  CNN_CK(c, cudaMemcpy(&e, c->errw, sizeof(int), cudaMemcpyDeviceToHost));
+  if (e == 0) return NS_OK;
+  cudaMemset(c->errw, 0, sizeof(int));
+  return cfail(c, NS_ETIMEOUT, "tensor-core convolution: a bounded wait expired");
 }
 
 int refresh_bf16(ns_cnn *c, cudaStream_t s) {
@@ -411,8 +614,14 @@ int ns_cnn_init(ns_cnn **out, int height, int width, int max_batch, unsigned lon
       cudaMalloc(&c->m, sizeof(float) * c->nparams) || cudaMalloc(&c->v, sizeof(float) * c->nparams) ||
       cudaMalloc(&c->y, sizeof(float) * img) || cudaMalloc(&c->dy, sizeof(float) * img) ||
       cudaMalloc(&c->dza, sizeof(float) * img * 32) || cudaMalloc(&c->dzb, sizeof(float) * img * 32) ||
-      cudaMalloc(&c->loss, sizeof(float)))
+      cudaMalloc(&c->loss, sizeof(float)) || cudaMalloc(&c->errw, sizeof(int)) ||
+      cudaMemset(c->errw, 0, sizeof(int)))
     return bail("allocation failed");
+  {
+    int dev = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (c->nsm < 1) c->nsm = 1;
+  }
   for (int l = 0; l < 4; ++l)
     if (cudaMalloc(&c->wb[l], sizeof(bf16) * ci[l] * co[l] * 9) || cudaMalloc(&c->wt[l], sizeof(bf16) * ci[l] * co[l] * 9))
       return bail("allocation failed");
@@ -462,7 +671,7 @@ int ns_cnn_gradients(ns_cnn *c, const float *x_dev, const float *t_dev, int batc
   if (rc) return cfail(c, NS_ECUDA, "ns_cnn_gradients: launch failed");
   CNN_CK(c, cudaMemcpy(grad_host, c->g, sizeof(float) * c->nparams, cudaMemcpyDeviceToHost));
   CNN_CK(c, cudaMemcpy(loss, c->loss, sizeof(float), cudaMemcpyDeviceToHost));
-  return NS_OK;
+  return check_err(c);
 }
 
 int ns_cnn_train_step(ns_cnn *c, const float *x_dev, const float *t_dev, int batch, float lr, float *loss_out,
@@ -482,6 +691,7 @@ int ns_cnn_train_step(ns_cnn *c, const float *x_dev, const float *t_dev, int bat
   if (loss_out) {
     CNN_CK(c, cudaMemcpyAsync(loss_out, c->loss, sizeof(float), cudaMemcpyDeviceToHost, s));
     CNN_CK(c, cudaStreamSynchronize(s));
+    return check_err(c);
   }
   return NS_OK;
 }
@@ -504,7 +714,7 @@ int ns_f32_axpy_f64(const float *src_dev, const double *base_dev, double *dst_de
 void ns_cnn_destroy(ns_cnn *c) {
   if (!c) return;
   cudaDeviceSynchronize();
-  void *ptrs[] = {c->p, c->g, c->m, c->v, c->y, c->dy, c->dza, c->dzb, c->loss};
+  void *ptrs[] = {c->p, c->g, c->m, c->v, c->y, c->dy, c->dza, c->dzb, c->loss, c->errw};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   for (int l = 0; l < 4; ++l) {

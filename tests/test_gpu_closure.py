@@ -116,6 +116,38 @@ def test_cnn_adam_first_step(ns, cn):
     assert agree.mean() > 0.995, agree.mean()
 
 
+def test_cnn_tensor_core_path_equals_cuda_core_path(ns, cn):
+    """The 32 -> 32 convolutions of widths that are multiples of 128 run on the
+    tensor cores (tcgen05 implicit GEMM), the others on the CUDA cores.  The
+    network is periodic and translation-equivariant, so a 256-wide input made
+    of a 64-wide one tiled four times must give the tiled 64-wide output and
+    gradients of the same network on the tiled batch: BF16 products are exact
+    on both paths, only the FP32 summation order (and, where it flips a BF16
+    rounding of an activation, that rounding) differs."""
+    p = params(cn, 600)
+    h = 64
+    x = inputs.random_phys((2, h, 64), 601)
+    t = inputs.random_phys((2, h, 64), 602)
+    xt, tt = np.tile(x, (1, 1, 4)), np.tile(t, (1, 1, 4))
+    with ns.CNN(h, 64, max_batch=2, seed=1) as a, ns.CNN(h, 256, max_batch=2, seed=1) as b:
+        a.set_params(p)
+        b.set_params(p)
+        xd, xtd = dev(x), dev(xt)
+        ya = torch.empty((2, h, 64), dtype=torch.float32, device="cuda")
+        yb = torch.empty((2, h, 256), dtype=torch.float32, device="cuda")
+        a.forward(xd.data_ptr(), ya.data_ptr(), 2)
+        b.forward(xtd.data_ptr(), yb.data_ptr(), 2)
+        torch.cuda.synchronize()
+        ya, yb = ya.cpu().numpy(), yb.cpu().numpy()
+        assert rel(yb, np.tile(ya, (1, 1, 4))) < 2e-3, rel(yb, np.tile(ya, (1, 1, 4)))
+        td, ttd = dev(t), dev(tt)
+        ga, la = a.gradients(xd.data_ptr(), td.data_ptr(), 2)
+        gb, lb = b.gradients(xtd.data_ptr(), ttd.data_ptr(), 2)
+    # the mean squared error over the tiled batch equals the untiled one
+    assert abs(lb - la) < 1e-4 * la
+    assert rel(gb, ga) < 3e-3, rel(gb, ga)
+
+
 def test_cnn_training_fits_a_teacher(ns, cn):
     """Teacher-student: targets from the oracle network with fixed parameters;
     a differently initialised student trained by the GPU Adam loop fits them."""
