@@ -24,8 +24,12 @@ and shuffles snapshot order.
 
 Fallback: a closed run checks the coarse enstrophy every ``check_every``
 steps; if it is not finite or exceeds ``blowup`` times its starting value,
-the run restores the last good state and continues as the plain coarse
-solve (``fell_back`` is set).
+the run restores the last good state and continues without the network:
+by default as the plain fine-grid solve, restarted from the last good coarse
+state prolonged to the fine grid (zero padding of the modes the coarse grid
+lacks), with the coarse view of the run the fine state filtered back to the
+coarse modes; with ``fallback="coarse"`` as the plain coarse solve.
+``fell_back`` is set either way.
 """
 from __future__ import annotations
 
@@ -81,6 +85,20 @@ def restrict_2d(spec: np.ndarray, n_from: int, n_to: int) -> np.ndarray:
     k = np.where(i <= kc_t, i, i - c_t)
     j = np.where(k >= 0, k, k + c_f)
     return np.ascontiguousarray(spec[j][:, :h_t])
+
+
+def prolong_2d(spec: np.ndarray, n_from: int, n_to: int) -> np.ndarray:
+    """The truncated (c, h) spectrum of an n_from grid placed into the
+    truncated spectrum of a finer n_to grid, zero on every mode the coarse
+    grid does not hold (index selection only; restrict_2d undoes it)."""
+    kc_f, c_f, h_f = inputs.truncation(n_from)
+    kc_t, c_t, h_t = inputs.truncation(n_to)
+    out = np.zeros((c_t, h_t), np.complex128)
+    i = np.arange(c_f)
+    k = np.where(i <= kc_f, i, i - c_f)
+    j = np.where(k >= 0, k, k + c_t)
+    out[j, :h_f] = spec
+    return out
 
 
 def forcing(cfg: KolmogorovConfig, n: int) -> np.ndarray:
@@ -209,9 +227,13 @@ class ClosureSolver:
     replayed."""
 
     def __init__(self, cfg: KolmogorovConfig, tr: Trained, check_every: int = 50, blowup: float = 100.0,
-                 use_graph: bool = True):
+                 use_graph: bool = True, fallback: str = "fine"):
         import torch
 
+        if fallback not in ("fine", "coarse"):
+            raise ValueError("fallback must be 'fine' or 'coarse'")
+        self.fallback = fallback
+        self.fine = None  # the plain fine-grid solve, created on fallback
         self.cfg, self.tr = cfg, tr
         n = cfg.n_coarse
         self.n2 = n * n
@@ -232,16 +254,43 @@ class ClosureSolver:
 
     def close(self):
         self.solver.close()
+        if self.fine is not None:
+            self.fine.close()
+            self.fine = None
+
+    @property
+    def on_fine(self) -> bool:
+        """True once the run has handed over to the plain fine-grid solve."""
+        return self.fine is not None
 
     def set_state_spectral(self, spec):
+        if self.fine is not None:
+            self.fine.close()
+            self.fine = None
+        self._plain_forcing()
         self.solver.set_state_spectral(spec)
         self.stream.synchronize()
         self._good = np.array(spec, copy=True)
         self._omega0 = self.solver.diagnostics()[1]
         self.fell_back = False
 
+    def _coarse_view(self):
+        """The coarse workspace holding the current coarse view of the run:
+        after a hand-over to the fine grid, the fine state filtered to the
+        coarse modes."""
+        if self.fine is not None:
+            self.solver.set_state_spectral(
+                restrict_2d(self.fine.get_state_spectral(), self.cfg.n_fine, self.cfg.n_coarse))
+        return self.solver
+
     def get_state_spectral(self):
-        return self.solver.get_state_spectral()
+        return self._coarse_view().get_state_spectral()
+
+    def diagnostics(self):
+        return self._coarse_view().diagnostics()
+
+    def energy_spectrum(self):
+        return self._coarse_view().energy_spectrum()
 
     def _correct(self):
         s, st = self.solver.state, self.stream.cuda_stream
@@ -294,10 +343,17 @@ class ClosureSolver:
         ns._check(ns.lib.ns_set_forcing_phys_device(s, ns.ctypes.c_void_p(self.F.data_ptr())), s)
 
     def step(self, nsteps: int):
+        """Advance by nsteps coarse steps (after a hand-over to the fine grid:
+        the same time in fine steps)."""
+        if self.fine is not None:
+            self.fine.step(nsteps * self.cfg.ratio)
+            return
         done = 0
         while done < nsteps:
             chunk = min(self.check_every, nsteps - done)
-            if self.fell_back:
+            if self.fine is not None:
+                self.fine.step(chunk * self.cfg.ratio)
+            elif self.fell_back:
                 self.solver.step(chunk)
             else:
                 self._run_corrected(chunk)
@@ -314,6 +370,9 @@ class ClosureSolver:
                     self.fell_back = True
                     self._plain_forcing()
                     self.solver.set_state_spectral(self._good)
+                    if self.fallback == "fine":
+                        self.fine = fine_solver(self.cfg)
+                        self.fine.set_state_spectral(prolong_2d(self._good, self.cfg.n_coarse, self.cfg.n_fine))
 
 
 def rel_l2(a: np.ndarray, b: np.ndarray) -> float:
@@ -349,16 +408,16 @@ def a_posteriori(cfg: KolmogorovConfig, tr: Trained, seed: int, t_eval: float, e
                 ref = restrict_2d(fine.get_state_spectral(), cfg.n_fine, nc)
                 filtered.set_state_spectral(ref)
                 wp, wq = plain.get_state_spectral(), closed.get_state_spectral()
-                er, ep, eq = filtered.energy_spectrum(), plain.energy_spectrum(), closed.solver.energy_spectrum()
+                er, ep, eq = filtered.energy_spectrum(), plain.energy_spectrum(), closed.energy_spectrum()
 
                 def spec_err(e):
                     return float(np.mean(np.abs(np.log(np.maximum(e[sh], 1e-300) / np.maximum(er[sh], 1e-300)))))
 
                 row = {"t": round(t, 6), "err_plain": rel_l2(wp, ref), "err_closure": rel_l2(wq, ref),
                        "enstrophy_fine": filtered.diagnostics()[1], "enstrophy_plain": plain.diagnostics()[1],
-                       "enstrophy_closure": closed.solver.diagnostics()[1],
+                       "enstrophy_closure": closed.diagnostics()[1],
                        "spec_err_plain": spec_err(ep), "spec_err_closure": spec_err(eq),
-                       "fell_back": closed.fell_back}
+                       "fell_back": closed.fell_back, "on_fine": closed.on_fine}
                 rows.append(row)
                 if log:
                     log(json.dumps(row))

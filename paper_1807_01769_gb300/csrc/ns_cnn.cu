@@ -17,7 +17,10 @@
 // weights, with the GELU derivative of the layer below fused in);
 // conv_bwd_weight (each block sums a 64x64 region in 16x16 sub-tiles and adds
 // its partial sums to the FP32 gradient with atomics: order-dependent in the
-// last bits, not bitwise reproducible); elementwise MSE and Adam.
+// last bits, not bitwise reproducible); elementwise MSE and Adam.  The 32 ->
+// 32 convolutions of widths that are multiples of 128 (forward, data and
+// weight gradients) run on the tensor cores instead (conv32_tc,
+// conv32_wgrad_tc below).
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -286,6 +289,147 @@ __global__ void __launch_bounds__(128) conv32_tc(const TIN *__restrict__ x, cons
   if (warp == 0) tc::tmem_dealloc(tslot, 64);
 }
 
+// Weight gradient of a 32 -> 32 layer on the tensor cores:
+//   dw[co][ci][tap] += sum_p dz[co](p) a[ci](p + off(tap)),  db[co] += sum_p dz[co](p)
+// per tap a GEMM D_tap[co][ci] = sum over pixels (K) of A[co][p] B_tap[p][ci],
+// both operands MN-major (8 channels contiguous per pixel): A from the
+// split dz row ([co chunk][pixel][8 co], hi and lo), B_tap from the ring of
+// input rows at slot (y + dy) mod 4, pixel 1 + dx (the layout of conv32_tc).
+// M = 128 is the smallest MMA height here: rows 0..31 of D are the 32 output
+// channels, rows 32..127 read other (in-bounds) shared memory and are
+// discarded (a row of D depends only on its own row of A).  The nine
+// 32-column accumulators (288 tensor-memory columns) sum over all rows of the
+// block's strip; the next row's loads overlap the MMAs of the current one.
+namespace ctc {
+constexpr unsigned kDz = 128 * 16 * 4;                      // one split part of a dz row: 4 chunks x 128 pixels
+constexpr unsigned kWgSmem = 4 * kDz + kRing + 128;         // dz hi / lo, two buffers each, then the ring
+constexpr unsigned kIdescW = nsk::tc::idesc_bf16(128, 32, true) | (1u << 16);  // A and B MN-major
+}  // namespace ctc
+
+__global__ void __launch_bounds__(128) conv32_wgrad_tc(const bf16 *__restrict__ a, const float *__restrict__ dz,
+                                                       float *__restrict__ dw, float *__restrict__ db, int H, int W,
+                                                       int rows_per_block, int *err) {
+  using namespace ctc;
+  namespace tc = nsk::tc;
+  extern __shared__ __align__(128) unsigned char csmb[];
+  unsigned char *dzs = csmb, *ring = csmb + 4 * kDz;  // dzs: [buffer][part][chunk][pixel][8]
+  __shared__ __align__(8) unsigned long long bar;
+  __shared__ unsigned tslot;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int strips = W / 128, segs = (H + rows_per_block - 1) / rows_per_block;
+  const int b = blockIdx.x / (strips * segs), rem = blockIdx.x % (strips * segs);
+  const int x0 = (rem / segs) * 128, y0 = (rem % segs) * rows_per_block;
+  const int y1 = min(H, y0 + rows_per_block);
+  const long long img = (long long)H * W;
+  const unsigned sbase = nsk::smem_addr(csmb);
+  if (warp == 0) tc::tmem_alloc(&tslot, 512);
+  if (tid == 0) nsk::mbar_init(&bar, 1);
+  float bacc[32];
+#pragma unroll
+  for (int i = 0; i < 32; ++i) bacc[i] = 0.0f;
+  auto load_a_row = [&](int yy) {
+    const int gy = ((yy % H) + H) % H, slot = yy & 3;
+    for (int i = tid; i < 4 * kQ; i += 128) {
+      const int c = i / kQ, q = i % kQ;
+      const int gx = (x0 - 1 + q + W) % W;
+      const bf16 *src = a + ((long long)b * 32 + 8 * c) * img + (long long)gy * W + gx;
+      unsigned short h[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) h[j] = __bfloat16_as_ushort(src[j * img]);
+      uint4 v;
+      v.x = h[0] | ((unsigned)h[1] << 16);
+      v.y = h[2] | ((unsigned)h[3] << 16);
+      v.z = h[4] | ((unsigned)h[5] << 16);
+      v.w = h[6] | ((unsigned)h[7] << 16);
+      *reinterpret_cast<uint4 *>(ring + slot * kSlot + c * kChunk + q * 16) = v;
+    }
+  };
+  // dz row yy into buffer yy & 1: this thread = pixel x0 + tid, all 32 channels
+  auto load_dz_row = [&](int yy) {
+    unsigned char *base = dzs + (yy & 1) * 2 * kDz;
+    const float *src = dz + (long long)b * 32 * img + (long long)yy * W + x0 + tid;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      float v[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        v[j] = src[(8 * c + j) * img];
+        bacc[8 * c + j] += v[j];
+      }
+      uint4 hi, lo;
+      tc::split2(v[0], v[1], hi.x, lo.x);
+      tc::split2(v[2], v[3], hi.y, lo.y);
+      tc::split2(v[4], v[5], hi.z, lo.z);
+      tc::split2(v[6], v[7], hi.w, lo.w);
+      *reinterpret_cast<uint4 *>(base + c * 2048 + tid * 16) = hi;
+      *reinterpret_cast<uint4 *>(base + kDz + c * 2048 + tid * 16) = lo;
+    }
+  };
+  load_a_row(y0 - 1);
+  load_a_row(y0);
+  load_a_row(y0 + 1);
+  load_dz_row(y0);
+  unsigned ph = 0;
+  bool bad = false;
+  for (int y = y0; y < y1; ++y) {
+    tc::fence_async_smem();
+    tc::fence_before();
+    if (__syncthreads_or(bad)) break;  // rows y - 1 .. y + 1 and dz row y in place; the MMAs of row y - 1 done
+    tc::fence_after();
+    if (tid == 0) {
+      const unsigned abase = sbase + (y & 1) * 2 * kDz;
+#pragma unroll 1
+      for (int tap = 0; tap < 9; ++tap) {
+        const int dy = tap / 3 - 1, dx = tap % 3 - 1;
+        const unsigned bbase = sbase + 4 * kDz + ((y + dy) & 3) * kSlot + (1 + dx) * 16;
+        const unsigned d = tslot + tap * 32;
+#pragma unroll
+        for (int part = 0; part < 2; ++part)
+#pragma unroll
+          for (int kk = 0; kk < 8; ++kk) {
+            const unsigned ad = abase + part * kDz + kk * 256, bd = bbase + kk * 256;
+            tc::mma(d, tc::sdesc(ad, 128, 2048), tc::sdesc(bd, 128, kChunk), kIdescW, (y > y0 || part || kk) ? 1u : 0u);
+          }
+      }
+      tc::commit(&bar);
+    }
+    // the next rows land while the MMAs of row y run (their slots and buffer
+    // were last read by the MMAs of row y - 1, which have completed)
+    if (y + 1 < y1) {
+      load_a_row(y + 2);
+      load_dz_row(y + 1);
+    }
+    bad |= !nsk::mbar_wait_bounded(&bar, ph);
+    ph ^= 1u;
+    tc::fence_after();
+  }
+  if (bad) {
+    if (tid == 0) atomicExch(err, 3);
+    nsk::mbar_wait_bounded(&bar, ph);  // an MMA group in flight may still write the accumulators
+  }
+  // bias: sum over the block's threads (pixels) of the per-channel sums
+#pragma unroll
+  for (int co = 0; co < 32; ++co) {
+    float v = bacc[co];
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    if (lane == 0 && !bad) atomicAdd(db + co, v);
+  }
+  // weights: warp 0's lanes are the 32 output channels
+  if (warp == 0 && !bad) {
+#pragma unroll 1
+    for (int tap = 0; tap < 9; ++tap) {
+      float v[32];
+      tc::tmem_ld<32>(tslot + tap * 32, v);
+      tc::tmem_wait_ld();
+#pragma unroll
+      for (int ci = 0; ci < 32; ++ci) atomicAdd(dw + (lane * 32 + ci) * 9 + tap, v[ci]);
+    }
+  }
+  tc::fence_before();
+  __syncthreads();
+  if (warp == 0) tc::tmem_dealloc(tslot, 512);
+}
+
 // dw[co][ci][k] += sum_b sum_p dz[b][co][p] a[b][ci][p + off(k)];  db[co] += sum dz[b][co][p]
 // One block per (image, 64x64 region), walking its 16 sub-tiles.
 template <int CIN, int COUT, typename TA>
@@ -476,6 +620,12 @@ int launch_c32(const ns_cnn *c, const TIN *x, const bf16 *w, const float *bias, 
   return (int)cudaGetLastError();
 }
 
+// weight gradient of a 32 -> 32 layer: the tensor cores when the width is a
+// multiple of 128, about one block per SM (each holds all of the SM's tensor
+// memory), else conv_bwd_weight
+int launch_w32(const ns_cnn *c, const bf16 *a, const float *dz, float *dw, float *db, int B, int H, int W,
+               cudaStream_t s);
+
 template <int CIN, int COUT, typename TA>
 int launch_bww(const TA *a, const float *dz, float *dw, float *db, int B, int H, int W, cudaStream_t s) {
   conv_bwd_weight<CIN, COUT, TA><<<dim3(W / 64, H / 64, B), 256, bww_smem(CIN, COUT), s>>>(a, dz, dw, db, H, W);
@@ -493,6 +643,17 @@ void bww_attr() {
                        (int)bww_smem(CIN, COUT));
 }
 
+int launch_w32(const ns_cnn *c, const bf16 *a, const float *dz, float *dw, float *db, int B, int H, int W,
+               cudaStream_t s) {
+  if (W % 128 != 0) return launch_bww<32, 32, bf16>(a, dz, dw, db, B, H, W, s);
+  const int strips = W / 128;
+  const int segs = std::max(1, std::min(H, c->nsm / (B * strips)));  // at most one wave
+  const int rows = (H + segs - 1) / segs;
+  const int blocks = B * strips * ((H + rows - 1) / rows);
+  conv32_wgrad_tc<<<blocks, 128, ctc::kWgSmem, s>>>(a, dz, dw, db, H, W, rows, c->errw);
+  return (int)cudaGetLastError();
+}
+
 // every kernel instance that forward() and backward() launch
 void set_attributes() {
   fwd_attr<1, 32, EPI_GELU, float, bf16>();
@@ -507,6 +668,7 @@ void set_attributes() {
                        (int)ctc::smem_bytes(false));
   cudaFuncSetAttribute(conv32_tc<EPI_GELU_BWD, float, float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)ctc::smem_bytes(true));
+  cudaFuncSetAttribute(conv32_wgrad_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ctc::kWgSmem);
 }
 
 // forward pass through all layers; keeps z_l, a_l for the backward pass
@@ -543,11 +705,11 @@ int backward(ns_cnn *c, const float *x, const float *t, int B, cudaStream_t s) {
   if ((rc = launch_fwd<1, 32, EPI_GELU_BWD, float, float>(c->dy, c->wt[3], nullptr, c->z[2], nullptr, c->dza, B, H, W,
                                                           s)))
     return rc;  // dz2
-  if ((rc = launch_bww<32, 32, bf16>(c->a[1], c->dza, g + c->woff[2], g + c->boff[2], B, H, W, s))) return rc;
+  if ((rc = launch_w32(c, c->a[1], c->dza, g + c->woff[2], g + c->boff[2], B, H, W, s))) return rc;
   if ((rc = launch_c32<EPI_GELU_BWD, float, float>(c, c->dza, c->wt[2], nullptr, c->z[1], nullptr, c->dzb, B, H, W,
                                                     s)))
     return rc;  // dz1
-  if ((rc = launch_bww<32, 32, bf16>(c->a[0], c->dzb, g + c->woff[1], g + c->boff[1], B, H, W, s))) return rc;
+  if ((rc = launch_w32(c, c->a[0], c->dzb, g + c->woff[1], g + c->boff[1], B, H, W, s))) return rc;
   if ((rc = launch_c32<EPI_GELU_BWD, float, float>(c, c->dzb, c->wt[1], nullptr, c->z[0], nullptr, c->dza, B, H, W,
                                                     s)))
     return rc;  // dz0

@@ -252,6 +252,46 @@ def test_closure_gains_over_the_plain_coarse_solve(ns):
         tr.net.close()
 
 
+@pytest.mark.parametrize("mode", ["fine", "coarse"])
+def test_closure_fallback_hands_over_to_the_plain_solve(ns, mode):
+    """A closed run that blows up (here: a network whose output is scaled by
+    1e8) restores its last good state and continues without the network: by
+    default as the plain fine-grid solve restarted from that state prolonged
+    to the fine grid, its coarse view the fine state filtered back; with
+    fallback="coarse" as the plain coarse solve.  Either way it must equal,
+    bit for bit, the plain solve started from the same state."""
+    from paper_1807_01769_gb300 import closure as C
+
+    cfg = C.KolmogorovConfig(n_fine=256, n_coarse=128, dt_coarse=4e-3)
+    w0 = inputs.random_vorticity_2d(128, seed=9, k0=8.0, energy=0.5)
+    net = ns.CNN(128, 128, 1, seed=3)
+    tr = C.Trained(net, x_scale=6.0, t_scale=1e8)
+    try:
+        cs = C.ClosureSolver(cfg, tr, check_every=5, fallback=mode)
+        try:
+            cs.set_state_spectral(w0)
+            cs.step(20)  # the check after 5 steps fails: the last good state is w0
+            assert cs.fell_back and cs.on_fine == (mode == "fine")
+            got = cs.get_state_spectral()
+            e, om = cs.diagnostics()
+            assert np.all(np.isfinite(got)) and np.isfinite(e) and np.isfinite(om)
+        finally:
+            cs.close()
+        if mode == "fine":
+            with C.fine_solver(cfg) as f:
+                f.set_state_spectral(C.prolong_2d(w0, 128, 256))
+                f.step(15 * cfg.ratio)
+                ref = C.restrict_2d(f.get_state_spectral(), 256, 128)
+        else:
+            with C.coarse_solver(cfg) as c:
+                c.set_state_spectral(w0)
+                c.step(15)
+                ref = c.get_state_spectral()
+        assert np.array_equal(got, ref)
+    finally:
+        net.close()
+
+
 def test_closure_graph_replay_equals_eager_steps(ns):
     """One corrected step captured into a CUDA graph and replayed gives the
     same state, bit for bit, as the same steps launched one by one."""
