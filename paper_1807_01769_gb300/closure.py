@@ -36,6 +36,7 @@ from __future__ import annotations
 import argparse
 import json
 import math
+import os
 import time
 from dataclasses import asdict, dataclass, field
 
@@ -156,11 +157,13 @@ class Trained:
 
 
 def train(X: np.ndarray, T: np.ndarray, steps: int = 3000, batch: int = 16, lr: float = 1e-3, seed: int = 0,
-          log=None) -> Trained:
+          log=None, noise: float = 0.0) -> Trained:
     """Adam on the mean squared error of normalised targets; the normalised
     snapshots are uploaded once and each minibatch is gathered on the device,
     on the stream the CNN runs on, from a per-epoch host permutation; cosine
-    learning-rate decay."""
+    learning-rate decay.  ``noise`` > 0 adds Gaussian noise of that standard
+    deviation to the normalised inputs of every minibatch (the network then
+    also sees states perturbed the way its own errors perturb a closed run)."""
     import torch
 
     n, h, w = X.shape
@@ -174,6 +177,8 @@ def train(X: np.ndarray, T: np.ndarray, steps: int = 3000, batch: int = 16, lr: 
     xb = torch.empty((batch, h, w), dtype=torch.float32, device="cuda")
     tb = torch.empty_like(xb)
     perm = None
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(seed)
     for k in range(steps):
         e = k % per_epoch
         if e == 0:
@@ -181,6 +186,8 @@ def train(X: np.ndarray, T: np.ndarray, steps: int = 3000, batch: int = 16, lr: 
         idx = torch.from_numpy(perm[e * batch:(e + 1) * batch]).cuda()
         torch.index_select(xs, 0, idx, out=xb)
         torch.index_select(ts, 0, idx, out=tb)
+        if noise > 0:
+            xb.add_(torch.randn(xb.shape, generator=gen, device="cuda"), alpha=noise)
         lr_k = lr * 0.5 * (1.0 + math.cos(math.pi * k / steps))
         want = (k % 50 == 0) or k == steps - 1
         loss = net.train_step(xb.data_ptr(), tb.data_ptr(), batch, lr_k, want_loss=want,
@@ -466,9 +473,12 @@ def main(argv=None):
     ap.add_argument("--train-steps", type=int, default=3000)
     ap.add_argument("--batch", type=int, default=16)
     ap.add_argument("--lr", type=float, default=1e-3)
+    ap.add_argument("--noise", type=float, default=0.0, help="input noise (std, normalised units) in training")
     ap.add_argument("--t-eval", type=float, default=2.0)
     ap.add_argument("--every", type=float, default=0.25)
     ap.add_argument("--out", default=None)
+    ap.add_argument("--data", default=None, help="npz file: the generated snapshots are loaded from it if it "
+                    "exists, else saved to it (several trainings on one data set)")
     a = ap.parse_args(argv)
     cfg = KolmogorovConfig(n_fine=a.n_fine, n_coarse=a.n_coarse, snaps_per_seed=a.snaps,
                            train_seeds=tuple(range(a.seeds)))
@@ -477,11 +487,17 @@ def main(argv=None):
         print(m, flush=True)
 
     t0 = time.perf_counter()
-    X, T, energy = generate(cfg, cfg.train_seeds, log)
+    if a.data and os.path.exists(a.data):
+        d = np.load(a.data)
+        X, T, energy = d["X"], d["T"], [tuple(e) for e in d["energy"]]
+    else:
+        X, T, energy = generate(cfg, cfg.train_seeds, log)
+        if a.data:
+            np.savez(a.data, X=X, T=T, energy=np.array(energy))
     t_gen = time.perf_counter() - t0
     log(f"generated {X.shape[0]} snapshots in {t_gen:.1f} s; std(omega_c) {X.std():.3f} std(tau) {T.std():.4f}")
     t0 = time.perf_counter()
-    tr = train(X, T, steps=a.train_steps, batch=a.batch, lr=a.lr, log=log)
+    tr = train(X, T, steps=a.train_steps, batch=a.batch, lr=a.lr, log=log, noise=a.noise)
     t_train = time.perf_counter() - t0
     Xe, Te, _ = generate(KolmogorovConfig(**{**asdict(cfg), "snaps_per_seed": 20}), (cfg.eval_seed,))
     prior = a_priori(tr, Xe, Te)
@@ -489,7 +505,8 @@ def main(argv=None):
     post = a_posteriori(cfg, tr, cfg.eval_seed, a.t_eval, a.every, log)
     times = step_times(cfg, tr)
     result = {"config": {k: (list(v) if isinstance(v, tuple) else v) for k, v in asdict(cfg).items()},
-              "train": {"steps": a.train_steps, "batch": a.batch, "lr": a.lr, "snapshots": int(X.shape[0]),
+              "train": {"steps": a.train_steps, "batch": a.batch, "lr": a.lr, "noise": a.noise,
+                        "snapshots": int(X.shape[0]),
                         "gen_s": t_gen, "train_s": t_train, "loss_first": tr.losses[0][1],
                         "loss_last": tr.losses[-1][1]},
               "fine_energy_enstrophy_last": energy, "a_priori": prior, "a_posteriori": post["rows"],
