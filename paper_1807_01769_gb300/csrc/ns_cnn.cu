@@ -377,19 +377,20 @@ __global__ void __launch_bounds__(128) conv32_wgrad_tc(const bf16 *__restrict__ 
     if (__syncthreads_or(bad)) break;  // rows y - 1 .. y + 1 and dz row y in place; the MMAs of row y - 1 done
     tc::fence_after();
     if (tid == 0) {
+      // consecutive MMAs go to different accumulators (tap innermost), so
+      // that no MMA waits for the one before it
       const unsigned abase = sbase + (y & 1) * 2 * kDz;
 #pragma unroll 1
-      for (int tap = 0; tap < 9; ++tap) {
-        const int dy = tap / 3 - 1, dx = tap % 3 - 1;
-        const unsigned bbase = sbase + 4 * kDz + ((y + dy) & 3) * kSlot + (1 + dx) * 16;
-        const unsigned d = tslot + tap * 32;
+      for (int step = 0; step < 16; ++step) {
+        const int part = step >> 3, kk = step & 7;
+        const unsigned ad = abase + part * kDz + kk * 256;
+        const unsigned long long adesc = tc::sdesc(ad, 128, 2048);
 #pragma unroll
-        for (int part = 0; part < 2; ++part)
-#pragma unroll
-          for (int kk = 0; kk < 8; ++kk) {
-            const unsigned ad = abase + part * kDz + kk * 256, bd = bbase + kk * 256;
-            tc::mma(d, tc::sdesc(ad, 128, 2048), tc::sdesc(bd, 128, kChunk), kIdescW, (y > y0 || part || kk) ? 1u : 0u);
-          }
+        for (int tap = 0; tap < 9; ++tap) {
+          const int dy = tap / 3 - 1, dx = tap % 3 - 1;
+          const unsigned bd = sbase + 4 * kDz + ((y + dy) & 3) * kSlot + (1 + dx) * 16 + kk * 256;
+          tc::mma(tslot + tap * 32, adesc, tc::sdesc(bd, 128, kChunk), kIdescW, (y > y0 || step) ? 1u : 0u);
+        }
       }
       tc::commit(&bar);
     }
