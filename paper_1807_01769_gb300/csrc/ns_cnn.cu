@@ -153,11 +153,63 @@ __device__ __forceinline__ unsigned woff(int tap, int co, int ci) {
 }
 }  // namespace ctc
 
+constexpr int kConvThreads = 256;  // two threads per tensor-memory lane (pixel)
+
+// One ring row (channels 0..31 at pixels x0 - 1 .. x0 + 128 of row yy, both
+// ends wrapped) gathered in two phases, so that the global loads of a row are
+// in flight while the block works on earlier rows: issue() loads this
+// thread's items (chunk c, pixel q) into registers, store() writes them to the
+// ring slot as 16-byte [chunk][pixel][8 channels] units (hi and lo for an
+// FP32 input).
+template <typename TIN>
+struct RowGather {
+  static constexpr int kItems = (4 * ctc::kQ + kConvThreads - 1) / kConvThreads;
+  float v[kItems][8];
+  int yy = 0;
+  __device__ __forceinline__ void issue(const TIN *__restrict__ x, int b, int x0, int row, int H, int W) {
+    yy = row;
+    const int gy = ((row % H) + H) % H;
+    const long long img = (long long)H * W;
+#pragma unroll
+    for (int it = 0; it < kItems; ++it) {
+      const int i = threadIdx.x + kConvThreads * it;
+      if (i < 4 * ctc::kQ) {
+        const int c = i / ctc::kQ, q = i % ctc::kQ;
+        int gx = x0 - 1 + q;
+        gx = gx < 0 ? gx + W : (gx >= W ? gx - W : gx);
+        const TIN *src = x + ((long long)b * 32 + 8 * c) * img + (long long)gy * W + gx;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) v[it][j] = ldf(src + j * img);
+      }
+    }
+  }
+  __device__ __forceinline__ void store(unsigned char *ring) const {
+    namespace tc = nsk::tc;
+    const int slot = yy & 3;
+#pragma unroll
+    for (int it = 0; it < kItems; ++it) {
+      const int i = threadIdx.x + kConvThreads * it;
+      if (i < 4 * ctc::kQ) {
+        const int c = i / ctc::kQ, q = i % ctc::kQ;
+        const unsigned o = slot * ctc::kSlot + c * ctc::kChunk + q * 16;
+        uint4 hi, lo;
+        tc::split2(v[it][0], v[it][1], hi.x, lo.x);
+        tc::split2(v[it][2], v[it][3], hi.y, lo.y);
+        tc::split2(v[it][4], v[it][5], hi.z, lo.z);
+        tc::split2(v[it][6], v[it][7], hi.w, lo.w);
+        *reinterpret_cast<uint4 *>(ring + o) = hi;  // exact for BF16 inputs (lo = 0)
+        if constexpr (sizeof(TIN) == 4) *reinterpret_cast<uint4 *>(ring + ctc::kRing + o) = lo;
+      }
+    }
+  }
+};
+
 template <int EPI, typename TIN, typename TOUT>
-__global__ void __launch_bounds__(128) conv32_tc(const TIN *__restrict__ x, const bf16 *__restrict__ w,
-                                                 const float *__restrict__ bias, const bf16 *__restrict__ zin,
-                                                 bf16 *__restrict__ zout, TOUT *__restrict__ out, int H, int W,
-                                                 int rows_per_block, int *err) {
+__global__ void __launch_bounds__(kConvThreads) conv32_tc(const TIN *__restrict__ x, const bf16 *__restrict__ w,
+                                                          const float *__restrict__ bias,
+                                                          const bf16 *__restrict__ zin, bf16 *__restrict__ zout,
+                                                          TOUT *__restrict__ out, int H, int W, int rows_per_block,
+                                                          int *err) {
   using namespace ctc;
   namespace tc = nsk::tc;
   constexpr bool SPLIT = sizeof(TIN) == 4;
@@ -172,7 +224,7 @@ __global__ void __launch_bounds__(128) conv32_tc(const TIN *__restrict__ x, cons
   const int y1 = min(H, y0 + rows_per_block);
   const long long img = (long long)H * W;
   const unsigned sbase = nsk::smem_addr(csmb);
-  for (int i = tid; i < 9 * 32 * 32; i += 128) {
+  for (int i = tid; i < 9 * 32 * 32; i += kConvThreads) {
     const int co = i / 288, r = i % 288, ci = r / 9, tap = r % 9;  // w[co][ci][tap]
     *reinterpret_cast<bf16 *>(wb + woff(tap, co, ci)) = w[i];
   }
@@ -181,68 +233,43 @@ __global__ void __launch_bounds__(128) conv32_tc(const TIN *__restrict__ x, cons
     nsk::mbar_init(&bars[0], 1);
     nsk::mbar_init(&bars[1], 1);
   }
-  // input row yy (wrapped) into ring slot yy mod 4: thread item (chunk c,
-  // pixel q) gathers 8 channels (one coalesced load per channel across the
-  // warp) into one 16-byte store (two for a split input)
-  auto load_row = [&](int yy) {
-    const int gy = ((yy % H) + H) % H, slot = yy & 3;
-    for (int i = tid; i < 4 * kQ; i += 128) {
-      const int c = i / kQ, q = i % kQ;
-      const int gx = (x0 - 1 + q + W) % W;
-      const TIN *src = x + ((long long)b * 32 + 8 * c) * img + (long long)gy * W + gx;
-      float v[8];
-#pragma unroll
-      for (int j = 0; j < 8; ++j) v[j] = ldf(src + j * img);
-      const unsigned o = slot * kSlot + c * kChunk + q * 16;
-      if constexpr (SPLIT) {
-        uint4 hi, lo;
-        tc::split2(v[0], v[1], hi.x, lo.x);
-        tc::split2(v[2], v[3], hi.y, lo.y);
-        tc::split2(v[4], v[5], hi.z, lo.z);
-        tc::split2(v[6], v[7], hi.w, lo.w);
-        *reinterpret_cast<uint4 *>(ring + o) = hi;
-        *reinterpret_cast<uint4 *>(ring + kRing + o) = lo;
-      } else {
-        uint4 hv;
-        const __nv_bfloat162 p0 = __floats2bfloat162_rn(v[0], v[1]), p1 = __floats2bfloat162_rn(v[2], v[3]),
-                             p2 = __floats2bfloat162_rn(v[4], v[5]), p3 = __floats2bfloat162_rn(v[6], v[7]);
-        hv.x = *reinterpret_cast<const unsigned *>(&p0);
-        hv.y = *reinterpret_cast<const unsigned *>(&p1);
-        hv.z = *reinterpret_cast<const unsigned *>(&p2);
-        hv.w = *reinterpret_cast<const unsigned *>(&p3);
-        *reinterpret_cast<uint4 *>(ring + o) = hv;
-      }
-    }
-  };
-  // epilogue of output row yy from accumulator buf: this thread = pixel x0 + tid
+  // epilogue of output row yy from accumulator buf: this thread = pixel
+  // x0 + tid % 128 (tensor-memory lane), output channels 16 (tid / 128) + 0..15
   auto epilogue = [&](int yy, int buf) {
-    float acc[32];
-    tc::tmem_ld<32>(tslot + ((unsigned)(warp * 32) << 16) + buf * 32, acc);
+    const int px = tid & 127, c0 = (tid >> 7) * 16;
+    float acc[16];
+    tc::tmem_ld<16>(tslot + ((unsigned)((warp & 3) * 32) << 16) + buf * 32 + c0, acc);
     tc::tmem_wait_ld();
-    const long long p = (long long)yy * W + x0 + tid;
+    const long long p = (long long)yy * W + x0 + px;
 #pragma unroll
-    for (int co = 0; co < 32; ++co) {
+    for (int j = 0; j < 16; ++j) {
+      const int co = c0 + j;
       const long long o = ((long long)b * 32 + co) * img + p;
       if (EPI == EPI_GELU) {
-        const float v = acc[co] + (bias ? bias[co] : 0.0f);
+        const float v = acc[j] + (bias ? bias[co] : 0.0f);
         zout[o] = __float2bfloat16(v);
         out[o] = (TOUT)__float2bfloat16(gelu_f(v));
       } else if (EPI == EPI_GELU_BWD) {
-        out[o] = (TOUT)(acc[co] * gelu_d(__bfloat162float(zin[o])));
+        out[o] = (TOUT)(acc[j] * gelu_d(__bfloat162float(zin[o])));
       } else {
-        out[o] = (TOUT)(acc[co] + (bias ? bias[co] : 0.0f));
+        out[o] = (TOUT)(acc[j] + (bias ? bias[co] : 0.0f));
       }
     }
   };
-  load_row(y0 - 1);
-  load_row(y0);
+  RowGather<TIN> g;
+  g.issue(x, b, x0, y0 - 1, H, W);
+  g.store(ring);
+  g.issue(x, b, x0, y0, H, W);
+  g.store(ring);
+  g.issue(x, b, x0, y0 + 1, H, W);
   unsigned ph[2] = {0u, 0u};
   bool bad = false;
   for (int y = y0; y < y1; ++y) {
-    load_row(y + 1);  // its slot was last read by the MMAs of row y - 2, already waited for
+    g.store(ring);  // row y + 1; its slot was last read by the MMAs of row y - 3, long completed
+    if (y + 2 <= y1) g.issue(x, b, x0, y + 2, H, W);  // in flight during this row's MMAs and epilogue
     tc::fence_async_smem();
     tc::fence_before();
-    if (__syncthreads_or(bad)) break;  // ring row visible; epilogue reads of this accumulator done
+    if (__syncthreads_or(bad)) break;  // ring rows visible; epilogue reads of this accumulator done
     tc::fence_after();
     const int buf = y & 1;
     if (tid == 0) {
@@ -306,9 +333,10 @@ constexpr unsigned kWgSmem = 4 * kDz + kRing + 128;         // dz hi / lo, two b
 constexpr unsigned kIdescW = nsk::tc::idesc_bf16(128, 32, true) | (1u << 16);  // A and B MN-major
 }  // namespace ctc
 
-__global__ void __launch_bounds__(128) conv32_wgrad_tc(const bf16 *__restrict__ a, const float *__restrict__ dz,
-                                                       float *__restrict__ dw, float *__restrict__ db, int H, int W,
-                                                       int rows_per_block, int *err) {
+__global__ void __launch_bounds__(kConvThreads) conv32_wgrad_tc(const bf16 *__restrict__ a,
+                                                                const float *__restrict__ dz, float *__restrict__ dw,
+                                                                float *__restrict__ db, int H, int W,
+                                                                int rows_per_block, int *err) {
   using namespace ctc;
   namespace tc = nsk::tc;
   extern __shared__ __align__(128) unsigned char csmb[];
@@ -316,6 +344,7 @@ __global__ void __launch_bounds__(128) conv32_wgrad_tc(const bf16 *__restrict__ 
   __shared__ __align__(8) unsigned long long bar;
   __shared__ unsigned tslot;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int px = tid & 127, c0 = (tid >> 7) * 16;  // this thread's pixel and dz channels c0 .. c0 + 15
   const int strips = W / 128, segs = (H + rows_per_block - 1) / rows_per_block;
   const int b = blockIdx.x / (strips * segs), rem = blockIdx.x % (strips * segs);
   const int x0 = (rem / segs) * 128, y0 = (rem % segs) * rows_per_block;
@@ -324,51 +353,48 @@ __global__ void __launch_bounds__(128) conv32_wgrad_tc(const bf16 *__restrict__ 
   const unsigned sbase = nsk::smem_addr(csmb);
   if (warp == 0) tc::tmem_alloc(&tslot, 512);
   if (tid == 0) nsk::mbar_init(&bar, 1);
-  float bacc[32];
+  float bacc[16];
 #pragma unroll
-  for (int i = 0; i < 32; ++i) bacc[i] = 0.0f;
-  auto load_a_row = [&](int yy) {
-    const int gy = ((yy % H) + H) % H, slot = yy & 3;
-    for (int i = tid; i < 4 * kQ; i += 128) {
-      const int c = i / kQ, q = i % kQ;
-      const int gx = (x0 - 1 + q + W) % W;
-      const bf16 *src = a + ((long long)b * 32 + 8 * c) * img + (long long)gy * W + gx;
-      unsigned short h[8];
+  for (int i = 0; i < 16; ++i) bacc[i] = 0.0f;
+  // dz row yy: issued into registers, stored (split) into buffer yy & 1
+  float dv[16];
+  int dyy = 0;
+  auto issue_dz = [&](int yy) {
+    dyy = yy;
+    const float *src = dz + ((long long)b * 32 + c0) * img + (long long)yy * W + x0 + px;
 #pragma unroll
-      for (int j = 0; j < 8; ++j) h[j] = __bfloat16_as_ushort(src[j * img]);
-      uint4 v;
-      v.x = h[0] | ((unsigned)h[1] << 16);
-      v.y = h[2] | ((unsigned)h[3] << 16);
-      v.z = h[4] | ((unsigned)h[5] << 16);
-      v.w = h[6] | ((unsigned)h[7] << 16);
-      *reinterpret_cast<uint4 *>(ring + slot * kSlot + c * kChunk + q * 16) = v;
-    }
+    for (int j = 0; j < 16; ++j) dv[j] = src[j * img];
   };
-  // dz row yy into buffer yy & 1: this thread = pixel x0 + tid, all 32 channels
-  auto load_dz_row = [&](int yy) {
-    unsigned char *base = dzs + (yy & 1) * 2 * kDz;
-    const float *src = dz + (long long)b * 32 * img + (long long)yy * W + x0 + tid;
+  auto store_dz = [&]() {
+    unsigned char *base = dzs + (dyy & 1) * 2 * kDz;
 #pragma unroll
-    for (int c = 0; c < 4; ++c) {
-      float v[8];
+    for (int j = 0; j < 16; ++j) bacc[j] += dv[j];
 #pragma unroll
-      for (int j = 0; j < 8; ++j) {
-        v[j] = src[(8 * c + j) * img];
-        bacc[8 * c + j] += v[j];
-      }
+    for (int h = 0; h < 2; ++h) {
+      const float *v = dv + 8 * h;
       uint4 hi, lo;
       tc::split2(v[0], v[1], hi.x, lo.x);
       tc::split2(v[2], v[3], hi.y, lo.y);
       tc::split2(v[4], v[5], hi.z, lo.z);
       tc::split2(v[6], v[7], hi.w, lo.w);
-      *reinterpret_cast<uint4 *>(base + c * 2048 + tid * 16) = hi;
-      *reinterpret_cast<uint4 *>(base + kDz + c * 2048 + tid * 16) = lo;
+      const int c = (c0 >> 3) + h;
+      *reinterpret_cast<uint4 *>(base + c * 2048 + px * 16) = hi;
+      *reinterpret_cast<uint4 *>(base + kDz + c * 2048 + px * 16) = lo;
     }
   };
-  load_a_row(y0 - 1);
-  load_a_row(y0);
-  load_a_row(y0 + 1);
-  load_dz_row(y0);
+  RowGather<bf16> g;
+  g.issue(a, b, x0, y0 - 1, H, W);
+  g.store(ring);
+  g.issue(a, b, x0, y0, H, W);
+  g.store(ring);
+  g.issue(a, b, x0, y0 + 1, H, W);
+  g.store(ring);
+  issue_dz(y0);
+  store_dz();
+  if (y0 + 1 < y1) {
+    g.issue(a, b, x0, y0 + 2, H, W);
+    issue_dz(y0 + 1);
+  }
   unsigned ph = 0;
   bool bad = false;
   for (int y = y0; y < y1; ++y) {
@@ -383,8 +409,7 @@ __global__ void __launch_bounds__(128) conv32_wgrad_tc(const bf16 *__restrict__ 
 #pragma unroll 1
       for (int step = 0; step < 16; ++step) {
         const int part = step >> 3, kk = step & 7;
-        const unsigned ad = abase + part * kDz + kk * 256;
-        const unsigned long long adesc = tc::sdesc(ad, 128, 2048);
+        const unsigned long long adesc = tc::sdesc(abase + part * kDz + kk * 256, 128, 2048);
 #pragma unroll
         for (int tap = 0; tap < 9; ++tap) {
           const int dy = tap / 3 - 1, dx = tap % 3 - 1;
@@ -394,11 +419,16 @@ __global__ void __launch_bounds__(128) conv32_wgrad_tc(const bf16 *__restrict__ 
       }
       tc::commit(&bar);
     }
-    // the next rows land while the MMAs of row y run (their slots and buffer
-    // were last read by the MMAs of row y - 1, which have completed)
+    // the next rows go into the slot / buffer the MMAs of row y - 1 read
+    // (completed), while the MMAs of row y run; the loads after them are in
+    // flight until the next iteration
     if (y + 1 < y1) {
-      load_a_row(y + 2);
-      load_dz_row(y + 1);
+      g.store(ring);  // row y + 2
+      store_dz();     // dz row y + 1
+      if (y + 2 < y1) {
+        g.issue(a, b, x0, y + 3, H, W);
+        issue_dz(y + 2);
+      }
     }
     bad |= !nsk::mbar_wait_bounded(&bar, ph);
     ph ^= 1u;
@@ -408,12 +438,12 @@ __global__ void __launch_bounds__(128) conv32_wgrad_tc(const bf16 *__restrict__ 
     if (tid == 0) atomicExch(err, 3);
     nsk::mbar_wait_bounded(&bar, ph);  // an MMA group in flight may still write the accumulators
   }
-  // bias: sum over the block's threads (pixels) of the per-channel sums
+  // bias: sum over the block's pixels of the per-channel sums
 #pragma unroll
-  for (int co = 0; co < 32; ++co) {
-    float v = bacc[co];
+  for (int j = 0; j < 16; ++j) {
+    float v = bacc[j];
     for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-    if (lane == 0 && !bad) atomicAdd(db + co, v);
+    if (lane == 0 && !bad) atomicAdd(db + c0 + j, v);
   }
   // weights: warp 0's lanes are the 32 output channels
   if (warp == 0 && !bad) {
@@ -616,7 +646,7 @@ int launch_c32(const ns_cnn *c, const TIN *x, const bf16 *w, const float *bias, 
   const int segs = std::max(1, std::min(H, (2 * c->nsm + B * strips - 1) / (B * strips)));
   const int rows = (H + segs - 1) / segs;
   const int blocks = B * strips * ((H + rows - 1) / rows);
-  conv32_tc<EPI, TIN, TOUT><<<blocks, 128, ctc::smem_bytes(sizeof(TIN) == 4), s>>>(x, w, bias, zin, zout, out, H, W,
+  conv32_tc<EPI, TIN, TOUT><<<blocks, kConvThreads, ctc::smem_bytes(sizeof(TIN) == 4), s>>>(x, w, bias, zin, zout, out, H, W,
                                                                                    rows, c->errw);
   return (int)cudaGetLastError();
 }
@@ -651,7 +681,7 @@ int launch_w32(const ns_cnn *c, const bf16 *a, const float *dz, float *dw, float
   const int segs = std::max(1, std::min(H, c->nsm / (B * strips)));  // at most one wave
   const int rows = (H + segs - 1) / segs;
   const int blocks = B * strips * ((H + rows - 1) / rows);
-  conv32_wgrad_tc<<<blocks, 128, ctc::kWgSmem, s>>>(a, dz, dw, db, H, W, rows, c->errw);
+  conv32_wgrad_tc<<<blocks, kConvThreads, ctc::kWgSmem, s>>>(a, dz, dw, db, H, W, rows, c->errw);
   return (int)cudaGetLastError();
 }
 
