@@ -521,6 +521,48 @@ __global__ void __launch_bounds__(256) conv_bwd_weight(const TA *__restrict__ a,
   }
 }
 
+// Weight gradient of the layers with one input or one output channel (32
+// channel pairs): one thread per (pair, tap), 288 threads, each summing the
+// 1024 pixels of a 32x32 region (four 16x16 sub-tiles staged in shared
+// memory); one atomic add per (pair, tap) and block, the bias from the tap-0
+// threads of input channel 0.
+template <int CIN, int COUT, typename TA>
+__global__ void __launch_bounds__(CIN * COUT * 9) conv_bwd_weight_small(const TA *__restrict__ a,
+                                                                       const float *__restrict__ dz,
+                                                                       float *__restrict__ dw,
+                                                                       float *__restrict__ db, int H, int W) {
+  static_assert(CIN * COUT == 32, "32 channel pairs");
+  __shared__ float sdz[COUT][TILE * TILE];
+  __shared__ float sa[CIN][18 * 18];
+  const int b = blockIdx.z;
+  const long long img = (long long)H * W;
+  const int u = threadIdx.x, pr = u / 9, tap = u % 9, co = pr / CIN, ci = pr % CIN;
+  const int ky = tap / 3, kx = tap % 3;
+  float acc = 0.0f, accb = 0.0f;
+  for (int sub = 0; sub < 4; ++sub) {
+    const int y0 = blockIdx.y * 32 + (sub / 2) * TILE, x0 = blockIdx.x * 32 + (sub % 2) * TILE;
+    __syncthreads();
+    for (int i = threadIdx.x; i < COUT * TILE * TILE; i += blockDim.x) {
+      const int c = i / (TILE * TILE), r = i % (TILE * TILE);
+      sdz[c][r] = dz[((long long)b * COUT + c) * img + (long long)(y0 + r / TILE) * W + x0 + r % TILE];
+    }
+    for (int i = threadIdx.x; i < CIN * 324; i += blockDim.x) {
+      const int c = i / 324, r = i % 324, yy = r / 18, xx = r % 18;
+      const int gy = (y0 + yy - 1 + H) % H, gx = (x0 + xx - 1 + W) % W;
+      sa[c][r] = ldf(a + ((long long)b * CIN + c) * img + (long long)gy * W + gx);
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int p = 0; p < TILE * TILE; ++p) {
+      const float g = sdz[co][p];
+      acc = fmaf(g, sa[ci][(p / TILE + ky) * 18 + p % TILE + kx], acc);
+      accb += g;
+    }
+  }
+  atomicAdd(dw + pr * 9 + tap, acc);
+  if (ci == 0 && tap == 0) atomicAdd(db + co, accb);
+}
+
 // flipped, transposed weights for the data gradient: wt[ci][co][8-k] = w[co][ci][k]
 __global__ void flip_weights(const bf16 *__restrict__ w, bf16 *__restrict__ wt, int cin, int cout) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -692,9 +734,7 @@ void set_attributes() {
   fwd_attr<32, 1, EPI_LINEAR, bf16, float>();
   fwd_attr<1, 32, EPI_GELU_BWD, float, float>();
   fwd_attr<32, 32, EPI_GELU_BWD, float, float>();
-  bww_attr<32, 1, bf16>();
   bww_attr<32, 32, bf16>();
-  bww_attr<1, 32, float>();
   cudaFuncSetAttribute(conv32_tc<EPI_GELU, bf16, bf16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)ctc::smem_bytes(false));
   cudaFuncSetAttribute(conv32_tc<EPI_GELU_BWD, float, float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -732,7 +772,9 @@ int backward(ns_cnn *c, const float *x, const float *t, int B, cudaStream_t s) {
     flip_weights<<<(c->cin[l] * c->cout[l] * 9 + 255) / 256, 256, 0, s>>>(c->wb[l], c->wt[l], c->cin[l], c->cout[l]);
   float *g = c->g;
   // layer 3: dz3 = dy
-  if ((rc = launch_bww<32, 1, bf16>(c->a[2], c->dy, g + c->woff[3], g + c->boff[3], B, H, W, s))) return rc;
+  conv_bwd_weight_small<32, 1, bf16><<<dim3(W / 32, H / 32, B), 288, 0, s>>>(c->a[2], c->dy, g + c->woff[3],
+                                                                             g + c->boff[3], H, W);
+  if ((rc = (int)cudaGetLastError())) return rc;
   if ((rc = launch_fwd<1, 32, EPI_GELU_BWD, float, float>(c->dy, c->wt[3], nullptr, c->z[2], nullptr, c->dza, B, H, W,
                                                           s)))
     return rc;  // dz2
@@ -744,7 +786,9 @@ int backward(ns_cnn *c, const float *x, const float *t, int B, cudaStream_t s) {
   if ((rc = launch_c32<EPI_GELU_BWD, float, float>(c, c->dzb, c->wt[1], nullptr, c->z[0], nullptr, c->dza, B, H, W,
                                                     s)))
     return rc;  // dz0
-  return launch_bww<1, 32, float>(x, c->dza, g + c->woff[0], g + c->boff[0], B, H, W, s);
+  conv_bwd_weight_small<1, 32, float><<<dim3(W / 32, H / 32, B), 288, 0, s>>>(x, c->dza, g + c->woff[0],
+                                                                              g + c->boff[0], H, W);
+  return (int)cudaGetLastError();
 }
 
 // the device error word (a tensor-core convolution whose bounded wait expired
