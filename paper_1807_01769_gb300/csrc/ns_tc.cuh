@@ -3,8 +3,8 @@
 // NS_FP32; only the x-line transforms and the product run here.
 //
 // Fields are paired into complex lines, z = x_a + i x_b: the six inverse
-// fields as (u_x, u_y), (u_z, w_x), (w_y, w_z), with u_z scaled per tile by a
-// power of two to the size of w_x; the forward fields as (n_x, n_y) of one
+// fields as (u_x, u_y), (u_z, w_x), (w_y, w_z), with u_z scaled per line by
+// a power of two to the size of w_x; the forward fields as (n_x, n_y) of one
 // line and n_z of two neighbouring lines.  Every transform
 // is then one complex DFT of length N = R1 R2, written as two GEMMs.  With
 // n = R2 a + b, k = c + R1 d and w = exp(2 pi i / N):
@@ -336,7 +336,7 @@ __global__ void __launch_bounds__(kThreads, 2)
   unsigned char *sm = dyn_smem<unsigned char>();
   __shared__ __align__(8) unsigned long long bars[3];  // stage A done, stage B done, tile landed
   __shared__ unsigned tslot;
-  __shared__ unsigned smax[2][2];  // largest |u_z|, |w_x| of a tile (float bits), by tile parity
+  __shared__ float lscale[128];  // 1 / (scale of u_z) per line of the tile
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int row = tid & 127, h = tid >> 7;
   const unsigned sbase = smem_addr(sm);
@@ -349,7 +349,6 @@ __global__ void __launch_bounds__(kThreads, 2)
     reinterpret_cast<float2 *>(sm + G::TW)[i] = make_float2(w.x, -w.y);
   }
   if (warp == 0) tmem_alloc(&tslot, G::TCOLS);
-  if (tid < 4) smax[tid >> 1][tid & 1] = 0u;
   if (tid == 0) {
     mbar_init(&bars[0], 1);
     mbar_init(&bars[1], 1);
@@ -421,54 +420,46 @@ __global__ void __launch_bounds__(kThreads, 2)
   const int line = row / R1, c = row % R1;  // this thread's stage-B row
   float umx = 0.f, umy = 0.f, umz = 0.f;
 
-  int tpar = 0;
-  for (long long tile = blockIdx.x; tile < tiles; tile += gridDim.x, tpar ^= 1) {
+  for (long long tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
     const long long line0 = line_base + tile * L;
-    // the pair (u_z, w_x) mixes fields of different size (|w| ~ |k| |u|), and
-    // a transform's rounding scales with the larger of its two fields: u_z
-    // enters scaled by s_uz = 2^e, the power of two that brings the tile's
-    // largest |u_z| near its largest |w_x| (exact both ways), and the product
-    // takes it back out
-    float inv_suz = 1.f;
     // ---------------------------------------------- inverse: three pairs --
     for (int pp = 0; pp < 3; ++pp) {
       wait_t();  // fields 2 pp, 2 pp + 1 of this tile's lines are in LAND
-      float sa = 1.f;
-      if (pp == 1) {
-        float ma = 0.f, mb = 0.f;
+      // the pair (u_z, w_x) mixes fields of different size (|w| ~ |k| |u|),
+      // and a transform's rounding scales with the larger of its two fields:
+      // u_z of a line enters scaled by s = 2^e, the power of two that brings
+      // the line's largest |u_z| near its largest |w_x| (exact both ways),
+      // and the product divides it out.  The R2 lanes that build a line's
+      // rows reduce its maxima together (both thread halves alike), so no
+      // block barrier is needed.
+      float sa[MT];
 #pragma unroll
-        for (int j = 0; j < MT; ++j) {
-          const int ra = row + 128 * j, ln = ra / R2, b = ra % R2;
+      for (int j = 0; j < MT; ++j) {
+        sa[j] = 1.f;
+        if (pp == 1) {
+          const int ra = row + 128 * j, ln = ra / R2, gl = lane % R2;
           const float2 *pa = land + ln * G::HS, *pb = pa + L * G::HS;
-#pragma unroll
-          for (int i = 0; i < CH; ++i) {
-            const int k = R2 * (h * CH + i) + b;
-            if (k <= KC || k >= N - KC) {
-              const int idx = k <= KC ? k : N - k;
-              const float2 xa = pa[idx], xb = pb[idx];
-              ma = fmaxf(ma, fmaxf(fabsf(xa.x), fabsf(xa.y)));
-              mb = fmaxf(mb, fmaxf(fabsf(xb.x), fabsf(xb.y)));
-            }
+          float ma = 0.f, mb = 0.f;
+          for (int k = gl; k <= KC; k += R2) {
+            const float2 xa = pa[k], xb = pb[k];
+            ma = fmaxf(ma, fmaxf(fabsf(xa.x), fabsf(xa.y)));
+            mb = fmaxf(mb, fmaxf(fabsf(xb.x), fabsf(xb.y)));
           }
-        }
-        for (int off = 16; off > 0; off >>= 1) {
-          ma = fmaxf(ma, __shfl_xor_sync(0xffffffffu, ma, off));
-          mb = fmaxf(mb, __shfl_xor_sync(0xffffffffu, mb, off));
-        }
-        if (lane == 0) {
-          atomicMax(&smax[tpar][0], __float_as_uint(ma));
-          atomicMax(&smax[tpar][1], __float_as_uint(mb));
-        }
-        __syncthreads();
-        const float ta = __uint_as_float(smax[tpar][0]), tb = __uint_as_float(smax[tpar][1]);
-        if (tid < 2) smax[tpar ^ 1][tid] = 0u;  // the next tile's slots (last read a tile ago)
-        if (ta > 0.f && tb > 0.f) {
-          int ea, eb;
-          frexpf(ta, &ea);
-          frexpf(tb, &eb);
-          const int e = max(-64, min(64, eb - ea));
-          sa = ldexpf(1.f, e);
-          inv_suz = ldexpf(1.f, -e);
+#pragma unroll
+          for (int off = R2 / 2; off > 0; off >>= 1) {
+            ma = fmaxf(ma, __shfl_xor_sync(0xffffffffu, ma, off, R2));
+            mb = fmaxf(mb, __shfl_xor_sync(0xffffffffu, mb, off, R2));
+          }
+          float inv = 1.f;
+          if (ma > 0.f && mb > 0.f) {
+            int ea, eb;
+            frexpf(ma, &ea);
+            frexpf(mb, &eb);
+            const int e = max(-64, min(64, eb - ea));
+            sa[j] = ldexpf(1.f, e);
+            inv = ldexpf(1.f, -e);
+          }
+          if (h == 0 && gl == 0) lscale[ln] = inv;  // read by the product after the next barriers
         }
       }
 #pragma unroll
@@ -487,8 +478,8 @@ __global__ void __launch_bounds__(kThreads, 2)
             xb = pb[idx];
           }
           if (k == 0) xa.y = xb.y = 0.f;  // the self-conjugate mode is real
-          xa.x *= sa;
-          xa.y *= sa;
+          xa.x *= sa[j];
+          xa.y *= sa[j];
           // k <= kc: z = xa + i xb;  k >= N - kc: z = conj(xa) + i conj(xb)
           zr[i] = lo ? xa.x - xb.y : xa.x + xb.y;
           zi[i] = lo ? xa.y + xb.x : xb.x - xa.y;
@@ -551,6 +542,7 @@ __global__ void __launch_bounds__(kThreads, 2)
         tmem_ld<CHK>(tlane + G::T3 + d0, wy);
         tmem_ld<CHK>(tlane + G::T3 + R2 + d0, wz);
         tmem_wait_ld();
+        const float inv_suz = lscale[line];
 #pragma unroll
         for (int i = 0; i < CHK; ++i) uz[i] *= inv_suz;
         float nx[CHK], ny[CHK], nz[CHK], nzp[CHK];
