@@ -869,18 +869,13 @@ __host__ __device__ constexpr int trunc_rows(int n) { return 2 * ((n - 1) / 3) +
 __host__ __device__ constexpr int tma_box_rows(int rows) { return rows < 256 ? rows : 256; }
 __host__ __device__ constexpr int tma_boxes(int rows) { return (rows + tma_box_rows(rows) - 1) / tma_box_rows(rows); }
 
-// inv2 with TMA loads: the same arithmetic as k3_inv2, persistent.  A block
-// walks the units (kx tile, plane z) blockIdx.x, blockIdx.x + gridDim.x, ...
-// and, in each, the fields 0..nf-1: one item per (unit, field).  Item j's
-// input column tile (the c retained ky rows of plane (f, z), W columns) lands
-// in a dense [rows][W] shared tile from a 3D tensor map over zb (kx, ky,
-// f N + z); the last box reaches past row c, where the tensor ends, so those
-// rows are zero-filled without any memory traffic.  Item j + 1 is issued as
-// soon as every thread has copied item j out of the tile, across unit
-// boundaries, so the copies never wait for a new block to start.
+// inv2 with TMA loads: the same arithmetic as k3_inv2.  Field f's input
+// column tile (the c retained ky rows of plane (f, z), W columns) lands in a
+// dense [rows][W] shared tile from a 3D tensor map over zb (kx, ky, f N + z);
+// the last box reaches past row c, where the tensor ends, so those rows are
+// zero-filled without any memory traffic.  Same hand-off as k3_fwd2_tma.
 template <typename R, int N, int W>
-__global__ void __launch_bounds__((N / 8) * W) k3_inv2_tma(Geo g, int nf, int z0, int nz,
-                                                            const __grid_constant__ CUtensorMap tm,
+__global__ void __launch_bounds__((N / 8) * W) k3_inv2_tma(Geo g, int nf, int z0, const __grid_constant__ CUtensorMap tm,
                                                             typename CplxOf<R>::T *__restrict__ yb,
                                                             const typename CplxOf<R>::T *__restrict__ tw, int *err) {
   using C = typename CplxOf<R>::T;
@@ -894,67 +889,65 @@ __global__ void __launch_bounds__((N / 8) * W) k3_inv2_tma(Geo g, int nf, int z0
   unsigned long long *bar = reinterpret_cast<unsigned long long *>(land + NBOX * BOXR * W);
   int &s_ok = *reinterpret_cast<int *>(bar + 1);
   const int w = threadIdx.x % W, t = threadIdx.x / W;
-  const int ntiles = g.hs / W;
-  const long long units = (long long)ntiles * nz;
-  const long long nitems = units > blockIdx.x ? ((units - 1 - blockIdx.x) / gridDim.x + 1) * nf : 0;
-  auto unit_of = [&](long long j) { return (long long)blockIdx.x + (j / nf) * gridDim.x; };
-  auto issue = [&](long long j) {
-    const long long u = unit_of(j);
-    const int tile = (int)(u % ntiles), z = z0 + (int)(u / ntiles), f = (int)(j % nf);
-    const int x8 = tile * W * (int)(sizeof(C) / 8);
+  const int kx = blockIdx.x * W + w;
+  const bool valid = kx < g.h;
+  const int z = z0 + blockIdx.y;
+  const int x8 = blockIdx.x * W * (int)(sizeof(C) / 8);
+  auto issue = [&](int f) {
     mbar_expect_tx(bar, (unsigned)LAND);
 #pragma unroll
     for (int b = 0; b < NBOX; ++b) tma_load_3d(land + b * BOXR * W, &tm, x8, b * BOXR, f * N + z, bar);
   };
   if (threadIdx.x == 0) {
     mbar_init(bar, 1);
-    if (nitems > 0) issue(0);  // no copy may outlive the block
+    if (nf > 0) issue(0);  // no copy may outlive the block
   }
-  for (long long j = 0; j < nitems; ++j) {
-    const long long u = unit_of(j);
-    const int tile = (int)(u % ntiles), z = z0 + (int)(u / ntiles), f = (int)(j % nf);
-    const int kx = tile * W + w;
-    const bool valid = kx < g.h;
+  int row[8];
+  bool live[8];
+#pragma unroll
+  for (int m = 0; m < 8; ++m) {
+    const int n = t + T * m;
+    live[m] = valid && retained(n, N, g.kc);
+    row[m] = compact_of(n, N, g.kc, g.c);
+  }
+  C *out = yb + (long long)z * N * g.hs + kx;
+  for (int f = 0; f < nf; ++f) {
     if (threadIdx.x == 0) {
-      bool ok = mbar_wait_bounded(bar, (unsigned)(j & 1));
+      bool ok = mbar_wait_bounded(bar, f & 1);
       if (!ok) {
         atomicExch(err, ERR_TMA_TIMEOUT);
-        mbar_wait_bounded(bar, (unsigned)(j & 1));  // give the copy in flight a last chance to land
+        mbar_wait_bounded(bar, f & 1);  // give the copy in flight a last chance to land
       }
       s_ok = ok;
     }
     __syncthreads();
     if (!s_ok) return;  // the whole block leaves together
-    mbar_try_wait(bar, (unsigned)(j & 1));  // completed: acquires the tile for this thread
+    mbar_try_wait(bar, f & 1);  // completed: acquires the tile for this thread
     C v[8];
 #pragma unroll
-    for (int m = 0; m < 8; ++m) {
-      const int n = t + T * m;
-      v[m] = valid && retained(n, N, g.kc) ? land[compact_of(n, N, g.kc, g.c) * W + w] : czero<C>();
-    }
+    for (int m = 0; m < 8; ++m) v[m] = live[m] ? land[row[m] * W + w] : czero<C>();
     __syncthreads();  // every thread has its values: the tile may be refilled
-    if (threadIdx.x == 0 && j + 1 < nitems) {
+    if (threadIdx.x == 0 && f + 1 < nf) {
       fence_proxy_async_smem();
-      issue(j + 1);
+      issue(f + 1);
     }
     fft_line<N, +1>(v, t, tw + N, SmCol<C, DB>{sm + w, P, N * P});
     if (valid) {
-      C *o = yb + f * g.yb_f + (long long)z * N * g.hs + kx;
+      C *o = out + f * g.yb_f;
 #pragma unroll
       for (int m = 0; m < 8; ++m) o[(long long)(t + T * m) * g.hs] = v[m];
     }
   }
 }
 
-// fwd2 with TMA loads: the same arithmetic as k3_fwd2, persistent like
-// k3_inv2_tma.  Item j's column tile (N rows of W columns, rows (f N + z) N ..
-// + N - 1 of yb viewed as a 2D array of 8-byte elements) lands in a dense
-// [N][W] shared tile (boxes of at most 256 rows); thread 0 waits for it
-// (bounded), the block barrier hands it to every thread, and each thread reads
-// its eight values t + T m of column w from the tile.
+// fwd2 with TMA loads: the same arithmetic as k3_fwd2.  Field f's column tile
+// (N rows of W columns, rows (f N + z) N .. + N - 1 of yb viewed as a 2D array
+// of 8-byte elements) lands in a dense [N][W] shared tile, issued by thread 0
+// one field ahead (boxes of at most 256 rows); thread 0 waits for it (bounded),
+// the block barrier hands it to every thread, and each thread reads its eight
+// values t + T m of column w from the tile.
 template <typename R, int N, int W>
-__global__ void __launch_bounds__((N / 8) * W) k3_fwd2_tma(Geo g, int nf, int z0, int nz,
-                                                            const __grid_constant__ CUtensorMap tm,
+__global__ void __launch_bounds__((N / 8) * W) k3_fwd2_tma(Geo g, int nf, int z0, const __grid_constant__ CUtensorMap tm,
                                                             typename CplxOf<R>::T *__restrict__ zb,
                                                             const typename CplxOf<R>::T *__restrict__ tw, int *err) {
   using C = typename CplxOf<R>::T;
@@ -969,14 +962,11 @@ __global__ void __launch_bounds__((N / 8) * W) k3_fwd2_tma(Geo g, int nf, int z0
   unsigned long long *bar = reinterpret_cast<unsigned long long *>(land + N * W);
   int &s_ok = *reinterpret_cast<int *>(bar + 1);
   const int w = threadIdx.x % W, t = threadIdx.x / W;
-  const int ntiles = g.hs / W;
-  const long long units = (long long)ntiles * nz;
-  const long long nitems = units > blockIdx.x ? ((units - 1 - blockIdx.x) / gridDim.x + 1) * nf : 0;
-  auto unit_of = [&](long long j) { return (long long)blockIdx.x + (j / nf) * gridDim.x; };
-  auto issue = [&](long long j) {
-    const long long u = unit_of(j);
-    const int tile = (int)(u % ntiles), z = z0 + (int)(u / ntiles), f = (int)(j % nf);
-    const int x8 = tile * W * (int)(sizeof(C) / 8);
+  const int kx = blockIdx.x * W + w;
+  const bool valid = kx < g.h;
+  const int z = z0 + blockIdx.y;
+  const int x8 = blockIdx.x * W * (int)(sizeof(C) / 8);
+  auto issue = [&](int f) {
     mbar_expect_tx(bar, TILE_BYTES);
     const int row0 = (f * N + z) * N;
 #pragma unroll
@@ -984,35 +974,32 @@ __global__ void __launch_bounds__((N / 8) * W) k3_fwd2_tma(Geo g, int nf, int z0
   };
   if (threadIdx.x == 0) {
     mbar_init(bar, 1);
-    if (nitems > 0) issue(0);  // no copy may outlive the block
+    if (nf > 0) issue(0);  // no copy may outlive the block
   }
-  for (long long j = 0; j < nitems; ++j) {
-    const long long u = unit_of(j);
-    const int tile = (int)(u % ntiles), z = z0 + (int)(u / ntiles), f = (int)(j % nf);
-    const int kx = tile * W + w;
-    const bool valid = kx < g.h;
+  C *out = zb + (long long)z * g.c * g.hs + kx;
+  for (int f = 0; f < nf; ++f) {
     if (threadIdx.x == 0) {
-      bool ok = mbar_wait_bounded(bar, (unsigned)(j & 1));
+      bool ok = mbar_wait_bounded(bar, f & 1);
       if (!ok) {
         atomicExch(err, ERR_TMA_TIMEOUT);
-        mbar_wait_bounded(bar, (unsigned)(j & 1));  // give the copy in flight a last chance to land
+        mbar_wait_bounded(bar, f & 1);  // give the copy in flight a last chance to land
       }
       s_ok = ok;
     }
     __syncthreads();
     if (!s_ok) return;  // the whole block leaves together
-    mbar_try_wait(bar, (unsigned)(j & 1));  // completed: acquires the tile for this thread
+    mbar_try_wait(bar, f & 1);  // completed: acquires the tile for this thread
     C v[8];
 #pragma unroll
     for (int m = 0; m < 8; ++m) v[m] = land[(t + T * m) * W + w];
     __syncthreads();  // every thread has its values: the tile may be refilled
-    if (threadIdx.x == 0 && j + 1 < nitems) {
+    if (threadIdx.x == 0 && f + 1 < nf) {
       fence_proxy_async_smem();
-      issue(j + 1);
+      issue(f + 1);
     }
     fft_line<N, -1>(v, t, tw + N, SmCol<C, DB>{sm + w, P, N * P});
     if (valid) {
-      C *o = zb + f * g.zb_f + (long long)z * g.c * g.hs + kx;
+      C *o = out + f * g.zb_f;
 #pragma unroll
       for (int m = 0; m < 8; ++m) {
         const int n = t + T * m;
@@ -1799,9 +1786,10 @@ struct Fwd1T {
 // and two rows of RK operands in flight; 512 points: 1024 threads, one block
 // per SM (fwd1 1.146 -> 1.034 ms per launch against the register-resident
 // form); 256 points: 512 threads, two blocks per SM (0.154 -> 0.148 ms;
-// 32 columns: 0.164 ms).
+// 32 columns: 0.164 ms); 1024 points: 8 columns, 1024 threads, one block per
+// SM (exchange tile 74 KB + spectral tile 131 KB).
 template <typename R, int N>
-using Fwd1Pick = Fwd1T<R, N, 16, true, 2, (N == 512 ? 1 : 2)>;
+using Fwd1Pick = Fwd1T<R, N, (N == 1024 ? 8 : 16), true, 2, (N == 256 ? 2 : 1)>;
 
 template <typename R, int N>
 struct Launch3 {
@@ -1826,8 +1814,8 @@ struct Launch3 {
   static constexpr size_t SM_F1 = col_tile_bytes(N, WH, sizeof(C)) + (size_t)36 * T * WH * sizeof(C);
   static constexpr size_t SM_F1S = col_tile_bytes(N, WH, sizeof(C)) + (size_t)18 * T * WH * sizeof(C);
   static_assert(SM_F1 <= kSmemMax, "fwd1 shared memory");
-  // fwd1 with the shared spectral tile: FP32, 256 and 512 points
-  static constexpr bool F1T = sizeof(R) == 4 && (N == 256 || N == 512);
+  // fwd1 with the shared spectral tile: FP32, 256 to 1024 points
+  static constexpr bool F1T = sizeof(R) == 4 && (N == 256 || N == 512 || N == 1024);
   static constexpr size_t SM_X = (size_t)L * smline_len(N / 2) * sizeof(C);
   static constexpr size_t SM_XP = SM_X + (size_t)24 * (N / 16) * L * sizeof(C);  // + parked velocity fields
   // warp-per-line x pass when a line fits in one warp
@@ -1836,8 +1824,8 @@ struct Launch3 {
   static constexpr int XW_LPW = XW ? 32 / (N / 16) : 1;
   static constexpr size_t SM_XW =
       (size_t)XW_WPB * (XW_LPW * xw_line_len<N, (XW_LPW > 1)>() + 3 * 8 * 32) * sizeof(C);
-  // paired-field x pass (FP32, 128 <= N <= 512)
-  static constexpr bool XP = sizeof(R) == 4 && N >= 128 && N <= 512;
+  // paired-field x pass (FP32, 128 <= N <= 1024)
+  static constexpr bool XP = sizeof(R) == 4 && N >= 128 && N <= 1024;
   static constexpr int XP_G = xp_groups<N>();
   static constexpr size_t SM_XPP = (size_t)XP_G * xp_group_elems(N) * sizeof(C);
 
@@ -1884,15 +1872,8 @@ struct Launch3 {
         const int nz = a.nz > 0 ? a.nz : N;
         if constexpr (YI_TMA) {
           if (a.tmap_zb != nullptr) {
-            static int per_sm = 0;  // persistent: one wave of resident blocks
-            if (per_sm == 0) {
-              cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k3_inv2_tma<R, N, WYI>, T * WYI, SM_YIT);
-              if (per_sm < 1) per_sm = 1;
-            }
-            const int units = (g.hs / WYI) * nz;
-            const int grid = cmin(units, per_sm * (a.nsm > 0 ? a.nsm : 1));
-            k3_inv2_tma<R, N, WYI><<<grid, T * WYI, SM_YIT, s>>>(
-                g, a.nf, a.z0, nz, *reinterpret_cast<const CUtensorMap *>(a.tmap_zb), (C *)a.yb, tw, a.err);
+            k3_inv2_tma<R, N, WYI><<<dim3(g.hs / WYI, nz), T * WYI, SM_YIT, s>>>(
+                g, a.nf, a.z0, *reinterpret_cast<const CUtensorMap *>(a.tmap_zb), (C *)a.yb, tw, a.err);
             break;
           }
         }
@@ -1918,15 +1899,8 @@ struct Launch3 {
         const int nz = a.nz > 0 ? a.nz : N;
         if constexpr (YF_TMA) {
           if (a.tmap_yb != nullptr) {
-            static int per_sm = 0;  // persistent: one wave of resident blocks
-            if (per_sm == 0) {
-              cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k3_fwd2_tma<R, N, WYF>, T * WYF, SM_YFT);
-              if (per_sm < 1) per_sm = 1;
-            }
-            const int units = (g.hs / WYF) * nz;
-            const int grid = cmin(units, per_sm * (a.nsm > 0 ? a.nsm : 1));
-            k3_fwd2_tma<R, N, WYF><<<grid, T * WYF, SM_YFT, s>>>(
-                g, a.nf, a.z0, nz, *reinterpret_cast<const CUtensorMap *>(a.tmap_yb), (C *)a.zb, tw, a.err);
+            k3_fwd2_tma<R, N, WYF><<<dim3(g.hs / WYF, nz), T * WYF, SM_YFT, s>>>(
+                g, a.nf, a.z0, *reinterpret_cast<const CUtensorMap *>(a.tmap_yb), (C *)a.zb, tw, a.err);
             break;
           }
         }

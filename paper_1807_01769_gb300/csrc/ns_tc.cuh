@@ -478,8 +478,10 @@ __global__ void __launch_bounds__(kThreads, 2)
             xb = pb[idx];
           }
           if (k == 0) xa.y = xb.y = 0.f;  // the self-conjugate mode is real
-          xa.x *= sa[j];
-          xa.y *= sa[j];
+          if (pp == 1) {
+            xa.x *= sa[j];
+            xa.y *= sa[j];
+          }
           // k <= kc: z = xa + i xb;  k >= N - kc: z = conj(xa) + i conj(xb)
           zr[i] = lo ? xa.x - xb.y : xa.x + xb.y;
           zi[i] = lo ? xa.y + xb.x : xb.x - xa.y;
