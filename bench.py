@@ -471,6 +471,12 @@ def run_gb300(args):
     h_in = torch.from_numpy(u0.view(np.float64).reshape(-1)).pin_memory()
     h_out = torch.empty(s.sizes["state_doubles"], dtype=torch.float64).pin_memory()
     e2e_reps = max(1, args.e2e_reps)
+    # one untimed job first: the first copies from freshly pinned buffers pay
+    # a one-time mapping cost (about 16 ms each way at 512^3)
+    s.set_state_spectral_ptr(h_in.data_ptr())
+    s.step(JOB_STEPS)
+    s.get_state_spectral_ptr(h_out.data_ptr())
+    s.energy_spectrum()
     barrier()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -509,7 +515,7 @@ def run_gb300(args):
                     "h2d_bytes_per_step": spec_bytes / JOB_STEPS,
                     "d2h_bytes_per_step": (spec_bytes + spec.nbytes) / JOB_STEPS,
                     "job": f"H2D of the FP64 initial spectrum (pinned), {JOB_STEPS} steps, D2H of the state and "
-                           f"spectrum; {e2e_reps} jobs"},
+                           f"spectrum; {e2e_reps} jobs after one untimed job"},
             "gpu_launches": launches_per_step * args.steps,
             "energy_after": e, "enstrophy_after": om,
         }

@@ -81,6 +81,18 @@ long long diag_blocks(const Geo &g) {
 
 long long diag_scratch_doubles(const Geo &g, int nbins) { return diag_blocks(g) * (nbins + 2); }
 
+// Shell index round(|k|) of an integer |k|^2 without a double-precision
+// square root: for k2 >= 1 it is the largest m with m (m - 1) < k2 (the tie
+// (m - 1/2)^2 = k2 never occurs for integers); an FP32 estimate is corrected
+// by integer comparisons.
+__device__ __forceinline__ int shell_of(long long k2) {
+  if (k2 <= 0) return 0;
+  int m = (int)(sqrtf((float)k2) + 0.5f);
+  while ((long long)m * (m - 1) >= k2) --m;
+  while ((long long)(m + 1) * m < k2) ++m;
+  return m;
+}
+
 // scratch row of block b: [energy, enstrophy, bins 0 .. nbins-1]
 template <typename C>
 __global__ void __launch_bounds__(32 * kDiagWarps) k_diag(Geo g, const C *__restrict__ u, int nbins, int rows_per_block,
@@ -110,7 +122,7 @@ __global__ void __launch_bounds__(32 * kDiagWarps) k_diag(Geo g, const C *__rest
       if (active) {
         const double w = kx == 0 ? 1.0 : 2.0;
         const long long k2 = (long long)kx * kx + (long long)ky * ky + (long long)kz * kz;
-        bin = (int)floor(sqrt((double)k2) + 0.5);
+        bin = shell_of(k2);
         if (g.dim == 3) {
           const C a = u[base + kx], b = u[g.st_comp + base + kx], c = u[2 * g.st_comp + base + kx];
           const double ax = a.x, ay = a.y, bx = b.x, by = b.y, cx = c.x, cy = c.y;
