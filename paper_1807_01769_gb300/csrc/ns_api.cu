@@ -92,6 +92,8 @@ struct ns_state {
   alignas(128) unsigned char tmap_yb[128];
   alignas(128) unsigned char tmap_zb[128];
   bool has_tmap = false, has_tmap_zb = false;
+  // omega_z left to the y pass (the first-axis passes store five curl fields)
+  bool wz = false;
   int *derr = nullptr;
   // 3D step schedule: the y inverse, x pass and y forward of a stage run as a
   // pipeline over zchunks plane chunks on three forked streams, the y inverse
@@ -171,6 +173,7 @@ Args base_args(ns_state *s) {
   a.tmap_zb = s->has_tmap_zb ? s->tmap_zb : nullptr;
   a.err = s->derr;
   a.nsm = s->nsm;
+  a.wz = s->wz ? 1 : 0;
   return a;
 }
 
@@ -571,9 +574,11 @@ int ns_init(ns_state **out, const ns_grid *grid, double nu, double dt, const dou
     if ((wi * s->cs) % 16 == 0) {
       const unsigned long long dims[3] = {g.hs * e8, (unsigned long long)g.c, 6ull * g.N},
                                strides[2] = {row, row * g.c};
-      const unsigned box[3] = {(unsigned)(wi * e8), (unsigned)std::min(g.c, 256), 1};
+      const unsigned box[3] = {(unsigned)(wi * e8), (unsigned)nsk::tma_box_rows(g.c), 1};
       s->has_tmap_zb = nsk::make_tensor_map(s->tmap_zb, s->zb, 3, dims, strides, box) == 0;
     }
+    // FP32 at 256 and 512 points: the y pass forms omega_z itself
+    s->wz = s->has_tmap_zb && s->cs == 8 && (g.N == 256 || g.N == 512);
   }
   INIT_CK(cudaMemcpyAsync(s->tw, tw.data(), tw.size(), cudaMemcpyHostToDevice, s->stream));
   INIT_CK(cudaMemcpyAsync(s->ef, ef.data(), ef.size(), cudaMemcpyHostToDevice, s->stream));
@@ -971,15 +976,16 @@ long long ns_kernel_bytes(const ns_state *s, int id) {
   const bool f = s->F != nullptr;
   if (s->grid.dim == 3) {
     const long long T = c * c * h, Z = N * c * h, Y = N * N * h;
+    const long long zc = s->wz ? 5 : 6;  // first-axis curl fields stored (omega_z left to inv2)
     switch (id) {
-      case 0: return cs * (3 * T + 6 * Z);
-      case 1: return cs * (6 * Z + 6 * Y);
+      case 0: return cs * (3 * T + zc * Z);
+      case 1: return cs * (zc * Z + 6 * Y);
       case 2: return cs * (6 * Y + 3 * Y);
       case 3: return cs * (3 * Y + 3 * Z);
-      default:  // 3 fields in, 6 out, plus the RK operands averaged over the
+      default:  // 3 fields in, zc out, plus the RK operands averaged over the
                 // stages (RK4: state-sized reads 18 T, writes 12 T per step over
                 // four stages; RK2: reads 6 T, writes 3 T over two)
-        return cs * (9 * Z + (s->order == 2 ? (9 * T) / 2 : (15 * T) / 2) + (f ? 3 * T : 0));
+        return cs * ((3 + zc) * Z + (s->order == 2 ? (9 * T) / 2 : (15 * T) / 2) + (f ? 3 * T : 0));
     }
   }
   const long long T = c * h, Y = N * h;

@@ -66,6 +66,8 @@ struct Args {
   const void *ek2, *ek22;    // OP_FWD1: E, E2 indexed by |k|^2 (hyper-viscosity), nullable
   unsigned long long *umax;  // OP_XPASS: [dim][kUmaxSlots] maxima of |u_i| as double bits (nullable)
   int nsm;     // streaming multiprocessors of the device (persistent grids)
+  int wz;      // 3D curl fields: omega_z (zb field 5) is not stored by OP_INV1 / OP_FWD1 but
+               // formed by OP_INV2 from u_x and u_y (FP32 at 256 and 512 points with TMA loads)
   int z0, nz;  // 3D OP_INV2 / OP_XPASS / OP_FWD2: planes z0 .. z0+nz-1 (nz = 0: all)
 };
 
@@ -97,6 +99,14 @@ int cfl_update(int prec, const Geo &g, double nu, unsigned long long *umax, doub
 // else a cudaError_t / CUresult value.
 int make_tensor_map(void *out, const void *base, int rank, const unsigned long long *dims,
                     const unsigned long long *strides_bytes, const unsigned *box);
+
+// Retained rows of a truncated axis (c = 2 kc + 1) and the TMA boxes that
+// cover them: as few boxes of at most 256 rows as possible, of equal height
+// (341 rows: 2 x 171; 683: 3 x 228), so the landing tile holds at most a few
+// rows more than the data.
+__host__ __device__ constexpr int trunc_rows(int n) { return 2 * ((n - 1) / 3) + 1; }
+__host__ __device__ constexpr int tma_boxes(int rows) { return (rows + 255) / 256; }
+__host__ __device__ constexpr int tma_box_rows(int rows) { return (rows + tma_boxes(rows) - 1) / tma_boxes(rows); }
 
 // Columns per tile of the y passes for complex elements of csize bytes on
 // N-point columns (tile rows of at most 128 bytes).  Inverse: 512-thread

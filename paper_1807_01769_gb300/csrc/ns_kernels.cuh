@@ -277,7 +277,7 @@ __host__ __device__ constexpr int xw_line_len() {
 template <typename R, int N, int W, bool CURL>
 __global__ void __launch_bounds__((N / 8) * W) k3_inv1(Geo g, const typename CplxOf<R>::T *__restrict__ src,
                                                         typename CplxOf<R>::T *__restrict__ zb,
-                                                        const typename CplxOf<R>::T *__restrict__ tw) {
+                                                        const typename CplxOf<R>::T *__restrict__ tw, int wz) {
   using C = typename CplxOf<R>::T;
   constexpr int T = N / 8;
   constexpr int P = pitch_of(W, sizeof(C));
@@ -336,7 +336,7 @@ __global__ void __launch_bounds__((N / 8) * W) k3_inv1(Geo g, const typename Cpl
     if (CURL && f == 0) {
 #pragma unroll
       for (int m = 0; m < 8; ++m) zx[m] = v[m];
-    } else if (CURL && f == 1 && valid) {
+    } else if (CURL && f == 1 && valid && !wz) {
 #pragma unroll
       for (int m = 0; m < 8; ++m)
         zb[5 * g.zb_f + (long long)(t + T * m) * plane + col] =
@@ -863,18 +863,21 @@ __device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *tm, in
       : "memory");
 }
 
-// Retained rows of a truncated axis (c = 2 kc + 1) and the TMA boxes that
-// cover them: rows per box (at most 256) and boxes per column tile.
-__host__ __device__ constexpr int trunc_rows(int n) { return 2 * ((n - 1) / 3) + 1; }
-__host__ __device__ constexpr int tma_box_rows(int rows) { return rows < 256 ? rows : 256; }
-__host__ __device__ constexpr int tma_boxes(int rows) { return (rows + tma_box_rows(rows) - 1) / tma_box_rows(rows); }
 
 // inv2 with TMA loads: the same arithmetic as k3_inv2.  Field f's input
 // column tile (the c retained ky rows of plane (f, z), W columns) lands in a
 // dense [rows][W] shared tile from a 3D tensor map over zb (kx, ky, f N + z);
 // the last box reaches past row c, where the tensor ends, so those rows are
 // zero-filled without any memory traffic.  Same hand-off as k3_fwd2_tma.
-template <typename R, int N, int W>
+//
+// WZ (nf = 6, the curl fields): omega_z = i (kx u_y - ky u_x) is pointwise in
+// (z, ky, kx), so it is not read from zb (its producer does not store it) but
+// formed here from the landed tiles of u_x and u_y.  Two landing tiles;
+// fields in the order u_x, u_y, omega_z, u_z, omega_x, omega_y: tile A takes
+// u_x, u_z, omega_y and tile B u_y, omega_x, each refilled as soon as every
+// thread has read it.  The same values and operations as a stored omega_z,
+// so the results are bit for bit those of the six-field form.
+template <typename R, int N, int W, bool WZ = false>
 __global__ void __launch_bounds__((N / 8) * W) k3_inv2_tma(Geo g, int nf, int z0, const __grid_constant__ CUtensorMap tm,
                                                             typename CplxOf<R>::T *__restrict__ yb,
                                                             const typename CplxOf<R>::T *__restrict__ tw, int *err) {
@@ -882,26 +885,26 @@ __global__ void __launch_bounds__((N / 8) * W) k3_inv2_tma(Geo g, int nf, int z0
   constexpr int T = N / 8;
   constexpr int P = pitch_of(W, sizeof(C));
   constexpr int CR = trunc_rows(N), BOXR = tma_box_rows(CR), NBOX = tma_boxes(CR);
-  constexpr size_t LAND = (size_t)NBOX * BOXR * W * sizeof(C);
-  constexpr bool DB = col_db(N, W, sizeof(C), LAND + 16);
+  constexpr int LROWS = NBOX * BOXR;
+  constexpr size_t LAND = (size_t)LROWS * W * sizeof(C);
+  constexpr int NLAND = WZ ? 2 : 1;
+  constexpr bool DB = col_db(N, W, sizeof(C), NLAND * LAND + 32);
   C *sm = dyn_smem<C>();
-  C *land = sm + (DB ? 2 : 1) * N * P;  // [NBOX * BOXR][W]
-  unsigned long long *bar = reinterpret_cast<unsigned long long *>(land + NBOX * BOXR * W);
-  int &s_ok = *reinterpret_cast<int *>(bar + 1);
+  C *land = sm + (DB ? 2 : 1) * N * P;  // [NLAND][LROWS][W]
+  unsigned long long *bar = reinterpret_cast<unsigned long long *>(land + NLAND * LROWS * W);  // one per tile
+  int &s_ok = *reinterpret_cast<int *>(bar + 2);
   const int w = threadIdx.x % W, t = threadIdx.x / W;
   const int kx = blockIdx.x * W + w;
   const bool valid = kx < g.h;
   const int z = z0 + blockIdx.y;
   const int x8 = blockIdx.x * W * (int)(sizeof(C) / 8);
-  auto issue = [&](int f) {
-    mbar_expect_tx(bar, (unsigned)LAND);
+  // field f into landing tile q
+  auto issue = [&](int q, int f) {
+    mbar_expect_tx(bar + q, (unsigned)LAND);
 #pragma unroll
-    for (int b = 0; b < NBOX; ++b) tma_load_3d(land + b * BOXR * W, &tm, x8, b * BOXR, f * N + z, bar);
+    for (int b = 0; b < NBOX; ++b)
+      tma_load_3d(land + (q * LROWS + b * BOXR) * W, &tm, x8, b * BOXR, f * N + z, bar + q);
   };
-  if (threadIdx.x == 0) {
-    mbar_init(bar, 1);
-    if (nf > 0) issue(0);  // no copy may outlive the block
-  }
   int row[8];
   bool live[8];
 #pragma unroll
@@ -911,32 +914,106 @@ __global__ void __launch_bounds__((N / 8) * W) k3_inv2_tma(Geo g, int nf, int z0
     row[m] = compact_of(n, N, g.kc, g.c);
   }
   C *out = yb + (long long)z * N * g.hs + kx;
-  for (int f = 0; f < nf; ++f) {
+  // wait (bounded) for tile q's phase ph; false: the block leaves
+  auto landed = [&](int q, unsigned ph) {
     if (threadIdx.x == 0) {
-      bool ok = mbar_wait_bounded(bar, f & 1);
+      bool ok = mbar_wait_bounded(bar + q, ph);
       if (!ok) {
         atomicExch(err, ERR_TMA_TIMEOUT);
-        mbar_wait_bounded(bar, f & 1);  // give the copy in flight a last chance to land
+        mbar_wait_bounded(bar + q, ph);  // give the copy in flight a last chance to land
       }
       s_ok = ok;
     }
     __syncthreads();
-    if (!s_ok) return;  // the whole block leaves together
-    mbar_try_wait(bar, f & 1);  // completed: acquires the tile for this thread
-    C v[8];
-#pragma unroll
-    for (int m = 0; m < 8; ++m) v[m] = live[m] ? land[row[m] * W + w] : czero<C>();
-    __syncthreads();  // every thread has its values: the tile may be refilled
-    if (threadIdx.x == 0 && f + 1 < nf) {
-      fence_proxy_async_smem();
-      issue(f + 1);
-    }
+    if (!s_ok) return false;
+    mbar_try_wait(bar + q, ph);  // completed: acquires the tile for this thread
+    return true;
+  };
+  auto transform_store = [&](C (&v)[8], int f) {
     fft_line<N, +1>(v, t, tw + N, SmCol<C, DB>{sm + w, P, N * P});
     if (valid) {
       C *o = out + f * g.yb_f;
 #pragma unroll
       for (int m = 0; m < 8; ++m) o[(long long)(t + T * m) * g.hs] = v[m];
     }
+  };
+  if constexpr (!WZ) {
+    if (threadIdx.x == 0) {
+      mbar_init(bar, 1);
+      if (nf > 0) issue(0, 0);  // no copy may outlive the block
+    }
+    for (int f = 0; f < nf; ++f) {
+      if (!landed(0, f & 1)) return;  // the whole block leaves together
+      C v[8];
+#pragma unroll
+      for (int m = 0; m < 8; ++m) v[m] = live[m] ? land[row[m] * W + w] : czero<C>();
+      __syncthreads();  // every thread has its values: the tile may be refilled
+      if (threadIdx.x == 0 && f + 1 < nf) {
+        fence_proxy_async_smem();
+        issue(0, f + 1);
+      }
+      transform_store(v, f);
+    }
+  } else {
+    const C *la = land, *lb = land + LROWS * W;
+    if (threadIdx.x == 0) {
+      mbar_init(bar, 1);
+      mbar_init(bar + 1, 1);
+      issue(0, 0);  // u_x
+      issue(1, 1);  // u_y
+    }
+    C v[8];
+    // u_x (tile A stays: omega_z needs it)
+    if (!landed(0, 0)) return;
+#pragma unroll
+    for (int m = 0; m < 8; ++m) v[m] = live[m] ? la[row[m] * W + w] : czero<C>();
+    transform_store(v, 0);
+    // u_y (tile B stays)
+    if (!landed(1, 0)) return;
+#pragma unroll
+    for (int m = 0; m < 8; ++m) v[m] = live[m] ? lb[row[m] * W + w] : czero<C>();
+    transform_store(v, 1);
+    // omega_z = i (kx u_y - ky u_x); then both tiles are refilled
+    {
+      const R kxr = (R)kx;
+#pragma unroll
+      for (int m = 0; m < 8; ++m) {
+        if (live[m]) {
+          const R kyr = (R)ktr_of(row[m], g.kc, g.c);
+          const C ux = la[row[m] * W + w], uy = lb[row[m] * W + w];
+          v[m] = cmuli(C{kxr * uy.x - kyr * ux.x, kxr * uy.y - kyr * ux.y});
+        } else {
+          v[m] = czero<C>();
+        }
+      }
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        fence_proxy_async_smem();
+        issue(0, 2);  // u_z
+        issue(1, 3);  // omega_x
+      }
+      transform_store(v, 5);
+    }
+    // u_z from tile A, which then takes omega_y
+    if (!landed(0, 1)) return;
+#pragma unroll
+    for (int m = 0; m < 8; ++m) v[m] = live[m] ? la[row[m] * W + w] : czero<C>();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      fence_proxy_async_smem();
+      issue(0, 4);
+    }
+    transform_store(v, 2);
+    // omega_x from tile B
+    if (!landed(1, 1)) return;
+#pragma unroll
+    for (int m = 0; m < 8; ++m) v[m] = live[m] ? lb[row[m] * W + w] : czero<C>();
+    transform_store(v, 3);
+    // omega_y from tile A
+    if (!landed(0, 0)) return;
+#pragma unroll
+    for (int m = 0; m < 8; ++m) v[m] = live[m] ? la[row[m] * W + w] : czero<C>();
+    transform_store(v, 4);
   }
 }
 
@@ -1024,6 +1101,7 @@ struct StepBufs {
   // hyper-viscous states: E, E2 indexed by |k|^2 (the operator does not
   // factor over the axes); null = the per-axis tables ef, ef2
   const R *ek2, *ek22;
+  int wz;  // 1: the next inverse leaves omega_z (zb field 5) to the y pass
 };
 
 // The time step of a stage update: read from device memory at each use when
@@ -1450,7 +1528,7 @@ __global__ void __launch_bounds__((N / 8) * W, MINB) k3_fwd1t(Geo g, StepBufs<R>
         if (valid) {
 #pragma unroll
           for (int m = 0; m < 8; ++m) b.zb[f * g.zb_f + (long long)(t + T * m) * plane + col] = v[m];
-          if (f == 1) {  // omega_z = i (kx u_y - ky u_x), u_x as this thread stored it for f = 0
+          if (f == 1 && !b.wz) {  // omega_z = i (kx u_y - ky u_x), u_x as this thread stored it for f = 0
 #pragma unroll
             for (int m = 0; m < 8; ++m) {
               const long long o = (long long)(t + T * m) * plane + col;
@@ -1749,6 +1827,7 @@ inline StepBufs<R> step_bufs(const Args &a) {
   b.dtp = a.dtp;
   b.ek2 = (const R *)a.ek2;
   b.ek22 = (const R *)a.ek22;
+  b.wz = a.wz;
   return b;
 }
 
@@ -1808,6 +1887,12 @@ struct Launch3 {
   static constexpr size_t SM_YIT = col_smem(
       N, WYI, sizeof(C), (size_t)tma_boxes(trunc_rows(N)) * tma_box_rows(trunc_rows(N)) * WYI * sizeof(C) + 16);
   static constexpr bool YI_TMA = (WYI * sizeof(C)) % 16 == 0 && SM_YIT <= kSmemMax;
+  // inv2 forming omega_z from u_x and u_y (two landing tiles): FP32 at 256 and
+  // 512 points, where the exchange tile stays double-buffered beside them
+  static constexpr size_t SM_YIW = col_smem(
+      N, WYI, sizeof(C), 2 * (size_t)tma_boxes(trunc_rows(N)) * tma_box_rows(trunc_rows(N)) * WYI * sizeof(C) + 32);
+  static constexpr bool YI_WZ = YI_TMA && sizeof(R) == 4 && (N == 256 || N == 512);
+  static_assert(!YI_WZ || SM_YIW <= kSmemMax, "inv2 with two landing tiles");
   // persistent fwd1: exchange tile + RK operand slots (3 comps x 6 per thread
   // for each operand: two for RK2/RK3, one for the other stages; the smaller
   // allocation leaves more of the SM's L1, which fwd1 is sensitive to)
@@ -1842,6 +1927,7 @@ struct Launch3 {
         set_smem(k3_inv1<R, N, WL, false>, SM_L);
         set_smem(k3_inv2<R, N, WYI>, SM_YI);
         if constexpr (YI_TMA) set_smem(k3_inv2_tma<R, N, WYI>, SM_YIT);
+        if constexpr (YI_WZ) set_smem(k3_inv2_tma<R, N, WYI, true>, SM_YIW);
         set_smem(k3_fwd2<R, N, WYF>, SM_YF);
         if constexpr (YF_TMA) set_smem(k3_fwd2_tma<R, N, WYF>, SM_YFT);
         if constexpr (!XW) set_smem(k3_xpass<R, N, L>, SM_XP);
@@ -1863,13 +1949,23 @@ struct Launch3 {
       case OP_INV1: {
         const dim3 grid(g.c * (g.hs / WL));
         if (a.curl)
-          k3_inv1<R, N, WL, true><<<grid, T * WL, SM_L, s>>>(g, (const C *)a.src, (C *)a.zb, tw);
+          k3_inv1<R, N, WL, true><<<grid, T * WL, SM_L, s>>>(g, (const C *)a.src, (C *)a.zb, tw, a.wz);
         else
-          k3_inv1<R, N, WL, false><<<grid, T * WL, SM_L, s>>>(g, (const C *)a.src, (C *)a.zb, tw);
+          k3_inv1<R, N, WL, false><<<grid, T * WL, SM_L, s>>>(g, (const C *)a.src, (C *)a.zb, tw, 0);
         break;
       }
       case OP_INV2: {
         const int nz = a.nz > 0 ? a.nz : N;
+        if (a.wz && a.nf == 6) {  // omega_z is formed here: only the TMA form with two landing tiles does it
+          if constexpr (YI_WZ) {
+            if (a.tmap_zb != nullptr && a.nf == 6) {
+              k3_inv2_tma<R, N, WYI, true><<<dim3(g.hs / WYI, nz), T * WYI, SM_YIW, s>>>(
+                  g, a.nf, a.z0, *reinterpret_cast<const CUtensorMap *>(a.tmap_zb), (C *)a.yb, tw, a.err);
+              break;
+            }
+          }
+          return -1;
+        }
         if constexpr (YI_TMA) {
           if (a.tmap_zb != nullptr) {
             k3_inv2_tma<R, N, WYI><<<dim3(g.hs / WYI, nz), T * WYI, SM_YIT, s>>>(

@@ -344,10 +344,11 @@ def test_max_size_3d_1024(ns, orc, prec, steps, tol):
     assert abs(e - re) < tol * re and abs(om - rom) < tol * rom
 
 
-def test_plane_chunk_pipeline_is_bitwise_identical(ns, monkeypatch):
+@pytest.mark.parametrize("n", [128, 256])
+def test_plane_chunk_pipeline_is_bitwise_identical(ns, monkeypatch, n):
     # the 3D y-x-y pipeline over plane chunks runs the same kernels on the same
-    # data in another order: results must not change by a bit
-    n = 128
+    # data in another order: results must not change by a bit (256: the y pass
+    # forms omega_z from u_x and u_y)
     u0 = ic(3, n, seed=12)
     out = []
     for chunks, look in [("1", "2"), ("8", "1"), ("16", "3")]:
