@@ -962,47 +962,58 @@ __global__ void __launch_bounds__((N / 8) * W) k3_inv2_tma(Geo g, int nf, int z0
       issue(0, 0);  // u_x
       issue(1, 1);  // u_y
     }
-    // items in order: u_x (tile A, kept), u_y (tile B, kept), omega_z (from
-    // both, then A takes u_z and B omega_x), u_z (A, then A takes omega_y),
-    // omega_x (B), omega_y (A); one loop so that the transform's code is
-    // emitted once
-#pragma unroll 1
-    for (int it = 0; it < 6; ++it) {
-      const int f = it == 2 ? 5 : (it < 2 ? it : it - 1);
-      const int q = (it == 1 || it == 4) ? 1 : 0;
-      const unsigned ph = (it == 3 || it == 4) ? 1u : 0u;
-      if (it != 2 && !landed(q, ph)) return;  // the whole block leaves together
-      const C *lt = q ? lb : la;
+    C v[8];
+    // u_x (tile A stays: omega_z needs it)
+    if (!landed(0, 0)) return;
+#pragma unroll
+    for (int m = 0; m < 8; ++m) v[m] = live[m] ? la[row[m] * W + w] : czero<C>();
+    transform_store(v, 0);
+    // u_y (tile B stays)
+    if (!landed(1, 0)) return;
+#pragma unroll
+    for (int m = 0; m < 8; ++m) v[m] = live[m] ? lb[row[m] * W + w] : czero<C>();
+    transform_store(v, 1);
+    // omega_z = i (kx u_y - ky u_x); then both tiles are refilled
+    {
       const R kxr = (R)kx;
-      C v[8];
 #pragma unroll
       for (int m = 0; m < 8; ++m) {
-        C x = czero<C>();
         if (live[m]) {
-          if (it == 2) {  // omega_z = i (kx u_y - ky u_x)
-            const R kyr = (R)ktr_of(row[m], g.kc, g.c);
-            const C ux = la[row[m] * W + w], uy = lb[row[m] * W + w];
-            x = cmuli(C{kxr * uy.x - kyr * ux.x, kxr * uy.y - kyr * ux.y});
-          } else {
-            x = lt[row[m] * W + w];
-          }
-        }
-        v[m] = x;
-      }
-      if (it == 2 || it == 3) {
-        __syncthreads();  // every thread has read the tiles being refilled
-        if (threadIdx.x == 0) {
-          fence_proxy_async_smem();
-          if (it == 2) {
-            issue(0, 2);  // u_z
-            issue(1, 3);  // omega_x
-          } else {
-            issue(0, 4);  // omega_y
-          }
+          const R kyr = (R)ktr_of(row[m], g.kc, g.c);
+          const C ux = la[row[m] * W + w], uy = lb[row[m] * W + w];
+          v[m] = cmuli(C{kxr * uy.x - kyr * ux.x, kxr * uy.y - kyr * ux.y});
+        } else {
+          v[m] = czero<C>();
         }
       }
-      transform_store(v, f);
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        fence_proxy_async_smem();
+        issue(0, 2);  // u_z
+        issue(1, 3);  // omega_x
+      }
+      transform_store(v, 5);
     }
+    // u_z from tile A, which then takes omega_y
+    if (!landed(0, 1)) return;
+#pragma unroll
+    for (int m = 0; m < 8; ++m) v[m] = live[m] ? la[row[m] * W + w] : czero<C>();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      fence_proxy_async_smem();
+      issue(0, 4);
+    }
+    transform_store(v, 2);
+    // omega_x from tile B
+    if (!landed(1, 1)) return;
+#pragma unroll
+    for (int m = 0; m < 8; ++m) v[m] = live[m] ? lb[row[m] * W + w] : czero<C>();
+    transform_store(v, 3);
+    // omega_y from tile A
+    if (!landed(0, 0)) return;
+#pragma unroll
+    for (int m = 0; m < 8; ++m) v[m] = live[m] ? la[row[m] * W + w] : czero<C>();
+    transform_store(v, 4);
   }
 }
 
