@@ -39,11 +39,31 @@ if ROOT not in sys.path:
 N_GRID = 512
 NU, DT = 2e-3, 1e-3
 JOB_STEPS = 20
-METRIC = "Mpoint*RK4-steps/s at 3D 512^3 FP32"
 UNIT = "Mpoint*steps/s"
-WORKLOAD = ("3D incompressible NS 512^3 FP32, random-phase solenoidal IC E(k)~k^4 exp(-2(k/4)^2), E=0.5, seed 0, "
+
+
+def metric_name(n=None, tc=False):
+    n = N_GRID if n is None else n
+    return f"Mpoint*RK4-steps/s at 3D {n}^3 " + ("FP32 (tensor-core x pass)" if tc else "FP32")
+
+
+def workload(n=None, tc=False):
+    n = N_GRID if n is None else n
+    return (f"3D incompressible NS {n}^3 " + ("FP32 with the x-line transforms on the tensor cores" if tc else "FP32")
+            + ", random-phase solenoidal IC E(k)~k^4 exp(-2(k/4)^2), E=0.5, seed 0, "
             "nu=2e-3, dt=1e-3, Lawson IF-RK4, 2/3 dealiasing")
-L2_NOTE = "inputs larger than L2: state 0.49 GB, pass buffers 3.6 GB vs 129 MB L2 (no flush needed)"
+
+
+def l2_note(n=None, elem=8):
+    """State and pass-buffer sizes of the n^3 run against the 129 MB L2."""
+    n = N_GRID if n is None else n
+    kc = (n - 1) // 3
+    c, h = 2 * kc + 1, kc + 1
+    hs = -(-h * elem // 128) * 128 // elem
+    state = 3 * c * c * hs * elem / 1e9
+    bufs = (6 * n * c * hs + 6 * n * n * hs) * elem / 1e9
+    return (f"inputs larger than L2: state {state:.2f} GB, pass buffers {bufs:.1f} GB vs 129 MB L2 "
+            "(no flush needed)")
 # Algorithmic bytes of one 512^3 FP32 step for the fused three-phase model
 # (truncated spectrum, middle-axis passes counted once): 252.8 B/point.
 MODEL_BYTES_PER_POINT = 252.8
@@ -390,11 +410,11 @@ def run_reference(args):
     v = n ** 3 * timed / t / 1e6
     sample = (f"{timed} of the {args.steps} requested Lawson IF-RK4 steps of the bench workload at {n}^3 in FP64 "
               f"timed after {warm} warm-up step(s) (time-bounded at {REF_BUDGET_S:.0f} s)")
-    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+    line = {"impl": "reference", "metric": metric_name(n), "value": v, "unit": UNIT, "n_gpus": args.gpus,
             "steps": timed, "warmup": warm, "requested_steps": args.steps, "requested_warmup": args.warmup,
             "ms_per_step": t / timed * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "n": n, "l2": L2_NOTE},
+            "config": {"workload": workload(n), "n": n, "l2": l2_note(n)},
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -494,13 +514,14 @@ def run_gb300(args):
         value = job_value(ws, pts, args.steps, ms_max)
         step_bytes = MODEL_BYTES_PER_POINT * pts
         line = {
-            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "metric": metric_name(tc=args.precision == "tc"), "value": value, "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps,
             "warmup": max(args.warmup, 3), "ms_per_step": ms_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32" if prec == ns.NS_FP32 else "f32+bf16x3",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD, "n": N_GRID, "precision": args.precision,
+            "config": {"workload": workload(tc=args.precision == "tc"), "n": N_GRID, "precision": args.precision,
                        "parallelism": f"replicas x{ws}",
-                       "l2": L2_NOTE, "job_steps": JOB_STEPS},
+                       "l2": l2_note(), "job_steps": JOB_STEPS},
             "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm, "peak_kind": peak_kind,
                          "unit": "GB/s", "frac": achieved / hbm, "traffic": traffic,
                          "algorithmic_bytes_per_launch": dom_bytes, "avg_launch_ms": dom_avg_s * 1e3},

@@ -863,6 +863,24 @@ __device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *tm, in
       : "memory");
 }
 
+// the same boxes into L2 only (no shared memory, no barrier)
+__device__ __forceinline__ void tma_prefetch_2d(const CUtensorMap *tm, int x, int y) {
+  asm volatile("cp.async.bulk.prefetch.tensor.2d.L2.global.tile [%0, {%1, %2}];\n" ::"l"(
+                   reinterpret_cast<unsigned long long>(tm)),
+               "r"(x), "r"(y)
+               : "memory");
+}
+__device__ __forceinline__ void tma_prefetch_3d(const CUtensorMap *tm, int x, int y, int z) {
+  asm volatile("cp.async.bulk.prefetch.tensor.3d.L2.global.tile [%0, {%1, %2, %3}];\n" ::"l"(
+                   reinterpret_cast<unsigned long long>(tm)),
+               "r"(x), "r"(y), "r"(z)
+               : "memory");
+}
+// Linear index of the block launched `ahead` blocks after this one, or -1.
+__device__ __forceinline__ long long block_ahead(int ahead) {
+  const long long nb = (long long)blockIdx.y * gridDim.x + blockIdx.x + ahead;
+  return (ahead > 0 && nb < (long long)gridDim.x * gridDim.y) ? nb : -1;
+}
 
 // inv2 with TMA loads: the same arithmetic as k3_inv2.  Field f's input
 // column tile (the c retained ky rows of plane (f, z), W columns) lands in a
@@ -877,10 +895,16 @@ __device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *tm, in
 // u_x, u_z, omega_y and tile B u_y, omega_x, each refilled as soon as every
 // thread has read it.  The same values and operations as a stored omega_z,
 // so the results are bit for bit those of the six-field form.
+//
+// pf = 8 ahead + at (0: off): while item `at` is transformed, thread 0 sends
+// the first tile(s) of the block launched `ahead` blocks later (one wave on,
+// the block likely to follow on this SM) to L2, so that block's first wait
+// ends on an L2 hit.
 template <typename R, int N, int W, bool WZ = false>
 __global__ void __launch_bounds__((N / 8) * W) k3_inv2_tma(Geo g, int nf, int z0, const __grid_constant__ CUtensorMap tm,
                                                             typename CplxOf<R>::T *__restrict__ yb,
-                                                            const typename CplxOf<R>::T *__restrict__ tw, int *err) {
+                                                            const typename CplxOf<R>::T *__restrict__ tw, int *err,
+                                                            int pf = 0) {
   using C = typename CplxOf<R>::T;
   constexpr int T = N / 8;
   constexpr int P = pitch_of(W, sizeof(C));
@@ -904,6 +928,18 @@ __global__ void __launch_bounds__((N / 8) * W) k3_inv2_tma(Geo g, int nf, int z0
 #pragma unroll
     for (int b = 0; b < NBOX; ++b)
       tma_load_3d(land + (q * LROWS + b * BOXR) * W, &tm, x8, b * BOXR, f * N + z, bar + q);
+  };
+  // pf = 8 ahead + at: at item `at`, the first field(s) of the block launched
+  // `ahead` blocks later go to L2
+  auto prefetch_ahead = [&](int item) {
+    if (threadIdx.x != 0 || pf < 8 || item != (pf & 7)) return;
+    const long long nb = block_ahead(pf >> 3);
+    if (nb < 0) return;
+    const int bx = (int)(nb % gridDim.x), zz = z0 + (int)(nb / gridDim.x);
+#pragma unroll
+    for (int f = 0; f < (WZ ? 2 : 1); ++f)
+#pragma unroll
+      for (int b = 0; b < NBOX; ++b) tma_prefetch_3d(&tm, bx * W * (int)(sizeof(C) / 8), b * BOXR, f * N + zz);
   };
   int row[8];
   bool live[8];
@@ -952,6 +988,7 @@ __global__ void __launch_bounds__((N / 8) * W) k3_inv2_tma(Geo g, int nf, int z0
         fence_proxy_async_smem();
         issue(0, f + 1);
       }
+      prefetch_ahead(f);
       transform_store(v, f);
     }
   } else {
@@ -967,11 +1004,13 @@ __global__ void __launch_bounds__((N / 8) * W) k3_inv2_tma(Geo g, int nf, int z0
     if (!landed(0, 0)) return;
 #pragma unroll
     for (int m = 0; m < 8; ++m) v[m] = live[m] ? la[row[m] * W + w] : czero<C>();
+    prefetch_ahead(0);
     transform_store(v, 0);
     // u_y (tile B stays)
     if (!landed(1, 0)) return;
 #pragma unroll
     for (int m = 0; m < 8; ++m) v[m] = live[m] ? lb[row[m] * W + w] : czero<C>();
+    prefetch_ahead(1);
     transform_store(v, 1);
     // omega_z = i (kx u_y - ky u_x); then both tiles are refilled
     {
@@ -992,6 +1031,7 @@ __global__ void __launch_bounds__((N / 8) * W) k3_inv2_tma(Geo g, int nf, int z0
         issue(0, 2);  // u_z
         issue(1, 3);  // omega_x
       }
+      prefetch_ahead(2);
       transform_store(v, 5);
     }
     // u_z from tile A, which then takes omega_y
@@ -1003,16 +1043,19 @@ __global__ void __launch_bounds__((N / 8) * W) k3_inv2_tma(Geo g, int nf, int z0
       fence_proxy_async_smem();
       issue(0, 4);
     }
+    prefetch_ahead(3);
     transform_store(v, 2);
     // omega_x from tile B
     if (!landed(1, 1)) return;
 #pragma unroll
     for (int m = 0; m < 8; ++m) v[m] = live[m] ? lb[row[m] * W + w] : czero<C>();
+    prefetch_ahead(4);
     transform_store(v, 3);
     // omega_y from tile A
     if (!landed(0, 0)) return;
 #pragma unroll
     for (int m = 0; m < 8; ++m) v[m] = live[m] ? la[row[m] * W + w] : czero<C>();
+    prefetch_ahead(5);
     transform_store(v, 4);
   }
 }
@@ -1022,11 +1065,13 @@ __global__ void __launch_bounds__((N / 8) * W) k3_inv2_tma(Geo g, int nf, int z0
 // of 8-byte elements) lands in a dense [N][W] shared tile, issued by thread 0
 // one field ahead (boxes of at most 256 rows); thread 0 waits for it (bounded),
 // the block barrier hands it to every thread, and each thread reads its eight
-// values t + T m of column w from the tile.
+// values t + T m of column w from the tile.  pf: as in k3_inv2_tma, field 0
+// of the block one wave later goes to L2 while field `at` is transformed.
 template <typename R, int N, int W>
 __global__ void __launch_bounds__((N / 8) * W) k3_fwd2_tma(Geo g, int nf, int z0, const __grid_constant__ CUtensorMap tm,
                                                             typename CplxOf<R>::T *__restrict__ zb,
-                                                            const typename CplxOf<R>::T *__restrict__ tw, int *err) {
+                                                            const typename CplxOf<R>::T *__restrict__ tw, int *err,
+                                                            int pf = 0) {
   using C = typename CplxOf<R>::T;
   constexpr int T = N / 8;
   constexpr int P = pitch_of(W, sizeof(C));
@@ -1073,6 +1118,15 @@ __global__ void __launch_bounds__((N / 8) * W) k3_fwd2_tma(Geo g, int nf, int z0
     if (threadIdx.x == 0 && f + 1 < nf) {
       fence_proxy_async_smem();
       issue(f + 1);
+    }
+    // pf = 8 ahead + at: at field `at`, field 0 of the block launched `ahead`
+    // blocks later goes to L2
+    if (threadIdx.x == 0 && pf >= 8 && f == (pf & 7)) {
+      const long long nb = block_ahead(pf >> 3);
+      if (nb >= 0) {
+        const int row0 = (z0 + (int)(nb / gridDim.x)) * N;
+        for (int r = 0; r < N; r += BOXR) tma_prefetch_2d(&tm, (int)(nb % gridDim.x) * W * (int)(sizeof(C) / 8), row0 + r);
+      }
     }
     fft_line<N, -1>(v, t, tw + N, SmCol<C, DB>{sm + w, P, N * P});
     if (valid) {
@@ -1386,7 +1440,13 @@ template <typename R, int N, int W>
 __host__ __device__ constexpr size_t fwd1t_smem() {
   return col_tile_bytes(N, W, 2 * sizeof(R)) + (size_t)3 * trunc_rows(N) * W * 2 * sizeof(R);
 }
-template <typename R, int N, int W, int MODE, bool INV, bool PF = false, int UR = 1, int MINB = 2>
+__device__ __forceinline__ void prefetch_l2(const void *p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
+
+// PFR >= 0: the tile's RK operand rows are prefetched into L2 while phase 1
+// transforms field PFR; PFN >= 0: the next tile's three input columns while
+// phase 3 transforms field PFN (a prefetch ahead of its loads, not a copy).
+template <typename R, int N, int W, int MODE, bool INV, bool PF = false, int UR = 1, int MINB = 2, int PFR = -1,
+          int PFN = -1>
 __global__ void __launch_bounds__((N / 8) * W, MINB) k3_fwd1t(Geo g, StepBufs<R> b) {
   using C = typename CplxOf<R>::T;
   constexpr int T = N / 8;
@@ -1419,6 +1479,19 @@ __global__ void __launch_bounds__((N / 8) * W, MINB) k3_fwd1t(Geo g, StepBufs<R>
 #pragma unroll 1
     for (int f = 0; f < 3; ++f) {
       C v[8];
+      if (f == PFR) {  // the W-column row segments of u, acc and F this tile's phase 2 reads
+        const long long col0 = (long long)iy * g.hs + (tile % nkt) * W;
+        const C *fo = MODE != MODE_PROJ ? b.F : nullptr;  // operands in order, null ones last
+        const C *op0 = NEED_U ? b.u : (NEED_ACC ? b.acc : fo);
+        const C *op1 = NEED_U && NEED_ACC ? b.acc : (NEED_U || NEED_ACC ? fo : nullptr);
+        const C *op2 = NEED_U && NEED_ACC ? fo : nullptr;
+        const int no = (op0 != nullptr) + (op1 != nullptr) + (op2 != nullptr);
+        for (int i = threadIdx.x; i < 3 * no * CR; i += blockDim.x) {
+          const int o = i / CR, r = i % CR;
+          const C *op = o < 3 ? op0 : (o < 6 ? op1 : op2);
+          prefetch_l2(op + (o % 3) * st + (long long)r * plane + col0);
+        }
+      }
       if (PF) {
 #pragma unroll
         for (int m = 0; m < 8; ++m) v[m] = xn[m];
@@ -1505,6 +1578,12 @@ __global__ void __launch_bounds__((N / 8) * W, MINB) k3_fwd1t(Geo g, StepBufs<R>
 #pragma unroll 1
       for (int f = 0; f < 5; ++f) {
         C v[8];
+        if (f == PFN && tile + (int)gridDim.x < ntiles) {
+          const int nt = tile + gridDim.x;
+          const long long col0 = (long long)(nt / nkt) * g.hs + (nt % nkt) * W;
+          for (int i = threadIdx.x; i < 3 * N; i += blockDim.x)
+            prefetch_l2(b.zb + (i / N) * g.zb_f + (long long)(i % N) * plane + col0);
+        }
 #pragma unroll
         for (int m = 0; m < 8; ++m) {
           const int n = t + T * m;
@@ -1833,31 +1912,31 @@ inline StepBufs<R> step_bufs(const Args &a) {
 
 // fwd1 with the shared spectral tile in a given shape: W columns, next-field
 // prefetch PF, UR rows of RK operands in flight, MINB resident blocks per SM
-template <typename R, int N, int W, bool PF, int UR, int MINB>
+template <typename R, int N, int W, bool PF, int UR, int MINB, int PFR = -1, int PFN = -1>
 struct Fwd1T {
   static constexpr size_t SM = fwd1t_smem<R, N, W>();
   static void prepare() {
-    set_smem(k3_fwd1t<R, N, W, MODE_RK1, true, PF, UR, MINB>, SM);
-    set_smem(k3_fwd1t<R, N, W, MODE_RK2, true, PF, UR, MINB>, SM);
-    set_smem(k3_fwd1t<R, N, W, MODE_RK3, true, PF, UR, MINB>, SM);
-    set_smem(k3_fwd1t<R, N, W, MODE_RK4, true, PF, UR, MINB>, SM);
-    set_smem(k3_fwd1t<R, N, W, MODE_RHS, false, PF, UR, MINB>, SM);
-    set_smem(k3_fwd1t<R, N, W, MODE_PROJ, false, PF, UR, MINB>, SM);
-    set_smem(k3_fwd1t<R, N, W, MODE_M1, true, PF, UR, MINB>, SM);
-    set_smem(k3_fwd1t<R, N, W, MODE_M2, true, PF, UR, MINB>, SM);
+    set_smem(k3_fwd1t<R, N, W, MODE_RK1, true, PF, UR, MINB, PFR, PFN>, SM);
+    set_smem(k3_fwd1t<R, N, W, MODE_RK2, true, PF, UR, MINB, PFR, PFN>, SM);
+    set_smem(k3_fwd1t<R, N, W, MODE_RK3, true, PF, UR, MINB, PFR, PFN>, SM);
+    set_smem(k3_fwd1t<R, N, W, MODE_RK4, true, PF, UR, MINB, PFR, PFN>, SM);
+    set_smem(k3_fwd1t<R, N, W, MODE_RHS, false, PF, UR, MINB, PFR, PFN>, SM);
+    set_smem(k3_fwd1t<R, N, W, MODE_PROJ, false, PF, UR, MINB, PFR, PFN>, SM);
+    set_smem(k3_fwd1t<R, N, W, MODE_M1, true, PF, UR, MINB, PFR, PFN>, SM);
+    set_smem(k3_fwd1t<R, N, W, MODE_M2, true, PF, UR, MINB, PFR, PFN>, SM);
   }
   static void launch(int mode, int nsm, const Geo &g, const StepBufs<R> &b, cudaStream_t s) {
     const int tiles = g.c * (g.hs / W), grid = cmin(tiles, MINB * (nsm > 0 ? nsm : 1));
     constexpr int NT = (N / 8) * W;
     switch (mode) {
-      case MODE_RK1: k3_fwd1t<R, N, W, MODE_RK1, true, PF, UR, MINB><<<grid, NT, SM, s>>>(g, b); break;
-      case MODE_RK2: k3_fwd1t<R, N, W, MODE_RK2, true, PF, UR, MINB><<<grid, NT, SM, s>>>(g, b); break;
-      case MODE_RK3: k3_fwd1t<R, N, W, MODE_RK3, true, PF, UR, MINB><<<grid, NT, SM, s>>>(g, b); break;
-      case MODE_RK4: k3_fwd1t<R, N, W, MODE_RK4, true, PF, UR, MINB><<<grid, NT, SM, s>>>(g, b); break;
-      case MODE_RHS: k3_fwd1t<R, N, W, MODE_RHS, false, PF, UR, MINB><<<grid, NT, SM, s>>>(g, b); break;
-      case MODE_M1: k3_fwd1t<R, N, W, MODE_M1, true, PF, UR, MINB><<<grid, NT, SM, s>>>(g, b); break;
-      case MODE_M2: k3_fwd1t<R, N, W, MODE_M2, true, PF, UR, MINB><<<grid, NT, SM, s>>>(g, b); break;
-      default: k3_fwd1t<R, N, W, MODE_PROJ, false, PF, UR, MINB><<<grid, NT, SM, s>>>(g, b); break;
+      case MODE_RK1: k3_fwd1t<R, N, W, MODE_RK1, true, PF, UR, MINB, PFR, PFN><<<grid, NT, SM, s>>>(g, b); break;
+      case MODE_RK2: k3_fwd1t<R, N, W, MODE_RK2, true, PF, UR, MINB, PFR, PFN><<<grid, NT, SM, s>>>(g, b); break;
+      case MODE_RK3: k3_fwd1t<R, N, W, MODE_RK3, true, PF, UR, MINB, PFR, PFN><<<grid, NT, SM, s>>>(g, b); break;
+      case MODE_RK4: k3_fwd1t<R, N, W, MODE_RK4, true, PF, UR, MINB, PFR, PFN><<<grid, NT, SM, s>>>(g, b); break;
+      case MODE_RHS: k3_fwd1t<R, N, W, MODE_RHS, false, PF, UR, MINB, PFR, PFN><<<grid, NT, SM, s>>>(g, b); break;
+      case MODE_M1: k3_fwd1t<R, N, W, MODE_M1, true, PF, UR, MINB, PFR, PFN><<<grid, NT, SM, s>>>(g, b); break;
+      case MODE_M2: k3_fwd1t<R, N, W, MODE_M2, true, PF, UR, MINB, PFR, PFN><<<grid, NT, SM, s>>>(g, b); break;
+      default: k3_fwd1t<R, N, W, MODE_PROJ, false, PF, UR, MINB, PFR, PFN><<<grid, NT, SM, s>>>(g, b); break;
     }
   }
 };
@@ -1866,9 +1945,19 @@ struct Fwd1T {
 // per SM (fwd1 1.146 -> 1.034 ms per launch against the register-resident
 // form); 256 points: 512 threads, two blocks per SM (0.154 -> 0.148 ms;
 // 32 columns: 0.164 ms); 1024 points: 8 columns, 1024 threads, one block per
-// SM (exchange tile 74 KB + spectral tile 131 KB).
+// SM (exchange tile 74 KB + spectral tile 131 KB).  L2 prefetches (256 and
+// 512 points): the RK operands while the last input field is transformed, the
+// next tile's inputs while the fourth of the five inverse transforms runs
+// (512 points: 0.980 -> 0.937 ms; the RK operands one field earlier 0.952, the
+// next tile one field later 0.966, either one alone 0.960 / 0.963; at 1024
+// points, with half-line rows, 14.51 -> 15.04 ms, so none there).
 template <typename R, int N>
-using Fwd1Pick = Fwd1T<R, N, (N == 1024 ? 8 : 16), true, 2, (N == 256 ? 2 : 1)>;
+using Fwd1Pick = Fwd1T<R, N, (N == 1024 ? 8 : 16), true, 2, (N == 256 ? 2 : 1), (N == 1024 ? -1 : 2),
+                       (N == 1024 ? -1 : 3)>;
+
+// Prefetch argument of the TMA y passes (see k3_inv2_tma): the block one
+// wave later (SMs x resident blocks per SM), at item `at` of this block.
+inline int wave_pf(int nsm, int per_sm, int at) { return 8 * (nsm > 0 ? nsm : 1) * (per_sm > 0 ? per_sm : 1) + at; }
 
 template <typename R, int N>
 struct Launch3 {
@@ -1892,6 +1981,8 @@ struct Launch3 {
   static constexpr size_t SM_YIW = col_smem(
       N, WYI, sizeof(C), 2 * (size_t)tma_boxes(trunc_rows(N)) * tma_box_rows(trunc_rows(N)) * WYI * sizeof(C) + 32);
   static constexpr bool YI_WZ = YI_TMA && sizeof(R) == 4 && (N == 256 || N == 512);
+  // resident blocks per SM of the TMA y passes (their L2 prefetch looks one wave ahead)
+  static inline int occ_yi = 1, occ_yiw = 1, occ_yf = 1;
   static_assert(!YI_WZ || SM_YIW <= kSmemMax, "inv2 with two landing tiles");
   // persistent fwd1: exchange tile + RK operand slots (3 comps x 6 per thread
   // for each operand: two for RK2/RK3, one for the other stages; the smaller
@@ -1926,10 +2017,19 @@ struct Launch3 {
         set_smem(k3_inv1<R, N, WL, true>, SM_L);
         set_smem(k3_inv1<R, N, WL, false>, SM_L);
         set_smem(k3_inv2<R, N, WYI>, SM_YI);
-        if constexpr (YI_TMA) set_smem(k3_inv2_tma<R, N, WYI>, SM_YIT);
-        if constexpr (YI_WZ) set_smem(k3_inv2_tma<R, N, WYI, true>, SM_YIW);
+        if constexpr (YI_TMA) {
+          set_smem(k3_inv2_tma<R, N, WYI>, SM_YIT);
+          cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_yi, k3_inv2_tma<R, N, WYI>, T * WYI, SM_YIT);
+        }
+        if constexpr (YI_WZ) {
+          set_smem(k3_inv2_tma<R, N, WYI, true>, SM_YIW);
+          cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_yiw, k3_inv2_tma<R, N, WYI, true>, T * WYI, SM_YIW);
+        }
         set_smem(k3_fwd2<R, N, WYF>, SM_YF);
-        if constexpr (YF_TMA) set_smem(k3_fwd2_tma<R, N, WYF>, SM_YFT);
+        if constexpr (YF_TMA) {
+          set_smem(k3_fwd2_tma<R, N, WYF>, SM_YFT);
+          cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_yf, k3_fwd2_tma<R, N, WYF>, T * WYF, SM_YFT);
+        }
         if constexpr (!XW) set_smem(k3_xpass<R, N, L>, SM_XP);
         set_smem(k_xfwd_real<R, N, L>, SM_X);
         set_smem(k_xinv_real<R, N, L>, SM_X);
@@ -1960,7 +2060,8 @@ struct Launch3 {
           if constexpr (YI_WZ) {
             if (a.tmap_zb != nullptr && a.nf == 6) {
               k3_inv2_tma<R, N, WYI, true><<<dim3(g.hs / WYI, nz), T * WYI, SM_YIW, s>>>(
-                  g, a.nf, a.z0, *reinterpret_cast<const CUtensorMap *>(a.tmap_zb), (C *)a.yb, tw, a.err);
+                  g, a.nf, a.z0, *reinterpret_cast<const CUtensorMap *>(a.tmap_zb), (C *)a.yb, tw, a.err,
+                  wave_pf(a.nsm, occ_yiw, 4));
               break;
             }
           }
@@ -1969,7 +2070,8 @@ struct Launch3 {
         if constexpr (YI_TMA) {
           if (a.tmap_zb != nullptr) {
             k3_inv2_tma<R, N, WYI><<<dim3(g.hs / WYI, nz), T * WYI, SM_YIT, s>>>(
-                g, a.nf, a.z0, *reinterpret_cast<const CUtensorMap *>(a.tmap_zb), (C *)a.yb, tw, a.err);
+                g, a.nf, a.z0, *reinterpret_cast<const CUtensorMap *>(a.tmap_zb), (C *)a.yb, tw, a.err,
+                wave_pf(a.nsm, occ_yi, a.nf > 4 ? 4 : a.nf - 1));
             break;
           }
         }
@@ -1996,7 +2098,8 @@ struct Launch3 {
         if constexpr (YF_TMA) {
           if (a.tmap_yb != nullptr) {
             k3_fwd2_tma<R, N, WYF><<<dim3(g.hs / WYF, nz), T * WYF, SM_YFT, s>>>(
-                g, a.nf, a.z0, *reinterpret_cast<const CUtensorMap *>(a.tmap_yb), (C *)a.zb, tw, a.err);
+                g, a.nf, a.z0, *reinterpret_cast<const CUtensorMap *>(a.tmap_yb), (C *)a.zb, tw, a.err,
+                wave_pf(a.nsm, occ_yf, a.nf > 2 ? 2 : a.nf - 1));
             break;
           }
         }
