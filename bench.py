@@ -440,9 +440,6 @@ def run_gb300(args):
 
     from paper_1807_01769_gb300 import inputs, ns
 
-    # cpu baseline first, before any GPU work (oracle threads, rank 0 only)
-    cpu = cpu_baseline() if (rank == 0 and ws == 1 and not args.no_cpu_baseline) else None
-
     u0 = inputs.random_velocity_3d(N_GRID, seed=0, k0=4.0, a=2.0, energy=0.5)
     prec = ns.NS_FP32_TC if args.precision == "tc" else ns.NS_FP32
     s = ns.Solver(3, N_GRID, prec, nu=NU, dt=DT)
@@ -540,8 +537,6 @@ def run_gb300(args):
             "gpu_launches": launches_per_step * args.steps,
             "energy_after": e, "enstrophy_after": om,
         }
-        if cpu is not None:
-            line["cpu_baseline"] = cpu
         if ws == 1 and not args.no_err:
             line["err_vs_fp64"] = err_vs_fp64()
         if ws == 1 and not args.no_ensemble:
@@ -553,6 +548,11 @@ def run_gb300(args):
                 line["tensor_core"] = tensor_core_bench(u0)
             except Exception as exc:  # noqa: BLE001
                 line["tensor_core"] = {"precision": "NS_FP32_TC", "error": f"{type(exc).__name__}: {exc}"}
+        # the oracle last, after every GPU measurement: its 25 GB of host
+        # memory, freed just before, slowed the pinned copies of the
+        # end-to-end jobs that followed it (uploads 4.8 -> ~40 ms)
+        if ws == 1 and not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline()
         print(json.dumps(line), flush=True)
     s.close()
     if ws > 1:
@@ -566,7 +566,7 @@ def main():
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--e2e-reps", type=int, default=2)
+    ap.add_argument("--e2e-reps", type=int, default=4)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-ensemble", action="store_true", help="skip the batched 2D ensemble measurement")
     ap.add_argument("--no-paper-shapes", action="store_true", help="skip the paper-grid measurements")

@@ -109,7 +109,11 @@ int ns_get_state(ns_state *s, double *phys_host);
 /* Set / get the state in the canonical truncated spectral layout (host
  * complex128 as double pairs).  Set rounds to the state precision.  The caller
  * supplies a Hermitian-consistent kx = 0 plane (u(0,-ky,-kz) = conj u(0,ky,kz));
- * the inverse transforms use the real part of self-conjugate sums.  Synchronise. */
+ * the inverse transforms use the real part of self-conjugate sums.  Synchronise.
+ * The buffer holds the whole state (state_doubles of ns_sizes).  A page-locked
+ * buffer the device can address (cudaHostAlloc, cudaHostRegister) is read or
+ * written in place by the conversion kernel over the host link; a pageable one
+ * goes through a device staging buffer.  Either way the same values. */
 int ns_set_state_spectral(ns_state *s, const double *spec_host);
 int ns_get_state_spectral(ns_state *s, double *spec_host);
 

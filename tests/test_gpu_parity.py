@@ -376,3 +376,26 @@ def test_rhs_512_band_limited_equals_oracle_64(ns, orc):
         s.set_state_spectral(embed(u_small, m, n))
         got = s.eval_rhs()
     assert rel_l2(low_modes(got, n, m), ref) < TOL_RHS[FP32]
+
+
+# ------------------------------------------------ pinned host buffers ---
+@pytest.mark.parametrize("dim,n,prec", [(3, 64, FP32), (3, 32, FP64), (2, 128, FP32), (2, 64, FP64)])
+def test_pinned_host_buffers_equal_pageable_ones(ns, dim, n, prec):
+    """A page-locked host buffer is converted in place over the host link, a
+    pageable one through device staging: the same state either way, bit for
+    bit, on the way in and on the way out, before and after steps."""
+    torch = pytest.importorskip("torch")
+    u0 = ic(dim, n, seed=3)
+    h_in = torch.from_numpy(np.ascontiguousarray(u0).view(np.float64).reshape(-1)).pin_memory()
+    with ns.Solver(dim, n, prec, nu=1e-3, dt=1e-3) as a, ns.Solver(dim, n, prec, nu=1e-3, dt=1e-3) as b:
+        a.set_state_spectral(u0)
+        b.set_state_spectral_ptr(h_in.data_ptr())
+        for steps in (0, 3):
+            a.step(steps)
+            b.step(steps)
+            h_out = torch.zeros(b.sizes["state_doubles"], dtype=torch.float64).pin_memory()
+            b.get_state_spectral_ptr(h_out.data_ptr())
+            pinned = h_out.numpy().view(np.complex128).reshape(a.spec_shape)
+            pageable = a.get_state_spectral()
+            assert np.array_equal(pinned, pageable)
+            assert np.array_equal(b.get_state_spectral(), pageable)
