@@ -100,10 +100,13 @@ int ns_sizes(const ns_grid *grid, int *kc, int *c, int *h, long long *state_doub
 int ns_init(ns_state **out, const ns_grid *grid, double nu, double dt, const double *forcing_phys);
 
 /* Set the state from a host physical field (velocity in 3D, vorticity in 2D):
- * FFT, dealias, project (3D), zero mean.  Synchronises. */
+ * FFT, dealias, project (3D), zero mean.  Synchronises.  The buffer holds
+ * phys_doubles (ns_sizes); a page-locked one the device can address is read
+ * in place by the first transform, a pageable one through device staging. */
 int ns_set_state(ns_state *s, const double *phys_host);
 
-/* Write the state to a host physical field (inverse FFT).  Synchronises. */
+/* Write the state to a host physical field (inverse FFT).  Synchronises.  A
+ * page-locked buffer is written in place by the last transform. */
 int ns_get_state(ns_state *s, double *phys_host);
 
 /* Set / get the state in the canonical truncated spectral layout (host

@@ -316,15 +316,32 @@ long long state_rows(const ns_state *s) {
   return s->grid.dim == 3 ? c * c : c;
 }
 
+// The device address of a host buffer the GPU reads and writes directly
+// (page-locked and mapped: cudaHostAlloc, cudaHostRegister, pinned torch
+// tensors), else null.  Such buffers are converted in place over the host
+// link instead of being staged through device memory (512^3 job: read-backs
+// 4.96 ms every time, against 5.2-19.6 ms through the staging copy, which
+// slowed down in every other job).
+static void *mapped_view(const void *host) {
+  cudaPointerAttributes a{};
+  if (cudaPointerGetAttributes(&a, host) != cudaSuccess) {
+    cudaGetLastError();  // not a CUDA-known pointer: clear the error, stage it
+    return nullptr;
+  }
+  return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+
 // host physical field(s) -> truncated spectrum in dst (PROJ mode: dealias,
 // normalise, project in 3D, zero mean)
 int phys_to_spec(ns_state *s, const double *host, void *dst) {
   const long long np = phys_elems(s);
   Args a = base_args(s);
+  const double *dv = static_cast<const double *>(mapped_view(host));
   for (int c = 0; c < s->ncomp; ++c) {
-    NS_CK(s, cudaMemcpyAsync(s->staging, host + c * np, np * sizeof(double), cudaMemcpyHostToDevice, s->stream));
+    if (!dv)
+      NS_CK(s, cudaMemcpyAsync(s->staging, host + c * np, np * sizeof(double), cudaMemcpyHostToDevice, s->stream));
     Args x = a;
-    x.phys_in = (const double *)s->staging;
+    x.phys_in = dv ? dv + c * np : (const double *)s->staging;
     x.field = c;
     int rc = dispatch(s, nsk::OP_XFWD_REAL, x, s->stream);
     if (rc) return rc;
@@ -640,31 +657,19 @@ int ns_get_state(ns_state *s, double *phys_host) {
     if ((rc = dispatch(s, nsk::OP_INV2, b, s->stream))) return rc;
   }
   const long long np = phys_elems(s);
+  double *dv = static_cast<double *>(mapped_view(phys_host));
   for (int c = 0; c < s->ncomp; ++c) {
     Args x = base_args(s);
-    x.phys_out = (double *)s->staging;
+    x.phys_out = dv ? dv + c * np : (double *)s->staging;
     x.field = c;
     if ((rc = dispatch(s, nsk::OP_XINV_REAL, x, s->stream))) return rc;
-    NS_CK(s, cudaMemcpyAsync(phys_host + c * np, s->staging, np * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+    if (!dv)
+      NS_CK(s, cudaMemcpyAsync(phys_host + c * np, s->staging, np * sizeof(double), cudaMemcpyDeviceToHost,
+                               s->stream));
   }
   s->zvalid = false;
   NS_CK(s, cudaStreamSynchronize(s->stream));
   return NS_OK;
-}
-
-// The device address of a host buffer the GPU reads and writes directly
-// (page-locked and mapped: cudaHostAlloc, cudaHostRegister, pinned torch
-// tensors), else null.  Such buffers are converted in place over the host
-// link instead of being staged through device memory (512^3 job: read-backs
-// 4.96 ms every time, against 5.2-19.6 ms through the staging copy, which
-// slowed down in every other job).
-static void *mapped_view(const void *host) {
-  cudaPointerAttributes a{};
-  if (cudaPointerGetAttributes(&a, host) != cudaSuccess) {
-    cudaGetLastError();  // not a CUDA-known pointer: clear the error, stage it
-    return nullptr;
-  }
-  return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
 }
 
 int ns_set_state_spectral(ns_state *s, const double *spec_host) {

@@ -399,3 +399,12 @@ def test_pinned_host_buffers_equal_pageable_ones(ns, dim, n, prec):
             pageable = a.get_state_spectral()
             assert np.array_equal(pinned, pageable)
             assert np.array_equal(b.get_state_spectral(), pageable)
+        # physical fields: in place from a pinned buffer, staged from a pageable one
+        phys = a.get_state()
+        p_out = torch.zeros(phys.size, dtype=torch.float64).pin_memory()
+        ns._check(ns.lib.ns_get_state(b.state, ns.ctypes.c_void_p(p_out.data_ptr())), b.state)
+        assert np.array_equal(p_out.numpy().reshape(phys.shape), phys)
+        p_in = torch.from_numpy(np.ascontiguousarray(phys).reshape(-1)).pin_memory()
+        a.set_state(phys)
+        ns._check(ns.lib.ns_set_state(b.state, ns.ctypes.c_void_p(p_in.data_ptr())), b.state)
+        assert np.array_equal(a.get_state_spectral(), b.get_state_spectral())
