@@ -67,6 +67,19 @@ def l2_note(n=None, elem=8):
 # Algorithmic bytes of one 512^3 FP32 step for the fused three-phase model
 # (truncated spectrum, middle-axis passes counted once): 252.8 B/point.
 MODEL_BYTES_PER_POINT = 252.8
+
+
+def flop_model(n):
+    """Dense-FFT flop counts (2.5 n log2 n per real transform of length n):
+    per point of a step, nine real 3D transforms per RK stage, four stages;
+    per x-pass launch, nine real x-line transforms per (z, y) line plus the
+    cross product (9 flops per point)."""
+    import math
+
+    lg = math.log2(n)
+    return 4 * 9 * 2.5 * 3 * lg, n * n * (9 * 2.5 * n * lg + 9 * n)
+
+
 # wall-clock bound of the reference arm's timed oracle steps (seconds)
 REF_BUDGET_S = 90.0
 
@@ -176,6 +189,21 @@ def traffic_from_profiles(kernel: str):
         if kv.get("kernel") == kernel and kv.get("n") == str(N_GRID) and kv.get("source_sha") == digest:
             return int(kv["dram_bytes_per_launch"])
     return None
+
+
+def flops_entry(ms_step, prof, fma_peak):
+    """Flop efficiency beside the HBM roofline: the dense-FFT model against the
+    measured FP32 FMA rate of the GPU."""
+    per_pt, xpass_flops = flop_model(N_GRID)
+    step_tf = per_pt * N_GRID ** 3 / (ms_step / 1e3) / 1e12
+    out = {"model_flop_per_point": per_pt, "achieved_tflops": step_tf, "peak_tflops": fma_peak,
+           "peak_kind": "measured FP32 FMA rate (ns_fp32_fma_peak)", "frac": step_tf / fma_peak,
+           "note": "dense-FFT count, 2.5 n log2 n per real transform; the pruned transforms do fewer"}
+    if "xpass" in prof and prof["xpass"][1] > 0:
+        xs = prof["xpass"][0] / prof["xpass"][1] / 1e3
+        out["xpass_tflops"] = xpass_flops / xs / 1e12
+        out["xpass_frac"] = out["xpass_tflops"] / fma_peak
+    return out
 
 
 def cpu_baseline(n=None, steps=1):
@@ -481,6 +509,7 @@ def run_gb300(args):
     hbm, peak_kind = peaks()
     achieved = dom_bytes / dom_avg_s / 1e9
     traffic = traffic_from_profiles(dom) if prec == ns.NS_FP32 else None
+    fma_peak = ns.fp32_fma_peak(local)  # TFLOP/s, measured on this GPU
 
     # end to end through the C ABI with pinned host buffers: upload the initial
     # state, advance one job (JOB_STEPS steps), read back state and spectrum
@@ -525,6 +554,7 @@ def run_gb300(args):
             "step_roofline": {"model_bytes_per_point": MODEL_BYTES_PER_POINT,
                               "achieved_gbs": step_bytes / (ms_max / args.steps / 1e3) / 1e9,
                               "frac": step_bytes / (ms_max / args.steps / 1e3) / 1e9 / hbm},
+            "flops": flops_entry(ms_max / args.steps, prof, fma_peak),
             "kernels": {k: {"ms_per_launch": v[0] / v[1], "launches_per_step": v[1] / 3,
                             "algorithmic_gbs": v[2] / (v[0] / v[1] / 1e3) / 1e9}
                         for k, v in prof.items() if v[1] > 0},

@@ -346,6 +346,16 @@ int ns_f32_axpy_f64(const float *src_dev, const double *base_dev, double *dst_de
 #define NS_NOALLOC_SCRATCH_DOUBLES 262144
 int ns_diagnostics_noalloc(const ns_grid *grid, const void *spec_dev, double *out_dev, void *cuda_stream);
 
+/* Measured FP32 fused-multiply-add rate of a device, in TFLOP/s (2 flops per
+ * FMA): every SM runs warps of eight independent FMA chains per thread, timed
+ * with CUDA events after one untimed launch.  It is the denominator of the
+ * flop efficiency reported beside the HBM roofline, since the FFT passes sit
+ * close to the FP32 ALU bound too (the paper's per-task profile, "CFD
+ * pseudo-spectral code comparisons / Tri-dimensional simulations", puts most
+ * of a step in the FFTs).  Runs on its own stream and synchronises; allocates
+ * 4 bytes per launched thread for the chains' results and frees them. */
+int ns_fp32_fma_peak(int device, double *tflops);
+
 /* Release everything the state owns.  Null is ignored. */
 void ns_destroy(ns_state *s);
 

@@ -12,6 +12,7 @@
 // the blocks, then a butterfly).
 #include <climits>
 
+#include "ns.h"
 #include "ns_fft.cuh"
 #include "ns_internal.h"
 
@@ -342,3 +343,61 @@ int budget(int prec, const Geo &g, const void *u, const void *F, double nu, doub
 }
 
 }  // namespace nsk
+
+// Eight independent FMA chains per thread (x <- a x + b with |a| < 1, so the
+// values stay bounded); the sum is stored so the chains are not removed.
+static __global__ void __launch_bounds__(256) k_fma_peak(float *out, int iters, float a, float b) {
+  float x[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) x[j] = (float)(threadIdx.x + j) * 1e-3f;
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int j = 0; j < 8; ++j) x[j] = fmaf(x[j], a, b);
+  }
+  float s = 0.f;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) s += x[j];
+  out[blockIdx.x * (long long)blockDim.x + threadIdx.x] = s;
+}
+
+extern "C" int ns_fp32_fma_peak(int device, double *tflops) {
+  if (!tflops) return NS_EINVAL;
+  *tflops = 0.0;
+  int prev = 0, nsm = 0;
+  if (cudaGetDevice(&prev) != cudaSuccess || cudaSetDevice(device) != cudaSuccess) return NS_ECUDA;
+  int rc = NS_OK;
+  cudaStream_t st = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  float *out = nullptr;
+  const int threads = 256, iters = 1 << 14;
+  do {
+    if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, device) != cudaSuccess || nsm <= 0) {
+      rc = NS_ECUDA;
+      break;
+    }
+    const int blocks = nsm * 8;  // 2048 threads per SM
+    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess ||
+        cudaMalloc(&out, sizeof(float) * (size_t)blocks * threads) != cudaSuccess) {
+      rc = NS_ECUDA;
+      break;
+    }
+    k_fma_peak<<<blocks, threads, 0, st>>>(out, iters, 0.999999f, 1e-7f);  // untimed
+    cudaEventRecord(e0, st);
+    k_fma_peak<<<blocks, threads, 0, st>>>(out, iters, 0.999999f, 1e-7f);
+    cudaEventRecord(e1, st);
+    float ms = 0.f;
+    if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess || ms <= 0.f) {
+      rc = NS_ECUDA;
+      break;
+    }
+    *tflops = 2.0 * 8.0 * iters * (double)blocks * threads / (ms * 1e-3) / 1e12;
+  } while (false);
+  if (out) cudaFree(out);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (st) cudaStreamDestroy(st);
+  cudaGetLastError();
+  cudaSetDevice(prev);
+  return rc;
+}

@@ -61,6 +61,7 @@ SIGNATURES = {
     "ns_kernel_bytes": ([_P, _I], _LL),
     "ns_device_bytes": ([_P], _LL),
     "ns_diagnostics_noalloc": ([ctypes.POINTER(ns_grid), _P, _P, _P], _I),
+    "ns_fp32_fma_peak": ([_I, _PD], _I),
     "ns_destroy": ([_P], None),
     "ns_last_error": ([_P], ctypes.c_char_p),
     "ns_ensemble_init": ([ctypes.POINTER(_P), _I, _P, _I, _D, _D, _I], _I),
@@ -156,6 +157,13 @@ def ns_step(state, nsteps: int) -> None:
 
 def ns_sync(state) -> None:
     _check(lib.ns_sync(state), state)
+
+
+def fp32_fma_peak(device: int = 0) -> float:
+    """Measured FP32 FMA rate of the device in TFLOP/s (ns_fp32_fma_peak)."""
+    t = ctypes.c_double()
+    _check(lib.ns_fp32_fma_peak(int(device), ctypes.byref(t)))
+    return t.value
 
 
 def ns_set_stream(state, stream_handle: int | None) -> None:
