@@ -123,6 +123,7 @@ def test_new_entry_points_check_arguments_before_any_device_call(ns):
     assert L.ns_cnn_gradients(None, None, None, 1, None, ns.ctypes.byref(f)) == E
     assert L.ns_cnn_train_step(None, None, None, 1, 1e-3, None, None) == E
     L.ns_cnn_destroy(None)
+    assert L.ns_fp32_fma_peak(0, None) == E
 
 
 @pytest.mark.parametrize("h,w,b", [(48, 64, 1), (64, 100, 1), (32, 32, 1), (64, 64, 0)])

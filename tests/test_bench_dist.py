@@ -71,3 +71,24 @@ def test_reference_arm_prints_on_rank_zero_only(rank):
         d = json.loads(lines[-1])
         assert d["impl"] == "reference" and d["n_gpus"] == 2 and d["value"] > 0
         assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["cpu_baseline"]["kind"] == "oracle"
+
+
+def test_flop_model_counts_every_transform():
+    """The bench's dense-FFT flop model, recounted transform by transform:
+    2.5 n log2 n flops per real transform of length n; per RK stage six
+    inverse and three forward real 3D transforms, each one 1D transform per
+    line along each of the three axes; per x-pass launch nine x-line
+    transforms per (z, y) line plus 9 flops per point for u x omega."""
+    import math
+
+    sys.path.insert(0, ROOT)
+    import bench
+
+    for n in (64, 256, 512, 1024):
+        per_pt, xpass = bench.flop_model(n)
+        lines_per_axis = n * n
+        one_axis = lines_per_axis * 2.5 * n * math.log2(n)
+        step = 4 * 9 * 3 * one_axis
+        assert per_pt * n ** 3 == pytest.approx(step, rel=1e-12)
+        assert xpass == pytest.approx(9 * one_axis + 9 * n ** 3, rel=1e-12)
+    assert bench.flop_model(512)[0] == pytest.approx(2430.0)

@@ -408,3 +408,15 @@ def test_pinned_host_buffers_equal_pageable_ones(ns, dim, n, prec):
         a.set_state(phys)
         ns._check(ns.lib.ns_set_state(b.state, ns.ctypes.c_void_p(p_in.data_ptr())), b.state)
         assert np.array_equal(a.get_state_spectral(), b.get_state_spectral())
+
+
+def test_fp32_fma_peak_is_a_plausible_rate(ns):
+    """The measured FP32 FMA rate that the bench divides by: positive, stable
+    between calls, and below the nominal rate of 128 FP32 lanes per SM at
+    2.07 GHz (a kernel that did less work than it claims would exceed it)."""
+    torch = pytest.importorskip("torch")
+    nsm = torch.cuda.get_device_properties(0).multi_processor_count
+    nominal = nsm * 128 * 2 * 2.07e9 / 1e12
+    a, b = ns.fp32_fma_peak(0), ns.fp32_fma_peak(0)
+    assert 0.3 * nominal < a < 1.02 * nominal
+    assert abs(a - b) < 0.05 * a
