@@ -302,9 +302,24 @@ def ensemble_bench(steps=50):
         e.step(steps)
         ev1.record(stream)
         torch.cuda.synchronize()
+        e.sync()
         ms = ev0.elapsed_time(ev1) / steps
         sched = e.schedule()
         tiles = e.tiles()
+        fused, fused_max = e.fused()
+        # the other form for the record: one cooperative launch per stage at the
+        # most resident blocks, or (if that was chosen) the two-launch form
+        if fused:
+            e.set_tiles(256, 8)
+        else:
+            e.set_fused(fused_max)
+        e.step(3)
+        ev0.record(stream)
+        e.step(steps)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        e.sync()
+        ms_other = ev0.elapsed_time(ev1) / steps
     solvers = [ns.Solver(2, n, ns.NS_FP32, nu=5e-4, dt=5e-4) for n in sizes]
     for s, u in zip(solvers, u0):
         s.set_stream(stream.cuda_stream)
@@ -323,7 +338,9 @@ def ensemble_bench(steps=50):
     return {"workload": ENSEMBLE_WORKLOAD, "metric": "Mpoint*RK4-steps/s", "steps": steps,
             "value": pts / (ms / 1e3) / 1e6, "ms_per_step": ms, "plain_value": pts / (ms_plain / 1e3) / 1e6,
             "plain_ms_per_step": ms_plain, "speedup_vs_plain": ms_plain / ms,
+            "one_launch_per_stage_ms_per_step" if not fused else "two_launches_per_stage_ms_per_step": ms_other,
             "schedule": {"y_block_threads": tiles[0], "x_block_warps": tiles[1],
+                         "one_launch_per_stage_blocks_per_sm": fused,
                          "x_blocks_per_sm": sched[0], "y_blocks_per_sm": sched[1],
                          "task_order": ["member-major", "round-robin"][sched[2]]}}
 

@@ -254,6 +254,17 @@ int ns_ensemble_set_schedule(ns_ensemble *e, int x_blocks_per_sm, int y_blocks_p
  * else NS_EINVAL).  Set synchronises the ensemble's stream. */
 int ns_ensemble_tiles(const ns_ensemble *e, int *y_threads, int *x_warps);
 int ns_ensemble_set_tiles(ns_ensemble *e, int y_threads, int x_warps);
+/* Fused form: every RK stage as ONE cooperative launch (the x pass over all
+ * members, a grid-wide barrier, the fused y pass) instead of two launches.
+ * Query the blocks per SM of that launch (0 = the two-launch form) and the
+ * most that can be resident; set 0 (two launches) or 1..max (else
+ * NS_EUNSUPPORTED).  A nonzero setting also selects the tile shapes it runs
+ * (256-thread y blocks, 8-warp x blocks); ns_ensemble_set_tiles returns to the
+ * two-launch form.  The barrier's wait is bounded: a wait that gives up is
+ * reported as NS_ETIMEOUT by ns_ensemble_sync.  Set synchronises the
+ * ensemble's stream.  Results are those of the two-launch form, bit for bit. */
+int ns_ensemble_fused(const ns_ensemble *e, int *blocks_per_sm, int *max_blocks_per_sm);
+int ns_ensemble_set_fused(ns_ensemble *e, int blocks_per_sm);
 
 /* Member state in the canonical 2D truncated spectral layout (host complex128
  * as double pairs, [c][h] of that member's grid).  Synchronise. */

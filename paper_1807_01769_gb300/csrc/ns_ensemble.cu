@@ -11,6 +11,8 @@
 // that of ns_step on the same grid.  Blocks walk a task list (member, unit)
 // with stride gridDim.x; the grid size per pass and the task order are the
 // schedule, chosen at init by timing the candidates (autotune) or fixed.
+// The fused form runs both passes of a stage in ONE cooperative launch, the
+// passes separated by a grid-wide barrier; it is a schedule candidate too.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -117,11 +119,92 @@ constexpr size_t ens_smem_x() {
   return (size_t)XW * ens_warp_region() * sizeof(C);
 }
 
+// ------------------------------------------------- fused stage (one launch) --
+constexpr long long kGridSpins = 1LL << 24;  // ~1 s of 64 ns naps
+enum EnsErr { ENS_ERR_GRID_TIMEOUT = 2 };
+
+// Grid-wide barrier of a cooperative launch (all blocks resident).  Thread 0
+// of each block counts in; the last block to arrive resets the count and
+// advances the generation word, the others wait (bounded) for it to change.
+// On time-out the error word is set and the block goes on: no block leaves
+// early, so no later block barrier waits for an exited thread.  The closing
+// acquire fence makes the other blocks' writes visible to this block's loads.
+__device__ __forceinline__ void ens_grid_barrier(unsigned *gbar, int *err) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned *gen = gbar + 1;
+    const unsigned g0 = *gen;
+    __threadfence();
+    if (atomicAdd(gbar, 1u) == gridDim.x - 1) {
+      atomicExch(gbar, 0u);
+      __threadfence();
+      atomicAdd(gbar + 1, 1u);
+    } else {
+      long long i = 0;
+      while (*gen == g0 && ++i < kGridSpins) __nanosleep(64);
+      if (*gen == g0) atomicExch(err, ENS_ERR_GRID_TIMEOUT);
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  asm volatile("fence.acq_rel.gpu;\n" ::: "memory");
+}
+
+// One RK stage in one launch: the x pass over its units (8 warps a block, as
+// k2e_xpass<R, 8>), the barrier, the fused y pass over its units (256
+// threads, as k2e_fwd1<R, MODE, 256>).  The same device functions as the
+// split form, so the same results bit for bit.
+// MINB: resident blocks per SM the registers are sized for (1: 255 registers,
+// the x phase without spills to speak of; 2: 128 registers, two blocks per SM
+// for both phases).
+template <typename R, int MODE, int MINB>
+__global__ void __launch_bounds__(256, MINB) k2e_stage_fused(const EnsMember<R> *__restrict__ mem,
+                                                      const int2 *__restrict__ xt, int nx,
+                                                      const int2 *__restrict__ yt, int ny, unsigned *gbar, int *err) {
+  using C = typename CplxOf<R>::T;
+  {
+    C *sm = dyn_smem<C>() + (threadIdx.x >> 5) * ens_warp_region();
+    for (int i = blockIdx.x; i < nx; i += gridDim.x) {
+      const int2 tk = xt[i];
+      const Geo g = mem[tk.x].g;
+      const StepBufs<R> b = mem[tk.x].b;
+      switch (g.N) {
+        case 64: xpass_2d_unit<R, 64, 8>(g, b.yb, b.tw, tk.y, sm); break;
+        case 128: xpass_2d_unit<R, 128, 8>(g, b.yb, b.tw, tk.y, sm); break;
+        case 256: xpass_2d_unit<R, 256, 8>(g, b.yb, b.tw, tk.y, sm); break;
+        default: xpass_2d_unit<R, 512, 8>(g, b.yb, b.tw, tk.y, sm); break;
+      }
+      __syncwarp();
+    }
+  }
+  ens_grid_barrier(gbar, err);  // every member's x lines are written
+  C *sm = dyn_smem<C>();
+  for (int i = blockIdx.x; i < ny; i += gridDim.x) {
+    const int2 tk = yt[i];
+    const Geo g = mem[tk.x].g;
+    const StepBufs<R> b = mem[tk.x].b;
+    switch (g.N) {
+      case 64: fwd1_2d_unit<R, 64, ens_w(64, 256), MODE, true>(g, b, tk.y, sm); break;
+      case 128: fwd1_2d_unit<R, 128, ens_w(128, 256), MODE, true>(g, b, tk.y, sm); break;
+      case 256: fwd1_2d_unit<R, 256, ens_w(256, 256), MODE, true>(g, b, tk.y, sm); break;
+      default: fwd1_2d_unit<R, 512, ens_w(512, 256), MODE, true>(g, b, tk.y, sm); break;
+    }
+    __syncthreads();
+  }
+}
+template <typename C>
+constexpr size_t ens_smem_fused() {
+  return std::max(ens_smem_x<C, 8>(), ens_smem_y<C, 256>());
+}
+
 struct EnsLaunch {
   const void *mem;
   const int2 *xt, *yt;
   int nx, ny, gx, gy;
   int ythreads, xwarps;  // tile shapes: y-pass block threads (256, 512), x-pass warps per block (4, 8)
+  int gf, gf_per_sm;     // fused form: blocks of its one launch per stage, per SM (0: the split form)
+  unsigned *gbar;        // fused form: barrier count and generation
+  int *err;              // device error word
 };
 
 template <typename R, int YT, int XW>
@@ -136,9 +219,29 @@ void ens_prepare_shape() {
 }
 template <typename R>
 int ens_prepare() {
+  using C = typename CplxOf<R>::T;
   ens_prepare_shape<R, 256, 4>();
   ens_prepare_shape<R, 512, 8>();
+  set_smem(k2e_stage_fused<R, MODE_RK1, 1>, ens_smem_fused<C>());
+  set_smem(k2e_stage_fused<R, MODE_RK2, 1>, ens_smem_fused<C>());
+  set_smem(k2e_stage_fused<R, MODE_RK3, 1>, ens_smem_fused<C>());
+  set_smem(k2e_stage_fused<R, MODE_RK4, 1>, ens_smem_fused<C>());
+  set_smem(k2e_stage_fused<R, MODE_RK1, 2>, ens_smem_fused<C>());
+  set_smem(k2e_stage_fused<R, MODE_RK2, 2>, ens_smem_fused<C>());
+  set_smem(k2e_stage_fused<R, MODE_RK3, 2>, ens_smem_fused<C>());
+  set_smem(k2e_stage_fused<R, MODE_RK4, 2>, ens_smem_fused<C>());
   return (int)cudaGetLastError();
+}
+// resident blocks per SM of the fused stage kernel (the most its cooperative
+// launch may ask for)
+template <typename R>
+int ens_fused_occupancy() {
+  using C = typename CplxOf<R>::T;
+  int occ = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k2e_stage_fused<R, MODE_RK2, 2>, 256, ens_smem_fused<C>()) !=
+      cudaSuccess)
+    occ = 0;
+  return occ;
 }
 
 template <typename R, int YT>
@@ -168,8 +271,40 @@ void ens_stage_shape(const EnsLaunch &l, int mode, cudaStream_t s) {
     default: k2e_fwd1<R, MODE_RK4, YT><<<l.gy, YT, sy, s>>>(m, l.yt, l.ny); break;
   }
 }
+template <typename R, int MODE, int MINB>
+cudaError_t ens_fused_launch(const EnsLaunch &l, cudaStream_t s) {
+  using C = typename CplxOf<R>::T;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)l.gf);
+  cfg.blockDim = dim3(256);
+  cfg.dynamicSmemBytes = ens_smem_fused<C>();
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeCooperative;
+  at[0].val.cooperative = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k2e_stage_fused<R, MODE, MINB>, (const EnsMember<R> *)l.mem, l.xt, l.nx, l.yt,
+                            l.ny, l.gbar, l.err);
+}
 template <typename R>
 int ens_stage(const EnsLaunch &l, int mode, cudaStream_t s) {
+  if (l.gf > 0 && l.gf_per_sm == 1) {
+    switch (mode) {
+      case MODE_RK1: return (int)ens_fused_launch<R, MODE_RK1, 1>(l, s);
+      case MODE_RK2: return (int)ens_fused_launch<R, MODE_RK2, 1>(l, s);
+      case MODE_RK3: return (int)ens_fused_launch<R, MODE_RK3, 1>(l, s);
+      default: return (int)ens_fused_launch<R, MODE_RK4, 1>(l, s);
+    }
+  }
+  if (l.gf > 0) {
+    switch (mode) {
+      case MODE_RK1: return (int)ens_fused_launch<R, MODE_RK1, 2>(l, s);
+      case MODE_RK2: return (int)ens_fused_launch<R, MODE_RK2, 2>(l, s);
+      case MODE_RK3: return (int)ens_fused_launch<R, MODE_RK3, 2>(l, s);
+      default: return (int)ens_fused_launch<R, MODE_RK4, 2>(l, s);
+    }
+  }
   if (l.ythreads == 512 && l.xwarps == 8)
     ens_stage_shape<R, 512, 8>(l, mode, s);
   else if (l.ythreads == 512)
@@ -213,6 +348,8 @@ struct ns_ensemble {
   void *mem = nullptr, *xt = nullptr, *yt = nullptr, *staging = nullptr, *diag = nullptr;
   int nx = 0, ny = 0, xb = 4, yb_per_sm = 2, order = 0;
   int ythreads = 256, xwarps = 4;  // tile shapes of the schedule
+  int fused = 0, fused_occ = 0;    // fused form: blocks per SM of its one launch per stage (0: split form)
+  void *gbar = nullptr, *derr = nullptr;
   long long diag_scratch = 0;
   int max_bins = 0;
   cudaStream_t own = nullptr, stream = nullptr, cap = nullptr;
@@ -303,6 +440,10 @@ nsk::EnsLaunch launch_of(const ns_ensemble *e) {
   l.gy = std::max(1, std::min(e->ny, e->yb_per_sm * e->nsm));
   l.ythreads = e->ythreads;
   l.xwarps = e->xwarps;
+  l.gf = e->fused > 0 ? e->fused * e->nsm : 0;
+  l.gf_per_sm = e->fused;
+  l.gbar = (unsigned *)e->gbar;
+  l.err = (int *)e->derr;
   return l;
 }
 
@@ -514,8 +655,13 @@ int ns_ensemble_init(ns_ensemble **out, int count, const int *n, int precision, 
   build_tasks(e, 0, xt, yt);
   if ((rc = emalloc(e, &e->mem, member_bytes * count)) || (rc = emalloc(e, &e->xt, sizeof(int2) * xt.size())) ||
       (rc = emalloc(e, &e->yt, sizeof(int2) * yt.size())) || (rc = emalloc(e, &e->staging, max_stage)) ||
-      (rc = emalloc(e, &e->diag, sizeof(double) * (size_t)(e->diag_scratch + e->max_bins + 2))))
+      (rc = emalloc(e, &e->diag, sizeof(double) * (size_t)(e->diag_scratch + e->max_bins + 2))) ||
+      (rc = emalloc(e, &e->gbar, 2 * sizeof(unsigned))) || (rc = emalloc(e, &e->derr, sizeof(int))))
     return bail(rc);
+  if (cudaMemset(e->gbar, 0, 2 * sizeof(unsigned)) != cudaSuccess || cudaMemset(e->derr, 0, sizeof(int)) != cudaSuccess) {
+    efail(e, NS_ECUDA, "cudaMemset failed");
+    return bail(NS_ECUDA);
+  }
   rc = precision == NS_FP32 ? upload_members<float>(e) : upload_members<double>(e);
   if (rc) return bail(rc);
   const int prc = precision == NS_FP32 ? nsk::ens_prepare<float>() : nsk::ens_prepare<double>();
@@ -523,6 +669,10 @@ int ns_ensemble_init(ns_ensemble **out, int count, const int *n, int precision, 
     efail(e, NS_ECUDA, "kernel attributes: %s", cudaGetErrorString((cudaError_t)prc));
     return bail(NS_ECUDA);
   }
+  int coop = 0;
+  cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, e->dev);
+  e->fused_occ = coop ? (precision == NS_FP32 ? nsk::ens_fused_occupancy<float>() : nsk::ens_fused_occupancy<double>())
+                      : 0;
   if ((rc = upload_tasks(e, 0))) return bail(rc);
   if (autotune) {
     // schedule candidates timed on the zero state (every transform costs the
@@ -530,7 +680,8 @@ int ns_ensemble_init(ns_ensemble **out, int count, const int *n, int precision, 
     // threads, i.e. kx tiles of W or 2W columns; x-pass blocks of 4 or 8
     // warps), blocks per SM of each pass and the task order
     float best = 1e30f;
-    int bx = e->xb, by = e->yb_per_sm, bo = 0, byt = 256, bxw = 4;
+    int bx = e->xb, by = e->yb_per_sm, bo = 0, byt = 256, bxw = 4, bf = 0;
+    e->fused = 0;
     for (int yt : {256, 512})
       for (int xw : {4, 8})
         for (int order = 0; order < 2; ++order) {
@@ -557,10 +708,33 @@ int ns_ensemble_init(ns_ensemble **out, int count, const int *n, int precision, 
               }
             }
         }
+    // the fused form: one cooperative launch per stage, 1 .. occupancy blocks per SM
+    e->ythreads = 256;
+    e->xwarps = 8;
+    for (int order = 0; order < 2; ++order) {
+      if ((rc = upload_tasks(e, order))) return bail(rc);
+      for (int f = 1; f <= e->fused_occ; ++f) {
+        e->fused = f;
+        const float ms = time_stage(e, 3);
+        e->fused = 0;
+        if (cudaGetLastError() != cudaSuccess) {
+          efail(e, NS_ECUDA, "autotune launch (fused form) failed");
+          return bail(NS_ECUDA);
+        }
+        if (ms < best) {
+          best = ms;
+          bo = order;
+          byt = 256;
+          bxw = 8;
+          bf = f;
+        }
+      }
+    }
     e->ythreads = byt;
     e->xwarps = bxw;
     e->xb = bx;
     e->yb_per_sm = by;
+    e->fused = bf;
     if ((rc = upload_tasks(e, bo))) return bail(rc);
     for (int m = 0; m < count; ++m) {  // the timing stages wrote the accumulators
       cudaMemset(e->acc[m], 0, e->cs * e->geo[m].st_comp);
@@ -610,6 +784,32 @@ int ns_ensemble_set_tiles(ns_ensemble *e, int y_threads, int x_warps) {
   ENS_CK(e, cudaStreamSynchronize(e->stream));
   e->ythreads = y_threads;
   e->xwarps = x_warps;
+  e->fused = 0;  // explicit tile shapes select the split form
+  int rc = upload_tasks(e, e->order);
+  if (rc) return rc;
+  drop_graph(e);
+  return NS_OK;
+}
+
+int ns_ensemble_fused(const ns_ensemble *e, int *blocks_per_sm, int *max_blocks_per_sm) {
+  if (!e) return NS_EINVAL;
+  if (blocks_per_sm) *blocks_per_sm = e->fused;
+  if (max_blocks_per_sm) *max_blocks_per_sm = e->fused_occ;
+  return NS_OK;
+}
+
+int ns_ensemble_set_fused(ns_ensemble *e, int blocks_per_sm) {
+  if (!e || blocks_per_sm < 0) return e ? efail(e, NS_EINVAL, "ns_ensemble_set_fused: blocks_per_sm < 0") : NS_EINVAL;
+  if (blocks_per_sm > e->fused_occ)
+    return efail(e, NS_EUNSUPPORTED, "ns_ensemble_set_fused: %d blocks per SM, at most %d can be resident",
+                 blocks_per_sm, e->fused_occ);
+  DevGuardE dg(e->dev);
+  ENS_CK(e, cudaStreamSynchronize(e->stream));
+  e->fused = blocks_per_sm;
+  if (blocks_per_sm > 0) {  // the fused kernel's tile shapes
+    e->ythreads = 256;
+    e->xwarps = 8;
+  }
   int rc = upload_tasks(e, e->order);
   if (rc) return rc;
   drop_graph(e);
@@ -627,6 +827,14 @@ int ns_ensemble_sync(ns_ensemble *e) {
   DevGuardE dg(e->dev);
   ENS_CK(e, cudaStreamSynchronize(e->stream));
   ENS_CK(e, cudaGetLastError());
+  int w = 0;
+  ENS_CK(e, cudaMemcpy(&w, e->derr, sizeof(int), cudaMemcpyDeviceToHost));
+  if (w != 0) {
+    ENS_CK(e, cudaMemset(e->derr, 0, sizeof(int)));
+    ENS_CK(e, cudaMemset(e->gbar, 0, 2 * sizeof(unsigned)));  // a count left behind by the abandoned barrier
+    return efail(e, NS_ETIMEOUT, "a bounded grid-wide wait gave up (code %d): results of the affected steps are invalid",
+                 w);
+  }
   return NS_OK;
 }
 

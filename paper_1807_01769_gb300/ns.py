@@ -69,6 +69,8 @@ SIGNATURES = {
     "ns_ensemble_set_schedule": ([_P, _I, _I, _I], _I),
     "ns_ensemble_tiles": ([_P, _PI, _PI], _I),
     "ns_ensemble_set_tiles": ([_P, _I, _I], _I),
+    "ns_ensemble_fused": ([_P, _PI, _PI], _I),
+    "ns_ensemble_set_fused": ([_P, _I], _I),
     "ns_ensemble_set_state_spectral": ([_P, _I, _P], _I),
     "ns_ensemble_get_state_spectral": ([_P, _I, _P], _I),
     "ns_ensemble_step": ([_P, _I], _I),
@@ -350,6 +352,15 @@ class Ensemble:
 
     def set_tiles(self, y_threads: int, x_warps: int) -> None:
         _echeck(lib.ns_ensemble_set_tiles(self.ens, int(y_threads), int(x_warps)), self.ens)
+
+    def fused(self):
+        """(blocks per SM of the one-launch-per-stage form, 0 = two launches; the most allowed)."""
+        a, b = _I(), _I()
+        _echeck(lib.ns_ensemble_fused(self.ens, ctypes.byref(a), ctypes.byref(b)), self.ens)
+        return a.value, b.value
+
+    def set_fused(self, blocks_per_sm: int) -> None:
+        _echeck(lib.ns_ensemble_set_fused(self.ens, int(blocks_per_sm)), self.ens)
 
     def set_state_spectral(self, member: int, spec) -> None:
         s = np.ascontiguousarray(spec, dtype=np.complex128).reshape(self.shapes[member])

@@ -61,6 +61,37 @@ def test_members_bitwise_equal_single_runs_for_every_schedule(ns, prec):
             e.set_tiles(384, 4)
 
 
+@pytest.mark.parametrize("prec", [FP32, FP64])
+def test_fused_form_equals_single_runs(ns, prec):
+    """One cooperative launch per RK stage (x pass, grid-wide barrier, fused y
+    pass) gives every member bit for bit the result of its own ns_step run,
+    for every allowed block count and both task orders."""
+    sizes = [128, 256, 64, 512, 128, 256]
+    nu, dt, steps = 5e-4, 5e-4, 5
+    u0 = [ic(n, seed) for seed, n in enumerate(sizes)]
+    ref = [single(ns, n, prec, nu, dt, steps, u) for n, u in zip(sizes, u0)]
+    with ns.Ensemble(sizes, prec, nu=nu, dt=dt, autotune=False) as e:
+        f, fmax = e.fused()
+        assert f == 0 and fmax >= 1
+        for bpsm in sorted({1, fmax}):
+            for order in (0, 1):
+                e.set_fused(bpsm)
+                e.set_schedule(2, 2, order)
+                assert e.fused() == (bpsm, fmax) and e.tiles() == (256, 8)
+                for m, u in enumerate(u0):
+                    e.set_state_spectral(m, u)
+                e.step(steps)
+                e.sync()  # the barrier's bounded waits all ended in time
+                for m in range(len(sizes)):
+                    assert np.array_equal(e.get_state_spectral(m), ref[m]), (bpsm, order, m)
+        with pytest.raises(ns.NSError):
+            e.set_fused(fmax + 1)
+        with pytest.raises(ns.NSError):
+            e.set_fused(-1)
+        e.set_tiles(256, 4)
+        assert e.fused()[0] == 0
+
+
 def test_members_match_oracle(ns, orc):
     sizes = [64, 128]
     nu, dt, steps = 1e-3, 1e-3, 20
@@ -108,11 +139,15 @@ def test_all_64_members_bitwise_under_mixed_schedules(ns):
     u0 = [ic(n, seed) for seed, n in enumerate(sizes)]
     ref = [single(ns, n, FP32, nu, dt, steps, u) for n, u in zip(sizes, u0)]
     with ns.Ensemble(sizes, FP32, nu=nu, dt=dt, autotune=False) as e:
-        for tiles, sched in [((256, 4), (4, 2, 0)), ((512, 8), (8, 4, 1)), ((512, 4), (1, 1, 0))]:
-            e.set_tiles(*tiles)
+        for tiles, sched in [((256, 4), (4, 2, 0)), ((512, 8), (8, 4, 1)), ((512, 4), (1, 1, 0)), ("fused", (1, 1, 1))]:
+            if tiles == "fused":
+                e.set_fused(1)
+            else:
+                e.set_tiles(*tiles)
             e.set_schedule(*sched)
             for m, u in enumerate(u0):
                 e.set_state_spectral(m, u)
             e.step(steps)
+            e.sync()
             bad = [m for m in range(len(sizes)) if not np.array_equal(e.get_state_spectral(m), ref[m])]
             assert not bad, (tiles, sched, bad[:8])
