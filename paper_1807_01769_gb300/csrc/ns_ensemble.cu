@@ -68,9 +68,19 @@ __host__ __device__ constexpr int ens_warp_region() {
               cmax(2 * xw_line_len<256, true>(), 1 * xw_line_len<512, false>()));
 }
 
-// XW warps per block (a tile shape of the schedule: 4 or 8)
+// One x-pass unit of grid size N behind a call: each size's transform gets
+// its own register allocation instead of the union of all four inlined
+// behind the switch (which needed 255 registers and spilled inside the
+// transforms); the call costs a register save and restore per unit.
+template <typename R, int N, int XW>
+__device__ __noinline__ void xpass_unit_call(const Geo &g, typename CplxOf<R>::T *yb, const typename CplxOf<R>::T *tw,
+                                             int unit, typename CplxOf<R>::T *sm) {
+  xpass_2d_unit<R, N, XW>(g, yb, tw, unit, sm);
+}
+// XW warps per block (a tile shape of the schedule: 4 or 8); 4-warp blocks
+// are sized for three resident per SM (168 registers)
 template <typename R, int XW = 4>
-__global__ void __launch_bounds__(32 * XW) k2e_xpass(const EnsMember<R> *__restrict__ mem, const int2 *__restrict__ tasks,
+__global__ void __launch_bounds__(32 * XW, XW == 4 ? 3 : 1) k2e_xpass(const EnsMember<R> *__restrict__ mem, const int2 *__restrict__ tasks,
                                                     int ntasks) {
   using C = typename CplxOf<R>::T;
   C *sm = dyn_smem<C>() + (threadIdx.x >> 5) * ens_warp_region();
@@ -79,10 +89,10 @@ __global__ void __launch_bounds__(32 * XW) k2e_xpass(const EnsMember<R> *__restr
     const Geo g = mem[tk.x].g;
     const StepBufs<R> b = mem[tk.x].b;
     switch (g.N) {
-      case 64: xpass_2d_unit<R, 64, XW>(g, b.yb, b.tw, tk.y, sm); break;
-      case 128: xpass_2d_unit<R, 128, XW>(g, b.yb, b.tw, tk.y, sm); break;
-      case 256: xpass_2d_unit<R, 256, XW>(g, b.yb, b.tw, tk.y, sm); break;
-      default: xpass_2d_unit<R, 512, XW>(g, b.yb, b.tw, tk.y, sm); break;
+      case 64: xpass_unit_call<R, 64, XW>(g, b.yb, b.tw, tk.y, sm); break;
+      case 128: xpass_unit_call<R, 128, XW>(g, b.yb, b.tw, tk.y, sm); break;
+      case 256: xpass_unit_call<R, 256, XW>(g, b.yb, b.tw, tk.y, sm); break;
+      default: xpass_unit_call<R, 512, XW>(g, b.yb, b.tw, tk.y, sm); break;
     }
     __syncwarp();
   }
@@ -169,10 +179,10 @@ __global__ void __launch_bounds__(256, MINB) k2e_stage_fused(const EnsMember<R> 
       const Geo g = mem[tk.x].g;
       const StepBufs<R> b = mem[tk.x].b;
       switch (g.N) {
-        case 64: xpass_2d_unit<R, 64, 8>(g, b.yb, b.tw, tk.y, sm); break;
-        case 128: xpass_2d_unit<R, 128, 8>(g, b.yb, b.tw, tk.y, sm); break;
-        case 256: xpass_2d_unit<R, 256, 8>(g, b.yb, b.tw, tk.y, sm); break;
-        default: xpass_2d_unit<R, 512, 8>(g, b.yb, b.tw, tk.y, sm); break;
+        case 64: xpass_unit_call<R, 64, 8>(g, b.yb, b.tw, tk.y, sm); break;
+        case 128: xpass_unit_call<R, 128, 8>(g, b.yb, b.tw, tk.y, sm); break;
+        case 256: xpass_unit_call<R, 256, 8>(g, b.yb, b.tw, tk.y, sm); break;
+        default: xpass_unit_call<R, 512, 8>(g, b.yb, b.tw, tk.y, sm); break;
       }
       __syncwarp();
     }
@@ -688,7 +698,7 @@ int ns_ensemble_init(ns_ensemble **out, int count, const int *n, int precision, 
           e->ythreads = yt;
           e->xwarps = xw;
           if ((rc = upload_tasks(e, order))) return bail(rc);
-          for (int xb : {1, 2, 4, 8})
+          for (int xb : {1, 2, 3, 4, 8})
             for (int ybp : {1, 2, 4}) {
               if (xb * 32 * xw > 2048 || ybp * yt > 2048) continue;  // resident threads per SM
               e->xb = xb;
